@@ -1,0 +1,395 @@
+/*
+ * pcf_oracle.c -- CPU reference for the PCF integral matrices.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg load this file.  It shares no code, header,
+ * table or helper with the CUDA library; the product path never calls it.
+ *
+ * Everything here is plain float64 C, written for readability, not speed:
+ *
+ *   orc_rectangles      rectangle iteration over [0, inf)     (Sec. 3, Alg. 1)
+ *   orc_integral        combine-and-integrate of h(f, g)      (Sec. 3, Alg. 2,
+ *                                                              Eq. simpleint)
+ *   orc_matrix          pairwise / cross matrices F_ij = r(I_ij)
+ *                                                             (Sec. 3.1; Sec. 2.2
+ *                                                              for r and h)
+ *   orc_segment_sq      integral of f^2 by segment iteration  (Sec. 3.2, Alg. 3)
+ *   orc_backward        gradient of sum_ij G_ij F_ij with respect to the
+ *                       breakpoint values and times (not in the paper; derived
+ *                       from Eq. simpleint by differentiating each rectangle)
+ *
+ * Combination functions h (Sec. 2.2): the L_p distance uses h(a,b) = |a-b|^p
+ * with r(x) = x^(1/p); the L2 inner product uses h(a,b) = a*b with r = id.
+ *
+ * Readings of points the paper leaves open (each one is listed with its reason
+ * in the design notes of the repository):
+ *  - a PCF is stored as n >= 1 breakpoints t_0 = 0 < t_1 < ... < t_{n-1} with
+ *    values v_0..v_{n-1}; v_{n-1} holds on [t_{n-1}, inf).
+ *  - the last rectangle [t_last, inf) adds 0 when h(v_f, v_g) = 0 and
+ *    h * inf (= +-inf) otherwise (0 * inf is not used).
+ *  - |d|^p: p = 1 gives |d|, p = 2 gives d*d, other integer p a left-to-right
+ *    product of |d|, non-integer p pow(|d|, p).  The root r uses sqrt for p = 2
+ *    and pow(x, 1/p) for other p != 1.
+ *  - gradient at a breakpoint that both PCFs share: each side takes the value
+ *    of the other PCF just before the breakpoint (left limit), which is what the
+ *    simultaneous advance of Alg. 1 hands out.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { ORC_L1 = 0, ORC_L2 = 1, ORC_LP = 2, ORC_GRAM = 3 };
+
+/* |d|^p as described in the header comment. */
+static double orc_pow_abs(double d, double p)
+{
+    double a = fabs(d);
+    if (p == 1.0) return a;
+    if (p == 2.0) return d * d;
+    if (p == floor(p) && p > 2.0 && p <= 64.0) {
+        double r = a;
+        for (int i = 1; i < (int)p; ++i) r = r * a;
+        return r;
+    }
+    return pow(a, p);
+}
+
+/* Combination function h of Sec. 2.2 for the requested matrix. */
+static double orc_h(int metric, double p, double a, double b)
+{
+    switch (metric) {
+    case ORC_L1: return fabs(a - b);
+    case ORC_L2: return (a - b) * (a - b);
+    case ORC_LP: return orc_pow_abs(a - b, p);
+    default: return a * b;  /* ORC_GRAM */
+    }
+}
+
+/* Partial derivative of h with respect to its first argument. */
+static double orc_dh_da(int metric, double p, double a, double b)
+{
+    double d = a - b;
+    double s = (d > 0.0) ? 1.0 : ((d < 0.0) ? -1.0 : 0.0);
+    switch (metric) {
+    case ORC_L1: return s;
+    case ORC_L2: return 2.0 * d;
+    case ORC_LP:
+        if (d == 0.0) return 0.0;
+        return p * orc_pow_abs(d, p - 1.0) * s;
+    default: return b;  /* ORC_GRAM */
+    }
+}
+
+/* Exponent of the metric (1 for L1, 2 for L2, p for LP, 1 for the Gram). */
+static double orc_exponent(int metric, double p)
+{
+    if (metric == ORC_L1) return 1.0;
+    if (metric == ORC_L2) return 2.0;
+    if (metric == ORC_LP) return p;
+    return 1.0;
+}
+
+/* r(x) of Sec. 2.2: x^(1/p) for distances when requested, else x. */
+static double orc_root(int metric, double p, int apply_root, double x)
+{
+    if (!apply_root || metric == ORC_GRAM) return x;
+    double e = orc_exponent(metric, p);
+    if (e == 1.0) return x;
+    if (e == 2.0) return sqrt(x);
+    return pow(x, 1.0 / e);
+}
+
+/* dr/dx at the integral value x. */
+static double orc_droot(int metric, double p, int apply_root, double x)
+{
+    if (!apply_root || metric == ORC_GRAM) return 1.0;
+    double e = orc_exponent(metric, p);
+    if (e == 1.0) return 1.0;
+    return (1.0 / e) * pow(x, 1.0 / e - 1.0);
+}
+
+/*
+ * Rectangle iteration of Alg. 1 with a = 0 and b = inf.
+ *
+ * Two cursors k (into f) and kg (into g) start at the breakpoint at t = 0.
+ * Each pass emits the rectangle that starts at the current scanline time
+ * with the values f(t), g(t), after moving whichever cursor has the earlier
+ * next breakpoint (both on a tie).  When neither can move, the final
+ * rectangle reaches to b = inf.  Rectangles are handed to `emit`; the
+ * return value is the number of rectangles.
+ */
+typedef void (*orc_emit_fn)(void* ctx, double l, double r, double vf, double vg,
+                            int64_t kf, int64_t kg, int moved_f, int moved_g);
+
+static int64_t orc_walk(const double* tf, const double* vf, int64_t nf,
+                        const double* tg, const double* vg, int64_t ng,
+                        orc_emit_fn emit, void* ctx)
+{
+    int64_t k = 0, kg = 0, count = 0;
+    double t = 0.0;
+    for (;;) {
+        double t_prev = t;
+        double a = vf[k], b = vg[kg];
+        int64_t k_old = k, kg_old = kg;
+        int moved_f = 0, moved_g = 0;
+        if (k + 1 < nf && kg + 1 < ng) {
+            /* sign of delta = t_{k+1} - t'_{k'+1} decides who moves */
+            if (tf[k + 1] <= tg[kg + 1]) { k += 1; moved_f = 1; }
+            if (tg[kg + 1] <= tf[k_old + 1]) { kg += 1; moved_g = 1; }
+        } else if (k + 1 < nf) {
+            k += 1; moved_f = 1;
+        } else if (kg + 1 < ng) {
+            kg += 1; moved_g = 1;
+        } else {
+            emit(ctx, t_prev, INFINITY, a, b, k_old, kg_old, 0, 0);
+            return count + 1;
+        }
+        t = (tf[k] > tg[kg]) ? tf[k] : tg[kg];
+        emit(ctx, t_prev, t, a, b, k_old, kg_old, moved_f, moved_g);
+        count += 1;
+    }
+}
+
+/* ---- rectangles as a list (for tests of Alg. 1 itself) ---- */
+typedef struct { double* l; double* r; double* a; double* b; int64_t cap; int64_t n; } orc_rect_list;
+
+static void orc_emit_list(void* ctx, double l, double r, double a, double b,
+                          int64_t kf, int64_t kg, int mf, int mg)
+{
+    (void)kf; (void)kg; (void)mf; (void)mg;
+    orc_rect_list* L = (orc_rect_list*)ctx;
+    if (L->n < L->cap) {
+        L->l[L->n] = l; L->r[L->n] = r; L->a[L->n] = a; L->b[L->n] = b;
+    }
+    L->n += 1;
+}
+
+int64_t orc_rectangles(const double* tf, const double* vf, int64_t nf,
+                       const double* tg, const double* vg, int64_t ng,
+                       double* l, double* r, double* a, double* b, int64_t cap)
+{
+    orc_rect_list L = { l, r, a, b, cap, 0 };
+    orc_walk(tf, vf, nf, tg, vg, ng, orc_emit_list, &L);
+    return L.n;
+}
+
+/* ---- Alg. 2: I = sum over rectangles of h(v_f, v_g) * (r - l) ---- */
+typedef struct { int metric; double p; double I; } orc_acc;
+
+static void orc_emit_acc(void* ctx, double l, double r, double a, double b,
+                         int64_t kf, int64_t kg, int mf, int mg)
+{
+    (void)kf; (void)kg; (void)mf; (void)mg;
+    orc_acc* A = (orc_acc*)ctx;
+    double h = orc_h(A->metric, A->p, a, b);
+    if (isinf(r)) {
+        if (h != 0.0) A->I += h * INFINITY;  /* diverging tail */
+        return;
+    }
+    A->I += h * (r - l);
+}
+
+double orc_integral(const double* tf, const double* vf, int64_t nf,
+                    const double* tg, const double* vg, int64_t ng,
+                    int metric, double p)
+{
+    orc_acc A = { metric, p, 0.0 };
+    orc_walk(tf, vf, nf, tg, vg, ng, orc_emit_acc, &A);
+    return A.I;
+}
+
+/* Number of rectangles of the pair = |T_f u T_g| (the merge-step count). */
+int64_t orc_merge_steps(const double* tf, int64_t nf, const double* tg, int64_t ng)
+{
+    int64_t i = 0, j = 0, m = 0;
+    while (i < nf || j < ng) {
+        if (j >= ng || (i < nf && tf[i] < tg[j])) { i++; }
+        else if (i >= nf || tg[j] < tf[i]) { j++; }
+        else { i++; j++; }
+        m++;
+    }
+    return m;
+}
+
+/* ---- matrices ---- */
+typedef struct {
+    int64_t na, nb;
+    const int64_t *oa, *ob;
+    const double *ta, *va, *tb, *vb;
+    int metric; double p; int apply_root;
+    int symmetric;       /* pairwise: fill only j >= i and mirror */
+    double* out;         /* na x nb row-major */
+    int64_t next_row;
+    pthread_mutex_t lock;
+} orc_job;
+
+static void orc_do_row(orc_job* J, int64_t i)
+{
+    const double* tf = J->ta + J->oa[i];
+    const double* vf = J->va + J->oa[i];
+    int64_t nf = J->oa[i + 1] - J->oa[i];
+    int64_t j0 = J->symmetric ? i : 0;
+    for (int64_t j = j0; j < J->nb; ++j) {
+        const double* tg = J->tb + J->ob[j];
+        const double* vg = J->vb + J->ob[j];
+        int64_t ng = J->ob[j + 1] - J->ob[j];
+        double I = orc_integral(tf, vf, nf, tg, vg, ng, J->metric, J->p);
+        double F = orc_root(J->metric, J->p, J->apply_root, I);
+        J->out[i * J->nb + j] = F;
+        if (J->symmetric) J->out[j * J->nb + i] = F;
+    }
+}
+
+static void* orc_worker(void* arg)
+{
+    orc_job* J = (orc_job*)arg;
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        int64_t i = J->next_row++;
+        pthread_mutex_unlock(&J->lock);
+        if (i >= J->na) return NULL;
+        orc_do_row(J, i);
+    }
+}
+
+/*
+ * F(C) of Sec. 3.1.  With (ob, tb, vb) == NULL the matrix is the pairwise
+ * matrix of set A (symmetric; rows [row_begin, row_end) of it); otherwise the
+ * cross matrix rows of A x B.  `out` is (row_end - row_begin) x nb.
+ */
+void orc_matrix(int64_t na, const int64_t* oa, const double* ta, const double* va,
+                int64_t nb, const int64_t* ob, const double* tb, const double* vb,
+                int64_t row_begin, int64_t row_end,
+                int metric, double p, int apply_root, double* out, int nthreads)
+{
+    orc_job J;
+    memset(&J, 0, sizeof J);
+    int pairwise = (ob == NULL);
+    /* rows of A restricted to [row_begin, row_end) */
+    J.na = row_end - row_begin;
+    J.oa = oa + row_begin;
+    J.ta = ta; J.va = va;
+    J.nb = pairwise ? na : nb;
+    J.ob = pairwise ? oa : ob;
+    J.tb = pairwise ? ta : tb;
+    J.vb = pairwise ? va : vb;
+    J.metric = metric; J.p = p; J.apply_root = apply_root;
+    J.symmetric = pairwise && row_begin == 0 && row_end == na;
+    J.out = out;
+    J.next_row = 0;
+    pthread_mutex_init(&J.lock, NULL);
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads == 1) {
+        orc_worker(&J);
+    } else {
+        pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
+        for (int i = 0; i < nthreads; ++i) pthread_create(&th[i], NULL, orc_worker, &J);
+        for (int i = 0; i < nthreads; ++i) pthread_join(th[i], NULL);
+        free(th);
+    }
+    pthread_mutex_destroy(&J.lock);
+    (void)J;
+    /* row_begin > 0 reuses the same loop: indices of oa are shifted above, and
+     * for the pairwise case the columns still run over all of A. */
+}
+
+/* Alg. 3 (segment iteration) for the integral of f^2 over [0, inf). */
+double orc_segment_sq(const double* t, const double* v, int64_t n)
+{
+    double I = 0.0;
+    for (int64_t k = 0; k + 1 < n; ++k) I += v[k] * v[k] * (t[k + 1] - t[k]);
+    if (v[n - 1] != 0.0) I += v[n - 1] * v[n - 1] * INFINITY;
+    return I;
+}
+
+/* ---- adjoint ---- */
+typedef struct {
+    int metric; double p; double w;
+    double *gvf, *gtf, *gvg, *gtg;   /* gradient slices of f and g */
+    const double *vf_arr, *vg_arr;
+} orc_grad_ctx;
+
+/*
+ * d/dv of a rectangle [l, r) with values (a, b): w * dh/da * (r - l) for the
+ * f side and w * dh/db * (r - l) = w * dh/da(b, a) * (r - l) for the g side
+ * (h is symmetric).  When the scanline moves f past its breakpoint t_{k+1}
+ * (the end of this rectangle), d/dt_{k+1} gains w * (h(v_k, b) - h(v_{k+1}, b))
+ * with b the value of g just before the breakpoint; likewise for g.
+ */
+static void orc_emit_grad(void* ctx, double l, double r, double a, double b,
+                          int64_t kf, int64_t kg, int mf, int mg)
+{
+    orc_grad_ctx* C = (orc_grad_ctx*)ctx;
+    double da = orc_dh_da(C->metric, C->p, a, b);
+    double db = orc_dh_da(C->metric, C->p, b, a);
+    if (isinf(r)) {
+        if (da != 0.0) C->gvf[kf] += C->w * da * INFINITY;
+        if (db != 0.0) C->gvg[kg] += C->w * db * INFINITY;
+        return;
+    }
+    C->gvf[kf] += C->w * da * (r - l);
+    C->gvg[kg] += C->w * db * (r - l);
+    if (mf) {
+        double a_new = C->vf_arr[kf + 1];
+        C->gtf[kf + 1] += C->w * (orc_h(C->metric, C->p, a, b) -
+                                  orc_h(C->metric, C->p, a_new, b));
+    }
+    if (mg) {
+        double b_new = C->vg_arr[kg + 1];
+        C->gtg[kg + 1] += C->w * (orc_h(C->metric, C->p, b, a) -
+                                  orc_h(C->metric, C->p, b_new, a));
+    }
+}
+
+/*
+ * Gradient of L = sum_{i,j} G_ij F_ij (G is n x n row-major, F the pairwise
+ * matrix of `metric`) with respect to values[nnz] and times[nnz].  Pairs with
+ * i != j are walked once with weight (G_ij + G_ji) r'(I_ij); a pair whose
+ * integral is 0 while r' is unbounded there contributes 0.  The Gram diagonal
+ * F_ii = int f_i^2 is differentiated by segment iteration (both arguments of
+ * h move together); distance diagonals are identically 0.
+ */
+void orc_backward(int64_t n, const int64_t* off, const double* t, const double* v,
+                  int metric, double p, int apply_root, const double* G,
+                  double* grad_v, double* grad_t)
+{
+    int64_t nnz = off[n];
+    memset(grad_v, 0, sizeof(double) * (size_t)nnz);
+    memset(grad_t, 0, sizeof(double) * (size_t)nnz);
+    for (int64_t i = 0; i < n; ++i) {
+        const double* ti = t + off[i];
+        const double* vi = v + off[i];
+        int64_t ni = off[i + 1] - off[i];
+        for (int64_t j = i + 1; j < n; ++j) {
+            const double* tj = t + off[j];
+            const double* vj = v + off[j];
+            int64_t nj = off[j + 1] - off[j];
+            double gsum = G[i * n + j] + G[j * n + i];
+            double w = gsum;
+            if (apply_root && metric != ORC_GRAM && orc_exponent(metric, p) != 1.0) {
+                double I = orc_integral(ti, vi, ni, tj, vj, nj, metric, p);
+                if (I == 0.0) continue;
+                w = gsum * orc_droot(metric, p, apply_root, I);
+            }
+            orc_grad_ctx C = { metric, p, w, grad_v + off[i], grad_t + off[i],
+                               grad_v + off[j], grad_t + off[j], vi, vj };
+            orc_walk(ti, vi, ni, tj, vj, nj, orc_emit_grad, &C);
+        }
+        if (metric == ORC_GRAM) {
+            double w = G[i * n + i];
+            double* gv = grad_v + off[i];
+            double* gt = grad_t + off[i];
+            for (int64_t k = 0; k < ni; ++k) {
+                double len = (k + 1 < ni) ? (ti[k + 1] - ti[k]) : INFINITY;
+                if (isinf(len)) {
+                    if (vi[k] != 0.0) gv[k] += w * 2.0 * vi[k] * INFINITY;
+                } else {
+                    gv[k] += w * 2.0 * vi[k] * len;
+                }
+                if (k >= 1) gt[k] += w * (vi[k - 1] * vi[k - 1] - vi[k] * vi[k]);
+            }
+        }
+    }
+}
