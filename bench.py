@@ -1,0 +1,382 @@
+"""Benchmark of the pairwise PCF integral-matrix path on GB300.
+
+Default workload: N = 20,000 stable-rank-like PCFs (n ~ U{50..500}, Exp(0.1)
+gaps, non-increasing integer values 200 -> 0), L1 distance + L2 distance + L2
+Gram matrices in one fused walk per pair, float32-compensated walk (headline)
+and the float64 walk side by side; outputs are full N x N float32 matrices.
+
+One step = the whole hot path on device-resident input: validate + length
+sort + pack (pcf_prepare) and the persistent tile walk (pcf_pairwise with
+PCF_PAIRWISE_PREPARED).  L2 is flushed (256 MiB write) before every timed
+step, outside the per-step CUDA-event brackets.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle
+(threaded float64 walk) on a bounded row sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2404_07183_gb300 import synth  # noqa: E402
+
+METRICS = ["l1", "l2", "gram"]
+# Algorithmic operations per merge step (frozen tally, see the design notes):
+# common part 5 (compare, select rectangle end, dt, fetch, advance) + d = a-b 1
+# L1 |d|*dt fma 1, L2 d*d + fma 2, Gram a*b + fma 2; compensated: the term is
+# a separate multiply and each accumulate is a 7-op TwoSum with compensation.
+TALLY = {"f32c": 5 + 1 + (1 + 7) + (2 + 7) + (2 + 7), "f32": 5 + 1 + 1 + 2 + 2,
+         "f64": 5 + 1 + 1 + 2 + 2}
+FP64_OPS_PER_STEP = 1 + 1 + 1 + 2 + 2   # dt, d, L1 fma, L2 mul+fma, Gram mul+fma
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def exact_walk_steps(s):
+    """sum over pairs i < j of |T_i u T_j| plus sum_i |T_i| (Gram diagonal):
+    |T_i u T_j| = n_i + n_j - |T_i n T_j|; t = 0 is shared by every pair and a
+    positive time shared by c PCFs is shared by c(c-1)/2 pairs."""
+    N, nnz = s.n, s.nnz
+    t = np.asarray(s.times, dtype=np.float64)
+    pos = t[t > 0]
+    _, counts = np.unique(pos, return_counts=True)
+    shared = int(np.sum(counts * (counts - 1) // 2))
+    pairs = (N - 1) * nnz - N * (N - 1) // 2 - shared
+    return int(pairs), int(nnz)
+
+
+def workload(rank=0):
+    s = synth.stable_rank(seed=1002 + rank)
+    return s
+
+
+def start_clock_sampler(path):
+    try:
+        fh = open(path, "w")
+        p = subprocess.Popen(
+            ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,"
+             "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap", "--format=csv,noheader,nounits", "-lms", "200"],
+            stdout=fh, stderr=subprocess.DEVNULL)
+        return p, fh
+    except Exception:
+        return None, None
+
+
+def stop_clock_sampler(p, fh, path, gpu_index):
+    if p is None:
+        return None
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    fh.close()
+    sm, mx, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        f = [x.strip() for x in line.split(",")]
+        if len(f) < 9 or f[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(f[1]))
+            mx = max(mx, float(f[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return None
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+def pipe_peaks():
+    """FP64 and FP32 FMA lane rates per SM per clock (own microbenchmark)."""
+    from paper_2404_07183_gb300 import build
+    lib = ctypes.CDLL(build.build_peaks())
+    lib.pcf_peak_fma.restype = ctypes.c_int
+    lib.pcf_peak_fma.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    out = {}
+    for name, f64, iters in (("fp64", 1, 2000), ("fp32", 0, 50000)):
+        clk, rate = ctypes.c_double(), ctypes.c_double()
+        rc = lib.pcf_peak_fma(f64, sms, iters, ctypes.byref(clk), ctypes.byref(rate))
+        out[name] = {"lane_ops_per_clk_per_sm": clk.value, "lane_ops_per_s": rate.value, "rc": rc}
+    out["sms"] = sms
+    return out
+
+
+# --------------------------------------------------------------------------
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    s = workload()
+    cores = len(os.sched_getaffinity(0))
+    rows_per_step = args.ref_rows
+    steps_rows = []
+    times = []
+    total_pairs = 0
+    rng = np.random.default_rng(0)
+    for k in range(args.warmup + args.steps):
+        r0 = int(rng.integers(0, s.n - rows_per_step))
+        t0 = time.perf_counter()
+        for m in METRICS:
+            oracle.matrix(s, metric=m, rows=(r0, r0 + rows_per_step), nthreads=cores)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            steps_rows.append(r0)
+            total_pairs += 3 * rows_per_step * s.n
+    elapsed = sum(times)
+    value = total_pairs / elapsed
+    line = {
+        "impl": "reference", "metric": "pair-integrals/s (L1+L2+Gram) and merge-steps/s",
+        "value": value, "unit": "pair-integrals/s", "n_gpus": 0, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
+        "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "stable_rank N=20000 n~U{50..500} L1+L2+Gram",
+                   "sample": f"{rows_per_step} consecutive rows x 20000 columns per step"},
+        "cpu_baseline": {"value": value, "unit": "pair-integrals/s", "cores": cores,
+                         "kind": "oracle",
+                         "sample": f"{rows_per_step} rows x {s.n} cols x 3 metrics per step"},
+        "e2e": {"value": value, "unit": "pair-integrals/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(s, seconds_target=12.0):
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    rows = 8
+    t0 = time.perf_counter()
+    oracle.matrix(s, metric="l1", rows=(0, rows), nthreads=cores)
+    dt = time.perf_counter() - t0
+    rows = int(max(8, min(s.n, rows * (seconds_target / 3.0) / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    for m in METRICS:
+        oracle.matrix(s, metric=m, rows=(1000, 1000 + rows), nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": 3 * rows * s.n / dt, "unit": "pair-integrals/s", "cores": cores,
+            "kind": "oracle", "seconds": dt,
+            "sample": f"rows 1000..{1000 + rows} x all {s.n} columns, L1+L2+Gram, "
+                      "float64 oracle walk, one thread per core"}
+
+
+def run_ours(args):
+    import torch
+    import paper_2404_07183_gb300 as P
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    P.build.build()
+
+    s = workload(rank)
+    N = s.n
+    walk_steps, diag_steps = exact_walk_steps(s)
+    pairs = 2 * (N * (N - 1) // 2) + N * (N + 1) // 2      # distances i<j, Gram i<=j
+    x = P.PcfTensors.from_numpy(s, f"cuda:{local}")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+    stream = torch.cuda.current_stream()
+
+    def make_outs():
+        return [torch.empty((N, N), dtype=torch.float32, device=f"cuda:{local}") for _ in METRICS]
+
+    results = {}
+    for prec in (args.precision, "f64") if not args.no_fp64 else (args.precision,):
+        outs = make_outs()
+        ws = torch.empty(P.pcf_workspace_size(x, None, prec), dtype=torch.uint8,
+                         device=f"cuda:{local}")
+
+        def step():
+            P.pcf_prepare(x, prec, workspace=ws)
+            e_mid = torch.cuda.Event(enable_timing=True)
+            e_mid.record(stream)
+            P.pcf_pairwise(x, METRICS, precision=prec, out=outs, workspace=ws, prepared=True,
+                           check=False)
+            return e_mid
+
+        steps = args.steps if prec == args.precision else max(1, min(args.steps, 2))
+        warm = args.warmup
+        for _ in range(warm):
+            step()
+        P.pcf_check(ws)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        sampler, sfh = (None, None)
+        clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_{prec}_r{rank}.csv")
+        if prec == args.precision:
+            os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+            sampler, sfh = start_clock_sampler(clk_path)
+        t_wall = time.perf_counter()
+        evs = []
+        for _ in range(steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            e1 = step()
+            e2.record(stream)
+            evs.append((e0, e1, e2))
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+        clocks = stop_clock_sampler(sampler, sfh, clk_path, local) if sampler else None
+        P.pcf_check(ws)
+        step_ms = [a.elapsed_time(c) for a, b, c in evs]
+        walk_ms = [b.elapsed_time(c) for a, b, c in evs]
+        tot = sum(step_ms)
+        if world > 1:
+            t = torch.tensor([tot], device=f"cuda:{local}", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            tot = float(t.item())
+        results[prec] = {"ms_per_step": tot / steps, "walk_ms": float(np.mean(walk_ms)),
+                         "prepare_ms": float(np.mean([a.elapsed_time(b) for a, b, c in evs])),
+                         "steps": steps, "wall_s": t_wall, "clocks": clocks}
+        del outs, ws
+
+    # end-to-end through the public API with host buffers (pinned), every step:
+    # H2D of the CSR, the whole path, D2H of the three matrices
+    prec = args.precision
+    host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+               for a in (s.offsets, s.times, s.values)]
+    host_out = [torch.empty((N, N), dtype=torch.float32).pin_memory() for _ in METRICS]
+    dev_in = [torch.empty_like(h, device=f"cuda:{local}") for h in host_in]
+    outs = make_outs()
+    ws = torch.empty(P.pcf_workspace_size(x, None, prec), dtype=torch.uint8, device=f"cuda:{local}")
+    h2d = sum(h.numel() * h.element_size() for h in host_in)
+    d2h = sum(h.numel() * h.element_size() for h in host_out)
+
+    def e2e_step():
+        for d, h in zip(dev_in, host_in):
+            d.copy_(h, non_blocking=True)
+        xd = P.PcfTensors(*dev_in)
+        P.pcf_pairwise(xd, METRICS, precision=prec, out=outs, workspace=ws, check=False)
+        for h, o in zip(host_out, outs):
+            h.copy_(o, non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    P.pcf_check(ws)
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    peaks = measured_peaks()
+    pp = pipe_peaks()
+    sms = pp["sms"]
+    fmax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    head = results[prec]
+    value = world * pairs / (head["ms_per_step"] * 1e-3)
+    walk_rate = walk_steps / (head["walk_ms"] * 1e-3)
+    issue_peak = sms * 128 * fmax / TALLY[prec]
+    line = {
+        "metric": "pair-integrals/s and merge-steps/s at 1 GB300 (FP32-comp vs FP64), % issue roofline",
+        "value": value, "unit": "pair-integrals/s", "n_gpus": world, "steps": head["steps"],
+        "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (compensated)",
+        "data": "synthetic",
+        "config": {"workload": "stable_rank N=20000 n~U{50..500} Exp(0.1) gaps, L1+L2+Gram fused",
+                   "N": N, "nnz": s.nnz, "metrics": METRICS, "precision": prec,
+                   "layout": "full N x N", "out_dtype": "f32",
+                   "pair_integrals_per_step": pairs, "merge_steps_per_step": walk_steps + diag_steps,
+                   "l2": "flushed by a 256 MiB write before each timed step (outside the timing)",
+                   "parallelism": f"{world} independent replicas (one per GPU)"},
+        "merge_steps_per_s": world * (walk_steps + diag_steps) / (head["ms_per_step"] * 1e-3),
+        "walk": {"ms": head["walk_ms"], "prepare_ms": head["prepare_ms"],
+                 "merge_steps_per_s": walk_rate},
+        "roofline": {"bound": "alu", "achieved": walk_rate, "peak": issue_peak,
+                     "unit": "merge-steps/s", "frac": walk_rate / issue_peak, "traffic": None,
+                     "peak_basis": f"{sms} SMs x 128 lanes x {fmax/1e6:.0f} MHz / {TALLY[prec]} "
+                                   "ops per merge step (fused L1+L2+Gram tally)"},
+        "gpu_launches": head["steps"] * (4 + 2),
+        "e2e": {"value": world * pairs / e2e_s, "unit": "pair-integrals/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_s * 1e3},
+        "pipe_peaks": pp,
+        "clocks": head["clocks"],
+    }
+    if "f64" in results:
+        f = results["f64"]
+        r64 = pp["fp64"]["lane_ops_per_clk_per_sm"]
+        fp64_peak = sms * r64 * fmax / FP64_OPS_PER_STEP
+        wr = walk_steps / (f["walk_ms"] * 1e-3)
+        line["fp64"] = {"value": pairs / (f["ms_per_step"] * 1e-3), "unit": "pair-integrals/s",
+                        "ms_per_step": f["ms_per_step"], "walk_ms": f["walk_ms"],
+                        "merge_steps_per_s": wr,
+                        "roofline": {"bound": "fp64 pipe", "achieved": wr, "peak": fp64_peak,
+                                     "unit": "merge-steps/s", "frac": wr / fp64_peak,
+                                     "peak_basis": f"{sms} SMs x {r64:.2f} FP64 lane-ops/clk x "
+                                                   f"{fmax/1e6:.0f} MHz / {FP64_OPS_PER_STEP} FP64 "
+                                                   "ops per step"}}
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(s)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="f32c", choices=["f32c", "f32", "f64"])
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ref-rows", type=int, default=48)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,214 @@
+/*
+ * pcf.h -- C ABI of the GB300 (sm_103a) PCF integral-matrix library.
+ *
+ * A piecewise constant function (PCF) f on [0, inf) is given by breakpoints
+ * 0 = t_0 < t_1 < ... < t_{n-1} and values v_0..v_{n-1}; f = v_k on
+ * [t_k, t_{k+1}) and f = v_{n-1} on [t_{n-1}, inf) (Sec. 2, PCF definition
+ * and its n x 2 matrix storage).  A collection of N PCFs is passed in CSR form
+ * (`pcf_csr`).
+ *
+ * For two PCFs f, g the library computes combination integrals
+ *     F(f, g) = r( int_0^inf h(f(t), g(t)) dt )                 (Sec. 2.2)
+ * with h(a,b) = |a-b|^p, r(x) = x^(1/p) for the L_p distance (p >= 1) and
+ * h(a,b) = a*b, r = id for the L2 inner product, by one linear-time merge walk
+ * over the two breakpoint lists per pair (rectangle iteration, Sec. 3 Alg. 1;
+ * accumulation, Alg. 2; Eq. simpleint), and assembles them into matrices
+ * (Sec. 3.1, "integrated combination matrix").
+ *
+ * Conventions for every entry point:
+ *  - All array pointers are DEVICE pointers owned by the caller.  The library
+ *    allocates nothing and keeps no state between calls; scratch memory is the
+ *    caller's `workspace` (size from pcf_workspace_size, 256-byte aligned).
+ *  - Work is enqueued on `stream` and returns without synchronizing.  The
+ *    return value reports argument errors found on the host.  Problems that
+ *    can only be seen in device data (an invalid PCF) are recorded in the
+ *    workspace; pcf_check() synchronizes the stream and returns them.  When
+ *    the device check fails, the compute kernels of that call skip all work
+ *    and the outputs are left unspecified.
+ *  - A PCF whose final value differs from that of its partner integrates to
+ *    +-inf for that pair (the last rectangle [t_last, inf) adds h * inf when
+ *    h != 0 and nothing when h = 0).
+ *  - Calls that share a workspace must be ordered on one stream.
+ */
+#ifndef PCF_H
+#define PCF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* The CUDA runtime's stream handle type (identical declaration). */
+typedef struct CUstream_st* cudaStream_t;
+
+/* Return codes. */
+enum pcf_status {
+    PCF_OK = 0,
+    PCF_EINVAL = 1,    /* bad argument, or invalid PCF data found on the device */
+    PCF_ENOWS = 2,     /* workspace missing, misaligned or too small */
+    PCF_ECUDA = 3,     /* a CUDA runtime call failed */
+    PCF_ETIMEOUT = 4,  /* a bounded device wait gave up */
+    PCF_EUNSUPPORTED = 5 /* valid request this build does not implement */
+};
+
+/* Element type of times/values/outputs. */
+enum pcf_dtype { PCF_F32 = 0, PCF_F64 = 1 };
+
+/* Which combination integral (Sec. 2.2). */
+enum pcf_metric {
+    PCF_L1 = 0,    /* h = |a-b|,    r = id (root of p = 1)                      */
+    PCF_L2 = 1,    /* h = (a-b)^2,  r = sqrt if apply_root                      */
+    PCF_LP = 2,    /* h = |a-b|^p,  r = x^(1/p) if apply_root; p >= 1           */
+    PCF_GRAM = 3   /* h = a*b,      r = id (L2 inner product / Gram matrix)     */
+};
+
+/* Arithmetic of the walk.  Breakpoint comparisons are exact in the walk type. */
+enum pcf_precision {
+    PCF_PREC_F64 = 0,      /* float64 walk and accumulation                     */
+    PCF_PREC_F32_COMP = 1, /* float32 walk, every rectangle's term added with an
+                              error-free TwoSum into a (sum, compensation) pair */
+    PCF_PREC_F32 = 2       /* float32 walk, plain float32 fused multiply-add    */
+};
+/* float64 input walked in a float32 precision is rounded to nearest float32
+ * when packed (times keep their order; times that round together become one
+ * breakpoint of both PCFs).  The p-th root is always taken in float64. */
+
+/* Output layout of the pairwise matrix. */
+enum pcf_layout {
+    PCF_OUT_FULL = 0,          /* N x N row-major, both triangles written      */
+    PCF_OUT_UPPER_PACKED = 1   /* row-major upper triangle with the diagonal:
+                                  (i, j), i <= j, at i*N - i*(i-1)/2 + (j - i) */
+};
+
+/* Workspace purpose for pcf_workspace_size. */
+enum pcf_ws_purpose { PCF_WS_FORWARD = 0, PCF_WS_BACKWARD = 1 };
+
+/* pcf_pairwise flags. */
+enum pcf_pairwise_flags {
+    PCF_PAIRWISE_PREPARED = 1  /* skip validating/packing x: the workspace holds x
+                                  as packed by pcf_prepare (or by a previous
+                                  pcf_pairwise) with the same x and precision */
+};
+
+/* pcf_cross flags. */
+enum pcf_cross_flags {
+    PCF_CROSS_REUSE_B = 1  /* skip validating/packing B: the workspace still holds
+                              B packed by the previous pcf_cross call made with
+                              the same B, precision and workspace */
+};
+
+/* A collection of N PCFs in CSR form (device arrays, read only).
+ *   offsets[N+1] (int64): PCF i owns entries [offsets[i], offsets[i+1]);
+ *                         offsets[0] = 0, offsets[N] = nnz, every PCF n_i >= 1.
+ *   times[nnz], values[nnz]: dtype elements; times[offsets[i]] = 0 (or -0),
+ *                         strictly increasing within a PCF; all finite. */
+typedef struct pcf_csr {
+    int64_t n;
+    int64_t nnz;
+    const int64_t* offsets;
+    const void* times;
+    const void* values;
+    int32_t dtype;      /* enum pcf_dtype */
+    int32_t reserved;
+} pcf_csr;
+
+/* One requested matrix.  Several may be computed in one walk (fused). */
+typedef struct pcf_integral {
+    int32_t metric;      /* enum pcf_metric */
+    int32_t apply_root;  /* distances: 1 -> F = I^(1/p) (p = 1, 2, p); 0 -> F = I */
+    double p;            /* exponent for PCF_LP (>= 1); ignored otherwise */
+    void* out;           /* device output, layout and dtype per call */
+} pcf_integral;
+
+/* Maximum number of pcf_integral entries per call. */
+#define PCF_MAX_INTEGRALS 4
+
+/*
+ * Bytes of workspace needed for pairwise (y == NULL) or cross (y != NULL) work
+ * on these collections at `precision`, for `purpose`.  Host-only; reads only
+ * x->n, x->nnz (and y's).  Returns PCF_EINVAL for bad sizes.
+ */
+int pcf_workspace_size(const pcf_csr* x, const pcf_csr* y, int precision,
+                       int purpose, size_t* bytes);
+
+/*
+ * Validate, sort by length and pack collection x into the workspace (the
+ * first stage of pcf_pairwise), so that several pcf_pairwise calls with
+ * PCF_PAIRWISE_PREPARED can reuse it.  Same workspace size as pcf_pairwise.
+ */
+int pcf_prepare(const pcf_csr* x, int precision, void* workspace, size_t workspace_bytes,
+                cudaStream_t stream);
+
+/*
+ * Pairwise integrated-combination matrices of one collection (Sec. 3.1).
+ * Computes nF <= PCF_MAX_INTEGRALS matrices of x in one pass: validation and
+ * packing of x (sorted by length), then one merge walk per unordered pair
+ * i <= j whose terms feed every requested integral.
+ *   F[k].out: N*N (FULL) or N*(N+1)/2 (UPPER_PACKED) elements of out_dtype.
+ *   Distance diagonals are exactly 0; Gram diagonals are ||f_i||^2.
+ *   flags: 0 or PCF_PAIRWISE_PREPARED.
+ * Returns PCF_OK, PCF_EINVAL (bad enum/argument, p < 1), PCF_ENOWS, PCF_ECUDA.
+ */
+int pcf_pairwise(const pcf_csr* x, const pcf_integral* F, int nF, int precision,
+                 int layout, int out_dtype, int flags, void* workspace,
+                 size_t workspace_bytes, cudaStream_t stream);
+
+/*
+ * Cross matrices between rows [row_begin, row_end) of collection a and all of
+ * collection b (the pairwise matrix of Sec. 3.1 taken between two sets).
+ * Output k is a (row_end - row_begin) x b->n row-major block with leading
+ * dimension ld_out (>= b->n) elements: out[(i - row_begin) * ld_out + j].
+ * Block streaming = repeated calls over consecutive row ranges (use
+ * PCF_CROSS_REUSE_B after the first).
+ */
+int pcf_cross(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row_end,
+              const pcf_integral* F, int nF, int precision, int64_t ld_out,
+              int out_dtype, int flags, void* workspace, size_t workspace_bytes,
+              cudaStream_t stream);
+
+/*
+ * Gradient of L = sum_{i,j} G_ij F_ij, F the FULL pairwise matrix of `metric`
+ * (p, apply_root as in pcf_pairwise), with respect to x->values and x->times.
+ * Not part of the paper (Sec. 3 only remarks that derivatives of a
+ * parametrised integrand are available); derived by differentiating each
+ * rectangle term of Eq. simpleint.  The walk is recomputed in float64; no
+ * forward intermediates are stored.
+ *   grad_out: N x N row-major G, dtype grad_dtype.
+ *   fwd_out:  N x N row-major F from pcf_pairwise (dtype grad_dtype); needed
+ *             only when apply_root = 1 and the exponent is not 1 (the chain
+ *             factor r'(I) is taken from F), else may be NULL.
+ *   grad_values, grad_times: nnz elements of x->dtype (overwritten).
+ * Conventions: d/dt_0 = 0 (t_0 = 0 is fixed).  At a breakpoint both PCFs
+ * share, each side's time derivative uses the other PCF's value just before
+ * the breakpoint (left derivative).  |a-b| has slope 0 at a = b.  A pair with
+ * F_ij = 0 contributes 0 when r'(0) is unbounded.
+ * Workspace: pcf_workspace_size(x, NULL, PCF_PREC_F64, PCF_WS_BACKWARD).
+ */
+int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root,
+                          const void* fwd_out, const void* grad_out, int grad_dtype,
+                          void* grad_values, void* grad_times,
+                          void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/*
+ * Synchronizes `stream` and returns the device-side status recorded in the
+ * workspace by the last call: PCF_OK, or PCF_EINVAL with *detail set to the
+ * reason code (1 offsets, 2 t_0 != 0, 3 times not increasing, 4 time not
+ * finite, 5 value not finite, 6 time or value outside float32 range for a
+ * float32 walk) and *index to the smallest offending entry (PCF index for
+ * reason 1, element index otherwise).  detail/index may be NULL.
+ */
+int pcf_check(const void* workspace, cudaStream_t stream, int* detail, int64_t* index);
+
+/* Static text for a status code. */
+const char* pcf_status_string(int status);
+
+/* Library build identification (static string). */
+const char* pcf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCF_H */

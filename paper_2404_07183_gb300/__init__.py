@@ -1,1 +1,11 @@
-"""GB300-native PCF integral matrices (placeholder; filled in below)."""
+"""GB300-native (sm_103a) PCF integral matrices.
+
+All-pairs and cross-set L_p distance and L2 Gram matrices of piecewise
+constant functions, one merge walk per pair, in hand-written CUDA behind the
+C ABI of ``include/pcf.h``.  See ``api`` for the Python binding and
+``synth`` for seeded synthetic inputs.
+"""
+from .api import (PairwiseFn, PcfError, PcfTensors, l2_kernel, parse_metric,  # noqa: F401
+                  pcf_check, pcf_cross, pcf_pairwise, pcf_pairwise_backward, pcf_prepare,
+                  pcf_workspace_size, pdist)
+from . import abi, build  # noqa: F401

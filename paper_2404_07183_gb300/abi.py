@@ -1,0 +1,97 @@
+"""ctypes view of the C ABI in ``include/pcf.h`` (argument marshalling only).
+
+Loading is lazy; there is no fallback: if the CUDA library has not been built
+(``paper_2404_07183_gb300.build``) every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+PCF_OK, PCF_EINVAL, PCF_ENOWS, PCF_ECUDA, PCF_ETIMEOUT, PCF_EUNSUPPORTED = range(6)
+PCF_F32, PCF_F64 = 0, 1
+PCF_L1, PCF_L2, PCF_LP, PCF_GRAM = 0, 1, 2, 3
+PCF_PREC_F64, PCF_PREC_F32_COMP, PCF_PREC_F32 = 0, 1, 2
+PCF_OUT_FULL, PCF_OUT_UPPER_PACKED = 0, 1
+PCF_WS_FORWARD, PCF_WS_BACKWARD = 0, 1
+PCF_CROSS_REUSE_B = 1
+PCF_PAIRWISE_PREPARED = 1
+PCF_MAX_INTEGRALS = 4
+
+ERR_DETAIL = {
+    1: "offsets not increasing / out of range",
+    2: "first breakpoint time is not 0",
+    3: "breakpoint times not strictly increasing",
+    4: "breakpoint time not finite",
+    5: "value not finite",
+    6: "time or value outside float32 range for a float32 walk",
+    7: "more coincident float32 breakpoints than one window holds",
+}
+
+SYMBOLS = ("pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross", "pcf_pairwise_backward",
+           "pcf_check", "pcf_status_string", "pcf_version")
+
+
+class PcfCsr(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("nnz", ctypes.c_int64),
+                ("offsets", ctypes.c_void_p), ("times", ctypes.c_void_p),
+                ("values", ctypes.c_void_p), ("dtype", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class PcfIntegral(ctypes.Structure):
+    _fields_ = [("metric", ctypes.c_int32), ("apply_root", ctypes.c_int32),
+                ("p", ctypes.c_double), ("out", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load (and optionally build) the CUDA library; raises if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(
+                    f"CUDA library {path} is not built; run "
+                    "`python -m paper_2404_07183_gb300.build` (no CPU fallback exists)")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        P, I, I64, D, SZ = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64,
+                            ctypes.c_double, ctypes.c_size_t)
+        CSR = ctypes.POINTER(PcfCsr)
+        INT = ctypes.POINTER(PcfIntegral)
+        lib.pcf_workspace_size.restype = I
+        lib.pcf_workspace_size.argtypes = [CSR, CSR, I, I, ctypes.POINTER(SZ)]
+        lib.pcf_pairwise.restype = I
+        lib.pcf_pairwise.argtypes = [CSR, INT, I, I, I, I, I, P, SZ, P]
+        lib.pcf_prepare.restype = I
+        lib.pcf_prepare.argtypes = [CSR, I, P, SZ, P]
+        lib.pcf_cross.restype = I
+        lib.pcf_cross.argtypes = [CSR, CSR, I64, I64, INT, I, I, I64, I, I, P, SZ, P]
+        lib.pcf_pairwise_backward.restype = I
+        lib.pcf_pairwise_backward.argtypes = [CSR, I, D, I, P, P, I, P, P, P, SZ, P]
+        lib.pcf_check.restype = I
+        lib.pcf_check.argtypes = [P, P, ctypes.POINTER(I), ctypes.POINTER(I64)]
+        lib.pcf_status_string.restype = ctypes.c_char_p
+        lib.pcf_status_string.argtypes = [I]
+        lib.pcf_version.restype = ctypes.c_char_p
+        lib.pcf_version.argtypes = []
+        _lib = lib
+        return lib
+
+
+def status_string(code: int) -> str:
+    return load().pcf_status_string(int(code)).decode()

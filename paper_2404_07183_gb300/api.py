@@ -1,0 +1,287 @@
+"""Python binding of the C ABI (same names), on PyTorch device tensors.
+
+PyTorch supplies device memory and streams only; every step of the
+computation runs in the library's CUDA kernels.  Metric requests are given as
+strings or tuples:
+
+    "l1" | "l2" | "gram" | ("lp", p)       -> root applied for distances
+    ("l2", False) / ("lp", p, False)       -> raw integral int |f-g|^p
+
+Functions raise ``PcfError`` on any non-OK status.  With ``check=True`` (the
+default) a call synchronizes its stream and also raises for invalid PCF data
+found on the device.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import abi
+
+__all__ = ["PcfError", "PcfTensors", "pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross",
+           "pcf_pairwise_backward", "pcf_check", "PairwiseFn", "pdist", "l2_kernel",
+           "parse_metric", "PRECISIONS"]
+
+PRECISIONS = {"f64": abi.PCF_PREC_F64, "f32c": abi.PCF_PREC_F32_COMP, "f32": abi.PCF_PREC_F32}
+_METRICS = {"l1": abi.PCF_L1, "l2": abi.PCF_L2, "lp": abi.PCF_LP, "gram": abi.PCF_GRAM}
+
+
+class PcfError(RuntimeError):
+    def __init__(self, code, what, detail=None, index=None):
+        msg = f"{what}: {abi.status_string(code)} (status {code})"
+        if detail:
+            msg += f"; {abi.ERR_DETAIL.get(detail, detail)} at index {index}"
+        super().__init__(msg)
+        self.code, self.detail, self.index = code, detail, index
+
+
+@dataclass
+class PcfTensors:
+    """A CSR collection of PCFs on one CUDA device."""
+    offsets: torch.Tensor   # int64 [N+1]
+    times: torch.Tensor     # float32/float64 [nnz]
+    values: torch.Tensor    # same dtype as times
+
+    @property
+    def n(self) -> int:
+        return int(self.offsets.numel() - 1)
+
+    @property
+    def nnz(self) -> int:
+        return int(self.times.numel())
+
+    @staticmethod
+    def from_numpy(s, device="cuda", dtype=None, pin=False):
+        """Copy a host CSR set (anything with offsets/times/values) to `device`."""
+        t, v = np.asarray(s.times), np.asarray(s.values)
+        if dtype is not None:
+            t, v = t.astype(dtype), v.astype(dtype)
+        ts = [torch.from_numpy(np.ascontiguousarray(a)) for a in (s.offsets, t, v)]
+        if pin:
+            ts = [a.pin_memory() for a in ts]
+        return PcfTensors(*(a.to(device, non_blocking=pin) for a in ts))
+
+    def csr(self) -> abi.PcfCsr:
+        for a in (self.offsets, self.times, self.values):
+            if not a.is_cuda or not a.is_contiguous():
+                raise ValueError("PcfTensors must be contiguous CUDA tensors")
+        if self.offsets.dtype != torch.int64:
+            raise ValueError("offsets must be int64")
+        if self.times.dtype != self.values.dtype or self.times.dtype not in (torch.float32, torch.float64):
+            raise ValueError("times/values must share float32 or float64")
+        c = abi.PcfCsr()
+        c.n, c.nnz = self.n, self.nnz
+        c.offsets, c.times, c.values = (self.offsets.data_ptr(), self.times.data_ptr(),
+                                        self.values.data_ptr())
+        c.dtype = abi.PCF_F64 if self.times.dtype == torch.float64 else abi.PCF_F32
+        return c
+
+
+def parse_metric(m):
+    """(metric_code, p, apply_root) from a request spec."""
+    if isinstance(m, str):
+        m = (m,)
+    name = m[0].lower()
+    if name not in _METRICS:
+        raise ValueError(f"unknown metric {m!r}")
+    code = _METRICS[name]
+    if code == abi.PCF_LP:
+        p = float(m[1])
+        root = bool(m[2]) if len(m) > 2 else True
+    else:
+        p = {abi.PCF_L1: 1.0, abi.PCF_L2: 2.0, abi.PCF_GRAM: 1.0}[code]
+        root = bool(m[1]) if len(m) > 1 else True
+    return code, p, root
+
+
+def _stream_handle(stream):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _prec(precision):
+    return PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+
+
+def pcf_workspace_size(x: PcfTensors, y: PcfTensors | None = None, precision="f32c",
+                       purpose="forward") -> int:
+    lib = abi.load()
+    cx = x.csr()
+    cy = y.csr() if y is not None else None
+    out = ctypes.c_size_t(0)
+    rc = lib.pcf_workspace_size(ctypes.byref(cx), ctypes.byref(cy) if cy else None,
+                                _prec(precision),
+                                abi.PCF_WS_BACKWARD if purpose == "backward" else abi.PCF_WS_FORWARD,
+                                ctypes.byref(out))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_workspace_size")
+    return int(out.value)
+
+
+def _workspace(nbytes, device, workspace):
+    if workspace is not None:
+        if workspace.numel() * workspace.element_size() < nbytes:
+            raise ValueError("workspace too small")
+        return workspace
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def pcf_check(workspace: torch.Tensor, stream=None, what="pcf"):
+    """Synchronize and raise if the device recorded invalid input."""
+    lib = abi.load()
+    detail = ctypes.c_int(0)
+    index = ctypes.c_int64(-1)
+    rc = lib.pcf_check(ctypes.c_void_p(workspace.data_ptr()), _stream_handle(stream),
+                       ctypes.byref(detail), ctypes.byref(index))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, what, detail.value, index.value)
+
+
+def _requests(metrics, outs):
+    arr = (abi.PcfIntegral * len(metrics))()
+    for k, (m, o) in enumerate(zip(metrics, outs)):
+        code, p, root = parse_metric(m)
+        arr[k].metric, arr[k].p, arr[k].apply_root = code, p, int(root)
+        arr[k].out = o.data_ptr() if o is not None and o.numel() else None
+    return arr
+
+
+def pcf_prepare(x: PcfTensors, precision="f32c", workspace=None, stream=None):
+    """Validate, sort and pack ``x`` into a workspace (returned) for later
+    ``pcf_pairwise(..., prepared=True, workspace=ws)`` calls."""
+    lib = abi.load()
+    ws = _workspace(pcf_workspace_size(x, None, precision), x.times.device, workspace)
+    cx = x.csr()
+    rc = lib.pcf_prepare(ctypes.byref(cx), _prec(precision), ctypes.c_void_p(ws.data_ptr()),
+                         ws.numel(), _stream_handle(stream))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_prepare")
+    return ws
+
+
+def pcf_pairwise(x: PcfTensors, metrics=("l1",), precision="f32c", layout="full",
+                 out_dtype=torch.float32, out=None, workspace=None, stream=None,
+                 check=True, prepared=False):
+    """Pairwise matrices F(C) (Sec. 3.1) of ``x`` for each requested metric.
+
+    Returns a list of tensors: N x N (layout "full") or N(N+1)/2 ("upper")."""
+    lib = abi.load()
+    if isinstance(metrics, (str, tuple)):
+        metrics = [metrics]
+    metrics = list(metrics)
+    n = x.n
+    lay = abi.PCF_OUT_FULL if layout == "full" else abi.PCF_OUT_UPPER_PACKED
+    shape = (n, n) if lay == abi.PCF_OUT_FULL else (n * (n + 1) // 2,)
+    dev = x.times.device
+    if out is None:
+        out = [torch.empty(shape, dtype=out_dtype, device=dev) for _ in metrics]
+    ws = _workspace(pcf_workspace_size(x, None, precision), dev, workspace)
+    cx = x.csr()
+    req = _requests(metrics, out)
+    od = abi.PCF_F64 if out[0].dtype == torch.float64 else abi.PCF_F32
+    if prepared and workspace is None:
+        raise ValueError("prepared=True needs the workspace returned by pcf_prepare")
+    rc = lib.pcf_pairwise(ctypes.byref(cx), req, len(metrics), _prec(precision), lay, od,
+                          abi.PCF_PAIRWISE_PREPARED if prepared else 0,
+                          ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_pairwise")
+    if check:
+        pcf_check(ws, stream, "pcf_pairwise")
+    return out
+
+
+def pcf_cross(a: PcfTensors, b: PcfTensors, row_begin=0, row_end=None, metrics=("l1",),
+              precision="f32c", out_dtype=torch.float32, out=None, ld_out=None,
+              reuse_b=False, workspace=None, stream=None, check=True):
+    """Rows [row_begin, row_end) of the cross matrices a x b."""
+    lib = abi.load()
+    if isinstance(metrics, (str, tuple)):
+        metrics = [metrics]
+    metrics = list(metrics)
+    row_end = a.n if row_end is None else row_end
+    rows = row_end - row_begin
+    ld = b.n if ld_out is None else ld_out
+    dev = b.times.device
+    if out is None:
+        out = [torch.empty((rows, ld), dtype=out_dtype, device=dev) for _ in metrics]
+    ws = _workspace(pcf_workspace_size(a, b, precision), dev, workspace)
+    ca, cb = a.csr(), b.csr()
+    req = _requests(metrics, out)
+    od = abi.PCF_F64 if out[0].dtype == torch.float64 else abi.PCF_F32
+    rc = lib.pcf_cross(ctypes.byref(ca), ctypes.byref(cb), int(row_begin), int(row_end), req,
+                       len(metrics), _prec(precision), int(ld), od,
+                       abi.PCF_CROSS_REUSE_B if reuse_b else 0,
+                       ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_cross")
+    if check:
+        pcf_check(ws, stream, "pcf_cross")
+    return out
+
+
+def pcf_pairwise_backward(x: PcfTensors, metric, grad_out: torch.Tensor, fwd_out=None,
+                          workspace=None, stream=None, check=True):
+    """(grad_values, grad_times) of sum(grad_out * F) for the FULL matrix F."""
+    lib = abi.load()
+    code, p, root = parse_metric(metric)
+    dev = x.times.device
+    gv = torch.empty_like(x.values)
+    gt = torch.empty_like(x.times)
+    ws = _workspace(pcf_workspace_size(x, None, "f64", "backward"), dev, workspace)
+    g = grad_out.contiguous()
+    if g.dtype not in (torch.float32, torch.float64):
+        g = g.to(torch.float64)
+    f = None
+    if fwd_out is not None:
+        f = fwd_out.contiguous()
+        if f.dtype != g.dtype:
+            raise ValueError("fwd_out and grad_out must share a dtype")
+    cx = x.csr()
+    rc = lib.pcf_pairwise_backward(
+        ctypes.byref(cx), code, p, int(root),
+        ctypes.c_void_p(f.data_ptr()) if f is not None else None,
+        ctypes.c_void_p(g.data_ptr()), abi.PCF_F64 if g.dtype == torch.float64 else abi.PCF_F32,
+        ctypes.c_void_p(gv.data_ptr()), ctypes.c_void_p(gt.data_ptr()),
+        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_pairwise_backward")
+    if check:
+        pcf_check(ws, stream, "pcf_pairwise_backward")
+    return gv, gt
+
+
+class PairwiseFn(torch.autograd.Function):
+    """F = pairwise matrix of one metric, differentiable in values and times.
+
+    The backward pass recomputes the merge walks (nothing but the output F is
+    saved)."""
+
+    @staticmethod
+    def forward(ctx, values, times, offsets, metric="l2", precision="f64"):
+        x = PcfTensors(offsets, times.detach(), values.detach())
+        out_dtype = values.dtype
+        F = pcf_pairwise(x, [metric], precision=precision, out_dtype=out_dtype)[0]
+        ctx.save_for_backward(values, times, offsets, F)
+        ctx.metric = metric
+        return F
+
+    @staticmethod
+    def backward(ctx, grad):
+        values, times, offsets, F = ctx.saved_tensors
+        x = PcfTensors(offsets, times.detach(), values.detach())
+        gv, gt = pcf_pairwise_backward(x, ctx.metric, grad.to(F.dtype), fwd_out=F)
+        return gv, gt, None, None, None
+
+
+def pdist(x: PcfTensors, p=1.0, precision="f64", out_dtype=torch.float64):
+    """L_p distance matrix (the paper's ``pdist``, Sec. 5.2)."""
+    return pcf_pairwise(x, [("lp", p)], precision=precision, out_dtype=out_dtype)[0]
+
+
+def l2_kernel(x: PcfTensors, precision="f64", out_dtype=torch.float64):
+    """L2 inner-product (Gram) matrix (the paper's ``l2_kernel``, Sec. 5.2)."""
+    return pcf_pairwise(x, ["gram"], precision=precision, out_dtype=out_dtype)[0]

@@ -1,0 +1,404 @@
+// api.cu -- the C ABI declared in include/pcf.h.
+//
+// Every entry point checks its host-visible arguments, lays out the caller's
+// workspace, and enqueues on the caller's stream:
+//   init header -> validate + length sort + pack (per collection)
+//   -> persistent tile walk (one launch per fused metric group)
+// or, for the adjoint, the recomputing gradient walk and a scatter back to
+// the input order.  Nothing is allocated and nothing is synchronized.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace pcfgb {
+
+int device_sm_count()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+}
+
+int device_smem_optin()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+size_t walk_smem_bytes(int window, int elem_bytes)
+{
+    return (size_t)4 * (size_t)window * (size_t)kGroup * (size_t)elem_bytes;
+}
+
+__global__ void init_header_kernel(Header* h, int keep_set1)
+{
+    h->err = kNoError;
+    h->maxlen[0] = 0;
+    if (!keep_set1) h->maxlen[1] = 0;
+    h->tiles = 0;
+}
+
+__global__ void reset_tiles_kernel(Header* h) { h->tiles = 0; }
+
+__global__ void zero_kernel(double* a, int64_t n)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = 0.0;
+}
+
+}  // namespace pcfgb
+
+using namespace pcfgb;
+
+namespace {
+
+bool csr_ok(const pcf_csr* x)
+{
+    if (!x) return false;
+    if (x->n < 0 || x->nnz < 0 || x->n > 0x7fffffffLL) return false;
+    if (x->dtype != PCF_F32 && x->dtype != PCF_F64) return false;
+    if (x->n > 0) {
+        if (x->nnz < x->n) return false;
+        if (!x->offsets || !x->times || !x->values) return false;
+    }
+    return true;
+}
+
+int elem_bytes_for(int precision) { return precision == PCF_PREC_F64 ? 16 : 8; }
+
+// Internal metric of one request: what the walk has to accumulate.
+enum ReqKind { RK_L1, RK_L2, RK_L3, RK_LP, RK_GRAM };
+
+int req_kind(const pcf_integral& f)
+{
+    switch (f.metric) {
+    case PCF_L1: return RK_L1;
+    case PCF_L2: return RK_L2;
+    case PCF_GRAM: return RK_GRAM;
+    case PCF_LP:
+        if (f.p == 1.0) return RK_L1;
+        if (f.p == 2.0) return RK_L2;
+        if (f.p == 3.0) return RK_L3;
+        return RK_LP;
+    default: return -1;
+    }
+}
+
+struct Launch {
+    int combo;
+    int idx[3];   // request index per combo slot
+    int n;
+};
+
+// Group requests into walks: the fused combinations first, the rest alone.
+std::vector<Launch> plan(const pcf_integral* F, int nF)
+{
+    std::vector<Launch> out;
+    std::vector<int> kinds(nF);
+    std::vector<bool> used(nF, false);
+    for (int i = 0; i < nF; ++i) kinds[i] = req_kind(F[i]);
+    auto find = [&](int kind) {
+        for (int i = 0; i < nF; ++i) if (!used[i] && kinds[i] == kind) return i;
+        return -1;
+    };
+    for (;;) {
+        int a = find(RK_L1), b = find(RK_L2), g = find(RK_GRAM), c = find(RK_L3);
+        if (a >= 0 && b >= 0 && g >= 0) {
+            used[a] = used[b] = used[g] = true;
+            out.push_back({kComboL1L2Gram, {a, b, g}, 3});
+            continue;
+        }
+        if (a >= 0 && b >= 0 && c >= 0) {
+            used[a] = used[b] = used[c] = true;
+            out.push_back({kComboL1L2L3, {a, b, c}, 3});
+            continue;
+        }
+        break;
+    }
+    for (int i = 0; i < nF; ++i) {
+        if (used[i]) continue;
+        int combo = kinds[i] == RK_L1 ? kComboL1 : kinds[i] == RK_L2 ? kComboL2
+                  : kinds[i] == RK_L3 ? kComboL3 : kinds[i] == RK_LP ? kComboLP : kComboGram;
+        out.push_back({combo, {i, -1, -1}, 1});
+    }
+    return out;
+}
+
+int check_requests(const pcf_integral* F, int nF, bool need_out)
+{
+    if (!F || nF < 1 || nF > PCF_MAX_INTEGRALS) return PCF_EINVAL;
+    for (int i = 0; i < nF; ++i) {
+        if (req_kind(F[i]) < 0) return PCF_EINVAL;
+        if (F[i].metric == PCF_LP && !(F[i].p >= 1.0 && std::isfinite(F[i].p))) return PCF_EINVAL;
+        if (need_out && !F[i].out) return PCF_EINVAL;
+    }
+    return PCF_OK;
+}
+
+int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int elem_bytes,
+              cudaStream_t s)
+{
+    const int optin = device_smem_optin();
+    int W = (int)((optin - 4096) / (4 * kGroup * elem_bytes));
+    if (W > 4096) W = 4096;
+    if (W < 8) return PCF_ECUDA;
+    wa.window = W;
+    const size_t smem = walk_smem_bytes(W, elem_bytes);
+    int64_t grid = device_sm_count();
+    if (grid > wa.ntiles) grid = wa.ntiles;
+    if (grid < 1) return PCF_OK;
+    for (const Launch& L : plan(F, nF)) {
+        wa.nout = L.n;
+        for (int k = 0; k < L.n; ++k) {
+            const pcf_integral& f = F[L.idx[k]];
+            wa.out[k] = f.out;
+            wa.metric[k] = f.metric;
+            wa.root[k] = f.apply_root ? 1 : 0;
+            wa.p[k] = f.metric == PCF_LP ? f.p : (f.metric == PCF_L2 ? 2.0 : 1.0);
+        }
+        reset_tiles_kernel<<<1, 1, 0, s>>>(wa.hdr);
+        cudaError_t e;
+        if (precision == PCF_PREC_F64) e = launch_walk_f64(L.combo, wa, (int)grid, smem, s);
+        else if (precision == PCF_PREC_F32_COMP) e = launch_walk_f32c(L.combo, wa, (int)grid, smem, s);
+        else e = launch_walk_f32(L.combo, wa, (int)grid, smem, s);
+        if (e != cudaSuccess) return PCF_ECUDA;
+    }
+    return PCF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pcf_workspace_size(const pcf_csr* x, const pcf_csr* y, int precision, int purpose,
+                       size_t* bytes)
+{
+    if (!bytes || !x || x->n < 0 || x->nnz < 0 || x->n > 0x7fffffffLL) return PCF_EINVAL;
+    if (y && (y->n < 0 || y->nnz < 0 || y->n > 0x7fffffffLL)) return PCF_EINVAL;
+    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32) return PCF_EINVAL;
+    if (purpose != PCF_WS_FORWARD && purpose != PCF_WS_BACKWARD) return PCF_EINVAL;
+    const int es = purpose == PCF_WS_BACKWARD ? 16 : elem_bytes_for(precision);
+    size_t b = sizeof(Header);
+    if (y) b += set_bytes(y->n, y->nnz, es);
+    b += set_bytes(x->n, x->nnz, es);
+    if (purpose == PCF_WS_BACKWARD) b += 2 * align_up(sizeof(double) * (size_t)x->nnz);
+    *bytes = b;
+    return PCF_OK;
+}
+
+static int pairwise_common(const pcf_csr* x, int precision, void* workspace,
+                           size_t workspace_bytes, Header** hdr_out, SetView* sv_out)
+{
+    size_t need = 0;
+    pcf_workspace_size(x, nullptr, precision, PCF_WS_FORWARD, &need);
+    if (!workspace || ((uintptr_t)workspace % kAlign) != 0 || workspace_bytes < need) return PCF_ENOWS;
+    char* cur = (char*)workspace;
+    *hdr_out = (Header*)cur;
+    cur += sizeof(Header);
+    *sv_out = carve_set(cur, x->n, x->nnz, elem_bytes_for(precision), 0);
+    return PCF_OK;
+}
+
+int pcf_prepare(const pcf_csr* x, int precision, void* workspace, size_t workspace_bytes,
+                cudaStream_t stream)
+{
+    if (!csr_ok(x)) return PCF_EINVAL;
+    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32) return PCF_EINVAL;
+    Header* hdr;
+    SetView sv;
+    int rc = pairwise_common(x, precision, workspace, workspace_bytes, &hdr, &sv);
+    if (rc != PCF_OK) return rc;
+    init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
+    if (x->n == 0) return cudaGetLastError() == cudaSuccess ? PCF_OK : PCF_ECUDA;
+    if (prepare_set(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz, true,
+                    precision == PCF_PREC_F64, hdr, sv, stream) != cudaSuccess)
+        return PCF_ECUDA;
+    return PCF_OK;
+}
+
+int pcf_pairwise(const pcf_csr* x, const pcf_integral* F, int nF, int precision, int layout,
+                 int out_dtype, int flags, void* workspace, size_t workspace_bytes,
+                 cudaStream_t stream)
+{
+    if (!csr_ok(x)) return PCF_EINVAL;
+    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32) return PCF_EINVAL;
+    if (layout != PCF_OUT_FULL && layout != PCF_OUT_UPPER_PACKED) return PCF_EINVAL;
+    if (out_dtype != PCF_F32 && out_dtype != PCF_F64) return PCF_EINVAL;
+    if (flags & ~PCF_PAIRWISE_PREPARED) return PCF_EINVAL;
+    int rc = check_requests(F, nF, x->n > 0);
+    if (rc != PCF_OK) return rc;
+    Header* hdr;
+    SetView sv;
+    rc = pairwise_common(x, precision, workspace, workspace_bytes, &hdr, &sv);
+    if (rc != PCF_OK) return rc;
+    if (x->n == 0) return PCF_OK;
+    const int es = elem_bytes_for(precision);
+    if (!(flags & PCF_PAIRWISE_PREPARED)) {
+        init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
+        if (prepare_set(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz, true,
+                        precision == PCF_PREC_F64, hdr, sv, stream) != cudaSuccess)
+            return PCF_ECUDA;
+    }
+
+    WalkArgs wa;
+    memset(&wa, 0, sizeof wa);
+    wa.pack_r = wa.pack_c = sv.packed;
+    wa.poff_r = wa.poff_c = sv.poff;
+    wa.slen_r = wa.slen_c = sv.slen;
+    wa.perm_r = wa.perm_c = sv.perm;
+    wa.n_r = wa.n_c = x->n;
+    wa.nb_r = wa.nb_c = (x->n + kTile - 1) / kTile;
+    wa.ntiles = wa.nb_r * (wa.nb_r + 1) / 2;
+    wa.symmetric = 1;
+    wa.hdr = hdr;
+    wa.layout = layout;
+    wa.out_f64 = out_dtype == PCF_F64;
+    wa.ld_out = x->n;
+    return run_walks(wa, F, nF, precision, es, stream);
+}
+
+int pcf_cross(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row_end,
+              const pcf_integral* F, int nF, int precision, int64_t ld_out, int out_dtype,
+              int flags, void* workspace, size_t workspace_bytes, cudaStream_t stream)
+{
+    if (!csr_ok(a) || !csr_ok(b)) return PCF_EINVAL;
+    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32) return PCF_EINVAL;
+    if (out_dtype != PCF_F32 && out_dtype != PCF_F64) return PCF_EINVAL;
+    if (row_begin < 0 || row_end < row_begin || row_end > a->n) return PCF_EINVAL;
+    if (ld_out < b->n) return PCF_EINVAL;
+    if (flags & ~PCF_CROSS_REUSE_B) return PCF_EINVAL;
+    const int64_t rows = row_end - row_begin;
+    int rc = check_requests(F, nF, rows > 0 && b->n > 0);
+    if (rc != PCF_OK) return rc;
+    size_t need = 0;
+    pcf_workspace_size(a, b, precision, PCF_WS_FORWARD, &need);
+    if (!workspace || ((uintptr_t)workspace % kAlign) != 0 || workspace_bytes < need) return PCF_ENOWS;
+    if (rows == 0 || b->n == 0) return PCF_OK;
+
+    char* cur = (char*)workspace;
+    Header* hdr = (Header*)cur;
+    cur += sizeof(Header);
+    const int es = elem_bytes_for(precision);
+    SetView sb = carve_set(cur, b->n, b->nnz, es, 1);
+    SetView sa = carve_set(cur, rows, a->nnz, es, 0);
+    const bool reuse = (flags & PCF_CROSS_REUSE_B) != 0;
+    init_header_kernel<<<1, 1, 0, stream>>>(hdr, reuse ? 1 : 0);
+    if (!reuse) {
+        if (prepare_set(b->offsets, b->times, b->values, b->dtype, b->n, b->nnz, true,
+                        precision == PCF_PREC_F64, hdr, sb, stream) != cudaSuccess)
+            return PCF_ECUDA;
+    }
+    if (prepare_set(a->offsets + row_begin, a->times, a->values, a->dtype, rows, a->nnz,
+                    row_begin == 0 && row_end == a->n, precision == PCF_PREC_F64, hdr, sa,
+                    stream) != cudaSuccess)
+        return PCF_ECUDA;
+
+    WalkArgs wa;
+    memset(&wa, 0, sizeof wa);
+    wa.pack_r = sa.packed; wa.poff_r = sa.poff; wa.slen_r = sa.slen; wa.perm_r = sa.perm;
+    wa.pack_c = sb.packed; wa.poff_c = sb.poff; wa.slen_c = sb.slen; wa.perm_c = sb.perm;
+    wa.n_r = rows;
+    wa.n_c = b->n;
+    wa.nb_r = (rows + kTile - 1) / kTile;
+    wa.nb_c = (b->n + kTile - 1) / kTile;
+    wa.ntiles = wa.nb_r * wa.nb_c;
+    wa.symmetric = 0;
+    wa.hdr = hdr;
+    wa.layout = PCF_OUT_FULL;
+    wa.out_f64 = out_dtype == PCF_F64;
+    wa.ld_out = ld_out;
+    return run_walks(wa, F, nF, precision, es, stream);
+}
+
+int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root,
+                          const void* fwd_out, const void* grad_out, int grad_dtype,
+                          void* grad_values, void* grad_times, void* workspace,
+                          size_t workspace_bytes, cudaStream_t stream)
+{
+    if (!csr_ok(x)) return PCF_EINVAL;
+    if (metric < PCF_L1 || metric > PCF_GRAM) return PCF_EINVAL;
+    if (metric == PCF_LP && !(p >= 1.0 && std::isfinite(p))) return PCF_EINVAL;
+    if (grad_dtype != PCF_F32 && grad_dtype != PCF_F64) return PCF_EINVAL;
+    const double ex = metric == PCF_L1 ? 1.0 : metric == PCF_L2 ? 2.0 : metric == PCF_LP ? p : 1.0;
+    const bool need_fwd = apply_root && metric != PCF_GRAM && ex != 1.0;
+    if (x->n > 0 && (!grad_out || !grad_values || !grad_times)) return PCF_EINVAL;
+    if (x->n > 0 && need_fwd && !fwd_out) return PCF_EINVAL;
+    size_t need = 0;
+    pcf_workspace_size(x, nullptr, PCF_PREC_F64, PCF_WS_BACKWARD, &need);
+    if (!workspace || ((uintptr_t)workspace % kAlign) != 0 || workspace_bytes < need) return PCF_ENOWS;
+    if (x->n == 0) return PCF_OK;
+
+    char* cur = (char*)workspace;
+    Header* hdr = (Header*)cur;
+    cur += sizeof(Header);
+    SetView sv = carve_set(cur, x->n, x->nnz, 16, 0);
+    double* gv = (double*)cur;
+    cur += align_up(sizeof(double) * (size_t)x->nnz);
+    double* gt = (double*)cur;
+    init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
+    if (prepare_set(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz, true, 1, hdr, sv,
+                    stream) != cudaSuccess)
+        return PCF_ECUDA;
+    {
+        int64_t blocks = (x->nnz + 255) / 256;
+        const int64_t cap = (int64_t)device_sm_count() * 16;
+        if (blocks > cap) blocks = cap;
+        zero_kernel<<<(int)blocks, 256, 0, stream>>>(gv, x->nnz);
+        zero_kernel<<<(int)blocks, 256, 0, stream>>>(gt, x->nnz);
+    }
+    BackArgs ba;
+    memset(&ba, 0, sizeof ba);
+    ba.pack = (const double2*)sv.packed;
+    ba.poff = sv.poff; ba.slen = sv.slen; ba.perm = sv.perm;
+    ba.n = x->n;
+    ba.nb = (x->n + kTile - 1) / kTile;
+    ba.ntiles = ba.nb * (ba.nb + 1) / 2;
+    ba.G = grad_out; ba.F = fwd_out; ba.g_f64 = grad_dtype == PCF_F64;
+    ba.metric = metric; ba.p = p; ba.apply_root = apply_root ? 1 : 0;
+    ba.gv = gv; ba.gt = gt; ba.hdr = hdr;
+    if (launch_backward(ba, stream) != cudaSuccess) return PCF_ECUDA;
+    if (launch_scatter_grad(sv, x->offsets, gv, gt, grad_values, grad_times,
+                            x->dtype == PCF_F64, hdr, stream) != cudaSuccess)
+        return PCF_ECUDA;
+    return PCF_OK;
+}
+
+int pcf_check(const void* workspace, cudaStream_t stream, int* detail, int64_t* index)
+{
+    if (!workspace) return PCF_ENOWS;
+    unsigned long long key = 0;
+    if (cudaMemcpyAsync(&key, workspace, sizeof key, cudaMemcpyDeviceToHost, stream) != cudaSuccess)
+        return PCF_ECUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return PCF_ECUDA;
+    if (key == kNoError) {
+        if (detail) *detail = 0;
+        if (index) *index = -1;
+        return PCF_OK;
+    }
+    if (detail) *detail = (int)(key >> 56);
+    if (index) *index = (int64_t)(key & ((1ull << 56) - 1));
+    return PCF_EINVAL;
+}
+
+const char* pcf_status_string(int status)
+{
+    switch (status) {
+    case PCF_OK: return "ok";
+    case PCF_EINVAL: return "invalid argument or invalid PCF data";
+    case PCF_ENOWS: return "workspace missing, misaligned or too small";
+    case PCF_ECUDA: return "CUDA runtime error";
+    case PCF_ETIMEOUT: return "bounded device wait gave up";
+    case PCF_EUNSUPPORTED: return "unsupported request";
+    default: return "unknown status";
+    }
+}
+
+const char* pcf_version(void) { return "pcf_gb300 1 sm_103a"; }
+
+}  // extern "C"

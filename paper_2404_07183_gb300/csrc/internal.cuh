@@ -1,0 +1,132 @@
+// internal.cuh -- shared declarations of the CUDA library (not installed).
+//
+// Data layout in HBM (all inside the caller's workspace):
+//   header   : device error key, max lengths, tile counter            (256 B)
+//   per set  : lens[N] int32      lengths in input order
+//              perm[N] int32      input index of the s-th shortest PCF
+//              slen[N] int32      lengths in sorted order
+//              tmpk/tmpv[N] int32 radix-sort ping-pong buffers
+//              poff[N+1] int64    packed offsets (exclusive scan of slen)
+//              packed[nnz]        "interval elements" in sorted order:
+//                                 element k of PCF s = (te_k, v_k), the value
+//                                 v_k on [t_k, te_k) with te_k = t_{k+1} and
+//                                 te_{n-1} = +inf; float or double pairs
+//   backward : gv[nnz], gt[nnz] float64 gradient accumulators (packed order)
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/pcf.h"
+
+namespace pcfgb {
+
+constexpr int kTile = 32;        // PCFs per tile side (rows and columns)
+constexpr int kGroup = 16;       // PCFs interleaved per shared-memory region
+constexpr int kTilePcfs = 64;    // 32 row PCFs + 32 column PCFs
+constexpr int kWalkThreads = 1024;  // 32 warps: one diagonal of the tile each
+constexpr size_t kAlign = 256;
+
+// Device-side error key: (detail << 56) | index, minimum wins; ~0 = no error.
+enum ErrDetail : int {
+    kErrOffsets = 1, kErrT0 = 2, kErrOrder = 3, kErrTimeNaN = 4,
+    kErrValueNaN = 5, kErrRange32 = 6, kErrDense32 = 7
+};
+constexpr unsigned long long kNoError = ~0ull;
+
+struct Header {
+    unsigned long long err;      // error key
+    unsigned int maxlen[2];      // max PCF length of set 0 / set 1
+    unsigned long long tiles;    // persistent-kernel tile counter
+    unsigned long long pad[29];
+};
+static_assert(sizeof(Header) == 256, "header is 256 bytes");
+
+#ifdef __CUDACC__
+__device__ __forceinline__ void record_error(Header* h, int detail, long long index)
+{
+    unsigned long long key = ((unsigned long long)detail << 56) |
+                             ((unsigned long long)index & ((1ull << 56) - 1));
+    atomicMin(&h->err, key);
+}
+#endif
+
+// Device pointers of one prepared (validated, sorted, packed) collection.
+struct SetView {
+    int64_t n = 0;          // number of PCFs
+    int64_t nnz = 0;        // upper bound on breakpoints (buffer capacity)
+    int32_t* lens = nullptr;
+    int32_t* perm = nullptr;
+    int32_t* slen = nullptr;
+    int32_t* tmpk = nullptr;
+    int32_t* tmpv = nullptr;
+    int64_t* poff = nullptr;
+    void* packed = nullptr;
+    int elem_bytes = 8;     // 8 (float pairs) or 16 (double pairs)
+    int slot = 0;           // which Header::maxlen entry
+};
+
+size_t set_bytes(int64_t n, int64_t nnz, int elem_bytes);
+SetView carve_set(char*& cursor, int64_t n, int64_t nnz, int elem_bytes, int slot);
+
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Validate + sort + pack one collection given by absolute CSR offsets
+// (offsets[0..n]) into arrays of total length nnz_total.  When `whole` is set
+// offsets[0] must be 0 and offsets[n] must equal nnz_total.
+cudaError_t prepare_set(const int64_t* offsets, const void* times, const void* values,
+                        int in_dtype, int64_t n, int64_t nnz_total, bool whole,
+                        int walk_f64, Header* hdr, SetView& sv, cudaStream_t s);
+
+// Arguments of the tile walk kernels.
+struct WalkArgs {
+    // rows (set R) and columns (set C), sorted + packed
+    const void* pack_r; const int64_t* poff_r; const int32_t* slen_r; const int32_t* perm_r;
+    const void* pack_c; const int64_t* poff_c; const int32_t* slen_c; const int32_t* perm_c;
+    int64_t n_r, n_c;
+    int64_t nb_r, nb_c;      // tile blocks
+    int64_t ntiles;
+    int symmetric;           // pairwise: upper-triangle tiles, R == C
+    int window;              // W: staged elements per PCF per window
+    Header* hdr;
+    // outputs
+    int nout;
+    void* out[PCF_MAX_INTEGRALS];
+    int metric[PCF_MAX_INTEGRALS];
+    int root[PCF_MAX_INTEGRALS];
+    double p[PCF_MAX_INTEGRALS];
+    int layout;              // pcf_layout (pairwise) ; cross always dense block
+    int out_f64;
+    int64_t ld_out;          // cross: leading dimension; pairwise: N
+};
+
+// Metric combination codes compiled into the walk kernels.
+enum Combo : int {
+    kComboL1 = 0, kComboL2 = 1, kComboGram = 2, kComboLP = 3, kComboL3 = 4,
+    kComboL1L2Gram = 5, kComboL1L2L3 = 6, kComboCount = 7
+};
+
+// Launch the persistent tile walk for one precision and metric combination.
+cudaError_t launch_walk_f64(int combo, const WalkArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_walk_f32c(int combo, const WalkArgs& a, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_walk_f32(int combo, const WalkArgs& a, int grid, size_t smem, cudaStream_t s);
+size_t walk_smem_bytes(int window, int elem_bytes);
+
+// Adjoint.
+struct BackArgs {
+    const double2* pack; const int64_t* poff; const int32_t* slen; const int32_t* perm;
+    int64_t n, nb, ntiles;
+    const void* G; const void* F; int g_f64;
+    int metric; double p; int apply_root;
+    double* gv; double* gt;      // packed-order accumulators
+    Header* hdr;
+};
+cudaError_t launch_backward(const BackArgs& a, cudaStream_t s);
+cudaError_t launch_scatter_grad(const SetView& sv, const int64_t* offsets, const double* gv,
+                                const double* gt, void* grad_values, void* grad_times,
+                                int out_f64, Header* hdr, cudaStream_t s);
+
+int device_sm_count();
+int device_smem_optin();
+
+}  // namespace pcfgb

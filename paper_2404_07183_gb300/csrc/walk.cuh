@@ -1,0 +1,373 @@
+// walk.cuh -- persistent pair-tile merge walk (rectangle iteration, Sec. 3
+// Alg. 1, with the accumulation of Alg. 2 / Eq. simpleint fused in).
+//
+// Work decomposition
+//   * PCFs are sorted by length and cut into blocks of 32; a tile is a
+//     (row block, column block) pair: 32 x 32 = 1024 pairs.  Pairwise calls
+//     visit the upper triangle of blocks; cross calls all blocks.  Tiles are
+//     handed out by one atomic counter (longest PCFs first) to one persistent
+//     1024-thread CTA per SM.
+//   * Warp w of the CTA takes the tile's w-th diagonal: lane l walks the pair
+//     (row (l + w) mod 32, column l).  Every lane of a half-warp (quarter-warp
+//     for 16-byte elements) therefore reads a different PCF of each side.
+//   * The tile's 64 PCFs are staged in shared memory in four regions of 16
+//     PCFs; element k of PCF slot s sits at (k * 16 + s) * sizeof(element), so
+//     the 16 PCFs of a region fall into 16 different bank groups and the
+//     data-dependent reads of a warp are free of bank conflicts whatever
+//     positions the lanes have reached.
+//   * Long PCFs are staged in time windows [T0, T1): T1 is the smallest end
+//     time of the W-th remaining element over the tile's PCFs, so every PCF's
+//     elements up to T1 fit.  A lane walks exactly the rectangles that end
+//     before T1 and resumes in the next window at element 0 of both its PCFs;
+//     the rectangles, their order and their arithmetic are the same as in one
+//     uninterrupted walk.
+//
+// The merge step (one rectangle per step, one side advances per step).
+// Because h is symmetric in its two arguments, the lane keeps its two cursors
+// as A (the side whose current interval ends first) and B.  A step emits the
+// rectangle [tc, te_A) with value h(v_A, v_B), loads A's next element, and
+// swaps A and B when that element ends after B's current one.  A breakpoint
+// shared by both PCFs costs one extra step whose rectangle has width 0 and
+// adds an exact zero.  Every step is one full-width shared-memory load and no
+// divergent branch; the step count of a pair is n_f + n_g - 2 plus the tail.
+#pragma once
+
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace pcfgb {
+
+constexpr int kF64 = 0, kF32C = 1, kF32 = 2;
+constexpr int MI_NONE = 0, MI_L1 = 1, MI_L2 = 2, MI_L3 = 3, MI_LP = 4, MI_GRAM = 5;
+
+__host__ __device__ constexpr int combo_n(int c)
+{
+    return (c == kComboL1L2Gram || c == kComboL1L2L3) ? 3 : 1;
+}
+
+__host__ __device__ constexpr int combo_metric(int c, int slot)
+{
+    return c == kComboL1 ? MI_L1
+         : c == kComboL2 ? MI_L2
+         : c == kComboGram ? MI_GRAM
+         : c == kComboLP ? MI_LP
+         : c == kComboL3 ? MI_L3
+         : c == kComboL1L2Gram ? (slot == 0 ? MI_L1 : slot == 1 ? MI_L2 : MI_GRAM)
+         : (slot == 0 ? MI_L1 : slot == 1 ? MI_L2 : MI_L3);
+}
+
+template <typename T> struct ElemOf;
+template <> struct ElemOf<float> { using type = float2; };
+template <> struct ElemOf<double> { using type = double2; };
+
+// h(a, b) of Sec. 2.2 for one metric, in the walk type.
+template <int MI, typename T>
+__device__ __forceinline__ T term_h(T a, T b, T d, T p)
+{
+    if constexpr (MI == MI_L1) return fabs(d);
+    else if constexpr (MI == MI_L2) return d * d;
+    else if constexpr (MI == MI_L3) { T ad = fabs(d); return ad * ad * ad; }
+    else if constexpr (MI == MI_LP) return pow(fabs(d), p);
+    else return a * b;
+}
+
+template <int PREC> struct Acc;
+template <> struct Acc<kF64> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double h, double dt) { s = fma(h, dt, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <> struct Acc<kF32> {
+    float s = 0.f;
+    __device__ __forceinline__ void add(float h, float dt) { s = fmaf(h, dt, s); }
+    __device__ __forceinline__ double value() const { return (double)s; }
+};
+// Knuth's TwoSum: s1 + err == s + x exactly; err is kept in c.
+template <> struct Acc<kF32C> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float h, float dt)
+    {
+        float x = __fmul_rn(h, dt);
+        float s1 = __fadd_rn(s, x);
+        float bp = __fsub_rn(s1, s);
+        float ap = __fsub_rn(s1, bp);
+        float e = __fadd_rn(__fsub_rn(s, ap), __fsub_rn(x, bp));
+        c = __fadd_rn(c, e);
+        s = s1;
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+template <int COMBO, int PREC, typename T>
+__device__ __forceinline__ void accumulate(Acc<PREC>* acc, T a, T b, T dt, T p)
+{
+    const T d = a - b;
+    acc[0].add(term_h<combo_metric(COMBO, 0)>(a, b, d, p), dt);
+    if constexpr (combo_n(COMBO) > 1) acc[1].add(term_h<combo_metric(COMBO, 1)>(a, b, d, p), dt);
+    if constexpr (combo_n(COMBO) > 2) acc[2].add(term_h<combo_metric(COMBO, 2)>(a, b, d, p), dt);
+}
+
+// Exact "x ends after y" for interval ends (non-negative, +inf allowed).
+// float64 compares go to the integer pipe through the bit patterns, which
+// order like the values for non-negative doubles.
+__device__ __forceinline__ bool ends_after(float x, float y) { return x > y; }
+__device__ __forceinline__ bool ends_after(double x, double y)
+{
+    return __double_as_longlong(x) > __double_as_longlong(y);
+}
+
+__device__ __forceinline__ double finalize_root(int metric, int root, double p, double I)
+{
+    if (!root || metric == PCF_GRAM) return I;
+    double e = metric == PCF_L1 ? 1.0 : metric == PCF_L2 ? 2.0 : p;
+    if (e == 1.0) return I;
+    if (e == 2.0) return sqrt(I);
+    return pow(I, 1.0 / e);
+}
+
+__device__ __forceinline__ void decode_tile(const WalkArgs& a, int64_t t, int64_t& bi, int64_t& bj)
+{
+    if (a.symmetric) {
+        const int64_t NB = a.nb_r;
+        double q = 2.0 * (double)NB + 1.0;
+        double disc = q * q - 8.0 * (double)t;
+        int64_t m = (int64_t)((q - sqrt(disc > 0.0 ? disc : 0.0)) * 0.5);
+        if (m < 0) m = 0;
+        while (m > 0 && m * NB - m * (m - 1) / 2 > t) --m;
+        while ((m + 1) * NB - (m + 1) * m / 2 <= t) ++m;
+        const int64_t within = t - (m * NB - m * (m - 1) / 2);
+        bj = NB - 1 - m;
+        bi = bj - within;
+    } else {
+        const int64_t q = t / a.nb_c, r = t - q * a.nb_c;
+        bi = a.nb_r - 1 - q;
+        bj = a.nb_c - 1 - r;
+    }
+}
+
+template <typename T, int PREC, int COMBO>
+__global__ void __launch_bounds__(kWalkThreads, 1) walk_kernel(const WalkArgs a)
+{
+    using E = typename ElemOf<T>::type;
+    constexpr int NM = combo_n(COMBO);
+    constexpr unsigned kRow = kGroup * sizeof(E);   // bytes between element k and k+1 of a PCF
+
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int32_t sS[kTilePcfs], sNext[kTilePcfs], sLen[kTilePcfs];
+    __shared__ int64_t sOff[kTilePcfs];
+    __shared__ T sT1part[2];
+    __shared__ int64_t sTile;
+
+    if (a.hdr->err != kNoError) return;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int W = a.window;
+    const unsigned regionBytes = (unsigned)W * kRow;
+    const T p0 = (T)a.p[0];
+
+    // this lane's pair inside every tile: row (lane + warp) & 31, column lane
+    const int my_r = (lane + warp) & 31;
+    const int my_c = lane;
+    const int pf = my_r;            // tile PCF index of the row side
+    const int pg = 32 + my_c;       // tile PCF index of the column side
+    const unsigned base_f = (unsigned)(pf >> 4) * regionBytes + (unsigned)(pf & 15) * sizeof(E);
+    const unsigned base_g = (unsigned)(pg >> 4) * regionBytes + (unsigned)(pg & 15) * sizeof(E);
+
+    for (;;) {
+        if (tid == 0) sTile = (int64_t)atomicAdd(&a.hdr->tiles, 1ull);
+        __syncthreads();
+        const int64_t t = sTile;
+        if (t >= a.ntiles) break;
+        int64_t bi, bj;
+        decode_tile(a, t, bi, bj);
+
+        // tile metadata
+        if (tid < kTilePcfs) {
+            const bool is_row = tid < 32;
+            const int64_t g = is_row ? bi * kTile + tid : bj * kTile + (tid - 32);
+            const int64_t nset = is_row ? a.n_r : a.n_c;
+            if (g < nset) {
+                sLen[tid] = is_row ? a.slen_r[g] : a.slen_c[g];
+                sOff[tid] = is_row ? a.poff_r[g] : a.poff_c[g];
+            } else {
+                sLen[tid] = 0;   // no PCF: never staged, never walked
+                sOff[tid] = 0;
+            }
+            sS[tid] = 0;
+        }
+        const bool lane_valid = (bi * kTile + my_r < a.n_r) && (bj * kTile + my_c < a.n_c);
+
+        Acc<PREC> acc[NM];
+        T T0 = T(0);            // start of the current window (block-uniform)
+        T tc = T(0);
+        T vA = T(0), vB = T(0);
+        __syncthreads();
+
+        for (;;) {
+            // ---- window end T1 = min over PCFs of te[S + W - 1] (clamped) ----
+            if (tid < kTilePcfs) {
+                T cand = T(INFINITY);
+                const int len = sLen[tid];
+                if (len > 0) {
+                    int idx = sS[tid] + W - 1;
+                    if (idx > len - 1) idx = len - 1;
+                    const E* src = reinterpret_cast<const E*>(tid < 32 ? a.pack_r : a.pack_c);
+                    cand = src[sOff[tid] + idx].x;
+                }
+                for (int o = 16; o > 0; o >>= 1) {
+                    T other = __shfl_xor_sync(0xffffffffu, cand, o);
+                    cand = other < cand ? other : cand;
+                }
+                if (lane == 0) sT1part[warp] = cand;
+            }
+            __syncthreads();
+            const T T1 = sT1part[0] < sT1part[1] ? sT1part[0] : sT1part[1];
+            if (!(T1 > T0)) {
+                // more than W coincident interval ends in one PCF (only possible
+                // when float64 times were rounded to float32): no progress
+                if (tid == 0) record_error(a.hdr, kErrDense32, bi * kTile);
+                return;
+            }
+
+            // ---- stage elements [S, S + min(W, len - S)) of all 64 PCFs ----
+            {
+                const int per_region = W * kGroup;
+                for (int q = tid; q < 4 * per_region; q += kWalkThreads) {
+                    const int region = q / per_region;
+                    const int r = q - region * per_region;
+                    const int k = r >> 4;
+                    const int p = region * kGroup + (r & 15);
+                    const int len = sLen[p];
+                    const int S = sS[p];
+                    if (S + k < len) {
+                        const E* src = reinterpret_cast<const E*>(p < 32 ? a.pack_r : a.pack_c);
+                        E e = src[sOff[p] + S + k];
+                        *reinterpret_cast<E*>(smem + (unsigned)region * regionBytes + (unsigned)r * sizeof(E)) = e;
+                    }
+                }
+            }
+            __syncthreads();
+
+            // ---- per PCF: first staged element whose interval ends at/after T1 ----
+            if (tid < kTilePcfs) {
+                const int len = sLen[tid];
+                int next = 0;
+                if (len > 0) {
+                    int cnt = len - sS[tid];
+                    if (cnt > W) cnt = W;
+                    const unsigned colbase = (unsigned)(tid >> 4) * regionBytes + (unsigned)(tid & 15) * sizeof(E);
+                    int lo = 0, hi = cnt - 1;          // te[hi] >= T1 holds by the choice of T1
+                    while (lo < hi) {
+                        int mid = (lo + hi) >> 1;
+                        T te = reinterpret_cast<const E*>(smem + colbase + (unsigned)mid * kRow)->x;
+                        if (te < T1) lo = mid + 1; else hi = mid;
+                    }
+                    next = sS[tid] + lo;
+                }
+                sNext[tid] = next;
+            }
+            __syncthreads();
+
+            // ---- walk this window ----
+            if (lane_valid) {
+                int cnt = (sNext[pf] - sS[pf]) + (sNext[pg] - sS[pg]);
+                unsigned pA = base_f, pB = base_g;
+                E ea = *reinterpret_cast<const E*>(smem + pA);
+                E eb = *reinterpret_cast<const E*>(smem + pB);
+                T teA = ea.x, teB = eb.x;
+                vA = ea.y; vB = eb.y;
+                if (ends_after(teA, teB)) {
+                    T x = teA; teA = teB; teB = x;
+                    x = vA; vA = vB; vB = x;
+                    unsigned u = pA; pA = pB; pB = u;
+                }
+#define PCF_WALK_STEP()                                                           \
+                {                                                                 \
+                    const T dt = teA - tc;                                        \
+                    tc = teA;                                                     \
+                    accumulate<COMBO, PREC, T>(acc, vA, vB, dt, p0);              \
+                    const E nx = *reinterpret_cast<const E*>(smem + pA + kRow);   \
+                    pA += kRow;                                                   \
+                    const bool sw = ends_after(nx.x, teB);                        \
+                    const T nteA = sw ? teB : nx.x;                               \
+                    const T nvA = sw ? vB : nx.y;                                 \
+                    const unsigned npA = sw ? pB : pA;                            \
+                    teB = sw ? nx.x : teB;                                        \
+                    vB = sw ? nx.y : vB;                                          \
+                    pB = sw ? pA : pB;                                            \
+                    teA = nteA; vA = nvA; pA = npA;                               \
+                }
+#pragma unroll 1
+                for (; cnt >= 4; cnt -= 4) {
+                    PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
+                }
+#pragma unroll 1
+                for (; cnt > 0; --cnt) PCF_WALK_STEP()
+#undef PCF_WALK_STEP
+            }
+            const bool last = !(T1 < T(INFINITY));
+            __syncthreads();
+            if (last) break;
+            T0 = T1;
+            if (tid < kTilePcfs) sS[tid] = sNext[tid];
+            __syncthreads();
+        }
+
+        // ---- tail, root, output ----
+        if (lane_valid) {
+            const int64_t gi = bi * kTile + my_r, gj = bj * kTile + my_c;
+            const int64_t i = a.perm_r[gi], j = a.perm_c[gj];
+            const T dlast = vA - vB;
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                const int MI = combo_metric(COMBO, m);
+                double I = acc[m].value();
+                T h;
+                if (MI == MI_GRAM) h = vA * vB;
+                else h = fabs(dlast);
+                if (h != T(0)) I = (h > T(0)) ? (double)INFINITY : -(double)INFINITY;
+                const double F = finalize_root(a.metric[m], a.root[m], a.p[m], I);
+                void* out = a.out[m];
+                auto put = [&](int64_t idx) {
+                    if (a.out_f64) reinterpret_cast<double*>(out)[idx] = F;
+                    else reinterpret_cast<float*>(out)[idx] = (float)F;
+                };
+                if (!a.symmetric) {
+                    put(i * a.ld_out + j);
+                } else if (a.layout == PCF_OUT_FULL) {
+                    put(i * a.ld_out + j);
+                    if (bi != bj) put(j * a.ld_out + i);
+                } else {
+                    const int64_t N = a.ld_out;
+                    const int64_t lo = i < j ? i : j, hi = i < j ? j : i;
+                    if (bi != bj || i <= j) put(lo * N - lo * (lo - 1) / 2 + (hi - lo));
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int PREC>
+cudaError_t launch_walk_t(int combo, const WalkArgs& a, int grid, size_t smem, cudaStream_t s)
+{
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, kWalkThreads, smem, s>>>(a);
+        return cudaGetLastError();
+    };
+    switch (combo) {
+    case kComboL1: return go(walk_kernel<T, PREC, kComboL1>);
+    case kComboL2: return go(walk_kernel<T, PREC, kComboL2>);
+    case kComboGram: return go(walk_kernel<T, PREC, kComboGram>);
+    case kComboLP: return go(walk_kernel<T, PREC, kComboLP>);
+    case kComboL3: return go(walk_kernel<T, PREC, kComboL3>);
+    case kComboL1L2Gram: return go(walk_kernel<T, PREC, kComboL1L2Gram>);
+    case kComboL1L2L3: return go(walk_kernel<T, PREC, kComboL1L2L3>);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pcfgb
