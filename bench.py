@@ -35,9 +35,9 @@ from paper_2404_07183_gb300 import synth  # noqa: E402
 METRICS = ["l1", "l2", "gram"]
 # Algorithmic operations per merge step (frozen tally, see the design notes):
 # common part 5 (compare, select rectangle end, dt, fetch, advance) + d = a-b 1
-# L1 |d|*dt fma 1, L2 d*d + fma 2, Gram a*b + fma 2; compensated: the term is
-# a separate multiply and each accumulate is a 7-op TwoSum with compensation.
-TALLY = {"f32c": 5 + 1 + (1 + 7) + (2 + 7) + (2 + 7), "f32": 5 + 1 + 1 + 2 + 2,
+# L1 |d|*dt fma 1, L2 d*d + fma 2, Gram a*b + fma 2; compensated (Kahan): each
+# accumulate is the fma that subtracts the compensation plus 3 additions.
+TALLY = {"f32c": 5 + 1 + (1 + 3) + (2 + 3) + (2 + 3), "f32": 5 + 1 + 1 + 2 + 2,
          "f64": 5 + 1 + 1 + 2 + 2}
 FP64_OPS_PER_STEP = 1 + 1 + 1 + 2 + 2   # dt, d, L1 fma, L2 mul+fma, Gram mul+fma
 
@@ -62,9 +62,10 @@ def exact_walk_steps(s):
     return int(pairs), int(nnz)
 
 
-def workload(rank=0):
-    s = synth.stable_rank(seed=1002 + rank)
-    return s
+def workload(rank=0, n=None):
+    if n:
+        return synth.stable_rank(n_pcfs=n, seed=1002 + rank)
+    return synth.stable_rank(seed=1002 + rank)
 
 
 def start_clock_sampler(path):
@@ -205,7 +206,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     P.build.build()
 
-    s = workload(rank)
+    s = workload(rank, args.n)
     N = s.n
     walk_steps, diag_steps = exact_walk_steps(s)
     pairs = 2 * (N * (N - 1) // 2) + N * (N + 1) // 2      # distances i<j, Gram i<=j
@@ -269,6 +270,10 @@ def run_ours(args):
                          "steps": steps, "wall_s": t_wall, "clocks": clocks}
         del outs, ws
 
+    if args.no_e2e:
+        if rank == 0:
+            print(json.dumps({"results": results, "N": N, "walk_steps": walk_steps}), flush=True)
+        return
     # end-to-end through the public API with host buffers (pinned), every step:
     # H2D of the CSR, the whole path, D2H of the three matrices
     prec = args.precision
@@ -369,6 +374,9 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=48)
+    ap.add_argument("--n", type=int, default=None,
+                    help="smaller stable-rank collection (profiling runs); default 20000")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -67,8 +67,9 @@ enum pcf_metric {
 /* Arithmetic of the walk.  Breakpoint comparisons are exact in the walk type. */
 enum pcf_precision {
     PCF_PREC_F64 = 0,      /* float64 walk and accumulation                     */
-    PCF_PREC_F32_COMP = 1, /* float32 walk, every rectangle's term added with an
-                              error-free TwoSum into a (sum, compensation) pair */
+    PCF_PREC_F32_COMP = 1, /* float32 walk, every rectangle's term added by Kahan's
+                              compensated summation into a (sum, compensation)
+                              pair; error <= 2u * sum|terms| + O(n u^2)        */
     PCF_PREC_F32 = 2       /* float32 walk, plain float32 fused multiply-add    */
 };
 /* float64 input walked in a float32 precision is rounded to nearest float32
@@ -196,8 +197,10 @@ int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root
  * workspace by the last call: PCF_OK, or PCF_EINVAL with *detail set to the
  * reason code (1 offsets, 2 t_0 != 0, 3 times not increasing, 4 time not
  * finite, 5 value not finite, 6 time or value outside float32 range for a
- * float32 walk) and *index to the smallest offending entry (PCF index for
- * reason 1, element index otherwise).  detail/index may be NULL.
+ * float32 walk, 7 more coincident float32 times than one window holds) and
+ * *index to the offending entry: an offsets error (reason 1, PCF index) is
+ * reported before element errors, and among element errors the smallest
+ * element index wins.  detail/index may be NULL.
  */
 int pcf_check(const void* workspace, cudaStream_t stream, int* detail, int64_t* index);
 

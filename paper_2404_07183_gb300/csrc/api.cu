@@ -381,8 +381,8 @@ int pcf_check(const void* workspace, cudaStream_t stream, int* detail, int64_t* 
         if (index) *index = -1;
         return PCF_OK;
     }
-    if (detail) *detail = (int)(key >> 56);
-    if (index) *index = (int64_t)(key & ((1ull << 56) - 1));
+    if (detail) *detail = (int)(key & 15ull);
+    if (index) *index = (int64_t)((key >> 4) & ((1ull << 58) - 1));
     return PCF_EINVAL;
 }
 

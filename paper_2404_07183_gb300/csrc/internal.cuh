@@ -27,7 +27,10 @@ constexpr int kTilePcfs = 64;    // 32 row PCFs + 32 column PCFs
 constexpr int kWalkThreads = 1024;  // 32 warps: one diagonal of the tile each
 constexpr size_t kAlign = 256;
 
-// Device-side error key: (detail << 56) | index, minimum wins; ~0 = no error.
+// Device-side error key, minimum wins (~0 = no error):
+//   bit 62: 0 for offsets errors (PCF index), 1 for element errors (element
+//   index); bits 4..61: index; bits 0..3: reason.  So a broken offsets array
+//   is reported first, then the smallest offending element.
 enum ErrDetail : int {
     kErrOffsets = 1, kErrT0 = 2, kErrOrder = 3, kErrTimeNaN = 4,
     kErrValueNaN = 5, kErrRange32 = 6, kErrDense32 = 7
@@ -45,8 +48,10 @@ static_assert(sizeof(Header) == 256, "header is 256 bytes");
 #ifdef __CUDACC__
 __device__ __forceinline__ void record_error(Header* h, int detail, long long index)
 {
-    unsigned long long key = ((unsigned long long)detail << 56) |
-                             ((unsigned long long)index & ((1ull << 56) - 1));
+    const unsigned long long cls = detail == kErrOffsets ? 0ull : 1ull;
+    const unsigned long long key = (cls << 62) |
+                                   (((unsigned long long)index & ((1ull << 58) - 1)) << 4) |
+                                   (unsigned long long)(detail & 15);
     atomicMin(&h->err, key);
 }
 #endif

@@ -23,13 +23,15 @@
 //     uninterrupted walk.
 //
 // The merge step (one rectangle per step, one side advances per step).
-// Because h is symmetric in its two arguments, the lane keeps its two cursors
-// as A (the side whose current interval ends first) and B.  A step emits the
-// rectangle [tc, te_A) with value h(v_A, v_B), loads A's next element, and
-// swaps A and B when that element ends after B's current one.  A breakpoint
-// shared by both PCFs costs one extra step whose rectangle has width 0 and
-// adds an exact zero.  Every step is one full-width shared-memory load and no
-// divergent branch; the step count of a pair is n_f + n_g - 2 plus the tail.
+// A lane holds, for each of its PCFs f (row) and g (column), the current
+// interval element (end time te, value v) and its shared-memory offset.  A
+// step emits the rectangle [tc, min(te_f, te_g)) with value h(v_f, v_g) and
+// then loads the next element of the side whose interval ends first (f on a
+// tie).  The two loads are predicated per lane: f-loads only touch the row
+// regions and g-loads only the column regions, so each stays bank-conflict
+// free.  A breakpoint shared by both PCFs costs one extra step whose rectangle
+// has width 0 and adds an exact zero.  The step count of a pair is
+// n_f + n_g - 2 plus the tail, known before the walk starts.
 #pragma once
 
 #include <cmath>
@@ -83,20 +85,22 @@ template <> struct Acc<kF32> {
     __device__ __forceinline__ void add(float h, float dt) { s = fmaf(h, dt, s); }
     __device__ __forceinline__ double value() const { return (double)s; }
 };
-// Knuth's TwoSum: s1 + err == s + x exactly; err is kept in c.
+// Kahan's compensated summation, one rectangle term per add.  The term
+// h * dt is formed inside the fused multiply-add that also removes the
+// running compensation (y = h*dt - c, one rounding), then
+//   t = s + y;  c = (t - s) - y;  s = t,
+// so c holds (the negative of) the low-order part lost by each addition and
+// the sum is s - c.  Error <= 2u * sum |terms| + O(n u^2).
 template <> struct Acc<kF32C> {
     float s = 0.f, c = 0.f;
     __device__ __forceinline__ void add(float h, float dt)
     {
-        float x = __fmul_rn(h, dt);
-        float s1 = __fadd_rn(s, x);
-        float bp = __fsub_rn(s1, s);
-        float ap = __fsub_rn(s1, bp);
-        float e = __fadd_rn(__fsub_rn(s, ap), __fsub_rn(x, bp));
-        c = __fadd_rn(c, e);
-        s = s1;
+        const float y = __fmaf_rn(h, dt, -c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
     }
-    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
 template <int COMBO, int PREC, typename T>
@@ -272,34 +276,32 @@ __global__ void __launch_bounds__(kWalkThreads, 1) walk_kernel(const WalkArgs a)
             // ---- walk this window ----
             if (lane_valid) {
                 int cnt = (sNext[pf] - sS[pf]) + (sNext[pg] - sS[pg]);
-                unsigned pA = base_f, pB = base_g;
-                E ea = *reinterpret_cast<const E*>(smem + pA);
-                E eb = *reinterpret_cast<const E*>(smem + pB);
-                T teA = ea.x, teB = eb.x;
-                vA = ea.y; vB = eb.y;
-                if (ends_after(teA, teB)) {
-                    T x = teA; teA = teB; teB = x;
-                    x = vA; vA = vB; vB = x;
-                    unsigned u = pA; pA = pB; pB = u;
-                }
+                unsigned af = base_f, ag = base_g;
+                const E ef = *reinterpret_cast<const E*>(smem + af);
+                const E eg = *reinterpret_cast<const E*>(smem + ag);
+                T tf = ef.x, tg = eg.x;
+                vA = ef.y;
+                vB = eg.y;
 #define PCF_WALK_STEP()                                                           \
                 {                                                                 \
-                    const T dt = teA - tc;                                        \
-                    tc = teA;                                                     \
+                    const bool adv_f = !ends_after(tf, tg);                       \
+                    const T tn = adv_f ? tf : tg;                                 \
+                    const T dt = tn - tc;                                         \
+                    tc = tn;                                                      \
                     accumulate<COMBO, PREC, T>(acc, vA, vB, dt, p0);              \
-                    const E nx = *reinterpret_cast<const E*>(smem + pA + kRow);   \
-                    pA += kRow;                                                   \
-                    const bool sw = ends_after(nx.x, teB);                        \
-                    const T nteA = sw ? teB : nx.x;                               \
-                    const T nvA = sw ? vB : nx.y;                                 \
-                    const unsigned npA = sw ? pB : pA;                            \
-                    teB = sw ? nx.x : teB;                                        \
-                    vB = sw ? nx.y : vB;                                          \
-                    pB = sw ? pA : pB;                                            \
-                    teA = nteA; vA = nvA; pA = npA;                               \
+                    if (adv_f) {                                                  \
+                        af += kRow;                                               \
+                        const E e = *reinterpret_cast<const E*>(smem + af);       \
+                        tf = e.x; vA = e.y;                                       \
+                    } else {                                                      \
+                        ag += kRow;                                               \
+                        const E e = *reinterpret_cast<const E*>(smem + ag);       \
+                        tg = e.x; vB = e.y;                                       \
+                    }                                                             \
                 }
 #pragma unroll 1
-                for (; cnt >= 4; cnt -= 4) {
+                for (; cnt >= 8; cnt -= 8) {
+                    PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
                     PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
                 }
 #pragma unroll 1

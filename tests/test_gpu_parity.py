@@ -88,10 +88,12 @@ def test_random_sets_vs_oracle(pcf, prec, m):
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32c"])
-@pytest.mark.parametrize("m", ["l1", "l2", "gram", ("lp", 3.0), ("l2", False)], ids=str)
+@pytest.mark.parametrize("m", ["l1", "l2", "gram", ("lp", 3.0, False), ("l2", False)], ids=str)
 def test_dyadic_bitwise(pcf, prec, m):
     """Integer gaps/values with many shared breakpoints: every integral is an
-    exact integer, so the GPU must return the oracle's value exactly."""
+    exact integer, so the GPU must return the oracle's value exactly.  (Roots
+    other than sqrt are compared with tolerance elsewhere: CUDA's pow and the
+    host libm's pow may differ in the last bit.)"""
     import torch
     s = synth.dyadic(100, seed=41, max_len=40, min_len=1, max_gap=3, max_abs_value=8)
     want = _oracle(s, m)
