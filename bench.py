@@ -364,6 +364,233 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+# --------------------------------------------------------------------------
+# Other workloads (one JSON line each): python bench.py --workload NAME|all
+# --------------------------------------------------------------------------
+def _timed(step, steps, warmup, flush, stream):
+    """Per-step device time (ms) with CUDA events; L2 flushed before each."""
+    import torch
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = []
+    for _ in range(steps):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in evs]
+
+
+def _cpu_rows(a, metrics, b=None, seconds_target=8.0, row0=0, p=None):
+    """Oracle on all host cores over a row block sized to ~seconds_target."""
+    import oracle
+    cores = len(os.sched_getaffinity(0))
+    ncols = a.n if b is None else b.n
+    rows = 2
+    t0 = time.perf_counter()
+    oracle.matrix(a, b, metric=metrics[0], p=p or 1.0, rows=(row0, row0 + rows), nthreads=cores)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    rows = int(max(2, min(a.n - row0, rows * seconds_target / (dt * len(metrics)))))
+    t0 = time.perf_counter()
+    for m in metrics:
+        mm, pp = (m, None) if isinstance(m, str) else (m[0], m[1])
+        oracle.matrix(a, b, metric=mm, p=pp or 1.0, rows=(row0, row0 + rows), nthreads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": len(metrics) * rows * ncols / dt, "unit": "pair-integrals/s",
+            "cores": cores, "kind": "oracle", "seconds": dt,
+            "sample": f"rows {row0}..{row0 + rows} x all {ncols} columns x {len(metrics)} "
+                      "metrics, float64 oracle walk, one thread per core"}
+
+
+def _line(name, value, unit, ms, steps, warmup, dtype, config, **extra):
+    d = {"metric": "pair-integrals/s and merge-steps/s at 1 GB300 (FP32-comp vs FP64), "
+                   "% issue roofline",
+         "workload": name, "value": value, "unit": unit, "n_gpus": 1, "steps": steps,
+         "warmup": warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+         "vs_baseline": None, "dtype": dtype, "data": "synthetic", "config": config}
+    d.update(extra)
+    return d
+
+
+def run_workload(name, args):
+    import torch
+    import paper_2404_07183_gb300 as P
+    P.build.build()
+    dev = "cuda:0"
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    pp = pipe_peaks()
+    sms = pp["sms"]
+    fmax = float(measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6
+    issue = lambda tally: sms * 128 * fmax / tally
+    fp64 = lambda ops: sms * pp["fp64"]["lane_ops_per_clk_per_sm"] * fmax / ops
+
+    if name == "uniform_small":
+        s = synth.uniform_small()
+        N = s.n
+        steps_walk, _ = exact_walk_steps(s)
+        x = P.PcfTensors.from_numpy(s, dev)
+        pairs = N * (N - 1) // 2
+        out = {}
+        for prec in ("f64", "f32c"):
+            o = [torch.empty((N, N), dtype=torch.float64, device=dev)]
+            ws = torch.empty(P.pcf_workspace_size(x, None, prec), dtype=torch.uint8, device=dev)
+
+            def step():
+                P.pcf_prepare(x, prec, workspace=ws)
+                P.pcf_pairwise(x, ["l1"], precision=prec, out=o, workspace=ws, prepared=True,
+                               check=False)
+            step()
+            P.pcf_check(ws)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                step()
+            ms = _timed(g.replay, args.steps, args.warmup, flush, stream)
+            P.pcf_check(ws)
+            out[prec] = float(np.mean(ms))
+        ms = out["f64"]
+        rate = steps_walk / (ms * 1e-3)
+        return _line(name, pairs / (ms * 1e-3), "pair-integrals/s", ms, args.steps, args.warmup,
+                     "f64", {"workload": "uniform_small N=1000 n~U{10..100} Exp(1) N(0,1) "
+                             "float64, L1 upper triangle", "N": N, "pairs": pairs,
+                             "merge_steps": steps_walk, "cuda_graph": True,
+                             "l2": "flushed between steps"},
+                     merge_steps_per_s=rate,
+                     roofline={"bound": "fp64 pipe", "achieved": rate, "peak": fp64(3),
+                               "unit": "merge-steps/s", "frac": rate / fp64(3),
+                               "note": "whole step (prepare + walk, 6 launches in one graph)"},
+                     f32c={"ms_per_step": out["f32c"], "value": pairs / (out["f32c"] * 1e-3)},
+                     cpu_baseline=_cpu_rows(s, ["l1"], seconds_target=4.0))
+
+    if name == "lognormal":
+        s = synth.lognormal()
+        N = s.n
+        steps_walk, diag = exact_walk_steps(s)
+        x = P.PcfTensors.from_numpy(s, dev)
+        pairs = N * (N + 1) // 2
+        o = [torch.empty((pairs,), dtype=torch.float32, device=dev)]
+        res = {}
+        for prec in ("f32c", "f32"):
+            ws = torch.empty(P.pcf_workspace_size(x, None, prec), dtype=torch.uint8, device=dev)
+            mids = []
+
+            def step():
+                P.pcf_prepare(x, prec, workspace=ws)
+                e = torch.cuda.Event(enable_timing=True)
+                e.record(stream)
+                mids.append(e)
+                P.pcf_pairwise(x, ["gram"], precision=prec, layout="upper", out=o, workspace=ws,
+                               prepared=True, check=False)
+            ms = _timed(step, max(1, min(args.steps, 2)), 1, flush, stream)
+            P.pcf_check(ws)
+            res[prec] = float(np.mean(ms))
+            del ws
+        ms = res["f32c"]
+        rate = (steps_walk + diag) / (ms * 1e-3)
+        tally = 5 + 2 + 3
+        return _line(name, pairs / (ms * 1e-3), "pair-integrals/s", ms, max(1, min(args.steps, 2)),
+                     1, "f32 (compensated)",
+                     {"workload": "lognormal N=100000 n=clip(round(LogNormal(ln100,1)),2,10000) "
+                                  "Exp(1) N(0,1) float32, L2 Gram upper triangle (packed, f32)",
+                      "N": N, "nnz": s.nnz, "max_len": int(s.lengths().max()), "pairs": pairs,
+                      "merge_steps": steps_walk + diag, "l2": "flushed between steps"},
+                     merge_steps_per_s=rate,
+                     roofline={"bound": "alu", "achieved": rate, "peak": issue(tally),
+                               "unit": "merge-steps/s", "frac": rate / issue(tally),
+                               "note": f"whole step; tally {tally} ops/step (Gram, Kahan)"},
+                     f32={"ms_per_step": res["f32"], "value": pairs / (res["f32"] * 1e-3),
+                          "frac": (steps_walk + diag) / (res["f32"] * 1e-3) / issue(5 + 2)},
+                     cpu_baseline=_cpu_rows(s, ["gram"], seconds_target=8.0, row0=N // 2))
+
+    if name == "gradient":
+        s, G = synth.gradient()
+        N = s.n
+        steps_walk, diag = exact_walk_steps(s)
+        x = P.PcfTensors.from_numpy(s, dev)
+        Gt = torch.from_numpy(G).to(dev)
+        pairs = N * (N - 1) // 2
+
+        def step():
+            P.pcf_pairwise_backward(x, ("l2", False), Gt, check=False)
+        ms = float(np.mean(_timed(step, args.steps, args.warmup, flush, stream)))
+        rate = steps_walk / (ms * 1e-3)
+        import oracle
+        sub = synth.subset(s, np.arange(300))
+        t0 = time.perf_counter()
+        oracle.backward(sub, G[:300, :300], metric="l2", p=2.0)
+        dt = time.perf_counter() - t0
+        return _line(name, pairs / (ms * 1e-3), "pair-gradients/s", ms, args.steps, args.warmup,
+                     "f64", {"workload": "gradient N=4096 n~U{20..200} Exp(1) N(0,1) float64, "
+                             "d(sum G*D2^2)/d(values, times)", "N": N, "pairs": pairs,
+                             "merge_steps": steps_walk, "l2": "flushed between steps"},
+                     merge_steps_per_s=rate,
+                     cpu_baseline={"value": 300 * 299 / 2 / dt, "unit": "pair-gradients/s",
+                                   "cores": 1, "kind": "oracle", "seconds": dt,
+                                   "sample": "first 300 PCFs, single-threaded oracle adjoint"})
+
+    if name == "euler":
+        a, b = synth.euler()
+        NA, NB = a.n, b.n
+        xa = P.PcfTensors.from_numpy(a, dev)
+        xb = P.PcfTensors.from_numpy(b, dev)
+        metrics = [("lp", 1.0), ("lp", 2.0), ("lp", 3.0)]
+        block = 2048
+        nblk = (NA + block - 1) // block
+        bufs = [[torch.empty((block, NB), dtype=torch.float32, device=dev) for _ in metrics]
+                for _ in range(2)]
+        host = [torch.empty((block, NB), dtype=torch.float32).pin_memory() for _ in metrics]
+        copy = torch.cuda.Stream()
+        done = [torch.cuda.Event(), torch.cuda.Event()]
+        ws = torch.empty(P.pcf_workspace_size(xa, xb, "f32c"), dtype=torch.uint8, device=dev)
+
+        def sweep():
+            for k in range(nblk):
+                r0, r1 = k * block, min(NA, (k + 1) * block)
+                buf = bufs[k % 2]
+                stream.wait_event(done[k % 2])
+                views = [t[: r1 - r0] for t in buf]
+                P.pcf_cross(xa, xb, r0, r1, metrics, precision="f32c", out=views, workspace=ws,
+                            reuse_b=k > 0, check=False)
+                ev = torch.cuda.Event()
+                ev.record(stream)
+                copy.wait_event(ev)
+                with torch.cuda.stream(copy):
+                    for h, v in zip(host, views):
+                        h[: r1 - r0].copy_(v, non_blocking=True)
+                    done[k % 2].record(copy)
+            stream.wait_stream(copy)
+        ms = float(np.mean(_timed(sweep, 1, 1, flush, stream)))
+        pairs = NA * NB
+        # |T_i u T_j| = n_i + n_j - 1 - (shared positive times); a time held by
+        # cA PCFs of A and cB PCFs of B is shared by cA * cB pairs
+        ta, ca = np.unique(np.asarray(a.times[a.times > 0], np.float64), return_counts=True)
+        tb, cb = np.unique(np.asarray(b.times[b.times > 0], np.float64), return_counts=True)
+        _, ia, ib = np.intersect1d(ta, tb, assume_unique=True, return_indices=True)
+        shared = int(np.sum(ca[ia].astype(np.int64) * cb[ib].astype(np.int64)))
+        steps_walk = NB * a.nnz + NA * b.nnz - pairs - shared
+        rate = steps_walk / (ms * 1e-3)
+        tally = 5 + 1 + (1 + 3) + (2 + 3) + (3 + 3)
+        return _line(name, 3 * pairs / (ms * 1e-3), "pair-integrals/s", ms, 1, 1,
+                     "f32 (compensated)",
+                     {"workload": "euler A x B 50000 x 50000, n=1000, integer steps +-1..3 at "
+                                  "Exp(1) times, float32; L1+L2+L3 fused, row blocks of 2048 "
+                                  "double-buffered with async D2H to pinned host",
+                      "pairs": pairs, "merge_steps": steps_walk, "blocks": nblk,
+                      "d2h_bytes_per_step": 3 * pairs * 4},
+                     merge_steps_per_s=rate,
+                     roofline={"bound": "alu", "achieved": rate, "peak": issue(tally),
+                               "unit": "merge-steps/s", "frac": rate / issue(tally),
+                               "note": f"whole sweep incl. packing per block; tally {tally}"},
+                     cpu_baseline=_cpu_rows(a, ["l1", "l2", ("lp", 3.0)], b=b, seconds_target=8.0))
+    raise SystemExit(f"unknown workload {name}")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -377,13 +604,20 @@ def main():
     ap.add_argument("--n", type=int, default=None,
                     help="smaller stable-rank collection (profiling runs); default 20000")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="stable_rank",
+                    choices=["stable_rank", "uniform_small", "lognormal", "gradient", "euler", "all"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "stable_rank":
         run_ours(args)
+    else:
+        names = (["uniform_small", "gradient", "lognormal", "euler"] if args.workload == "all"
+                 else [args.workload])
+        for nm in names:
+            print(json.dumps(run_workload(nm, args)), flush=True)
 
 
 if __name__ == "__main__":

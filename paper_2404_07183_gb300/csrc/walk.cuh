@@ -121,6 +121,54 @@ __device__ __forceinline__ bool ends_after(double x, double y)
     return __double_as_longlong(x) > __double_as_longlong(y);
 }
 
+// Predicated advance of the side whose interval ends first (f on a tie):
+// its shared-memory cursor moves to the next element (kRowBytes further) and
+// the element's (end time, value) is loaded in place.  Written as PTX so the
+// two loads stay predicated and land directly in the cursor registers after
+// the step's arithmetic has consumed the old values (the "memory" clobber
+// keeps the shared-memory reads behind the staging barrier).
+template <unsigned kRowBytes>
+__device__ __forceinline__ void advance_cursor(unsigned& af, float& tf, float& vf,
+                                               unsigned& ag, float& tg, float& vg)
+{
+    asm volatile("{\n\t"
+                 ".reg .pred p;\n\t"
+                 "setp.le.f32 p, %1, %4;\n\t"
+                 "@p add.u32 %0, %0, %6;\n\t"
+                 "@p ld.shared.v2.f32 {%1, %2}, [%0];\n\t"
+                 "@!p add.u32 %3, %3, %6;\n\t"
+                 "@!p ld.shared.v2.f32 {%4, %5}, [%3];\n\t"
+                 "}"
+                 : "+r"(af), "+f"(tf), "+f"(vf), "+r"(ag), "+f"(tg), "+f"(vg)
+                 : "n"(kRowBytes)
+                 : "memory");
+}
+
+// float64: the order test runs on the bit patterns (integer pipe).
+template <unsigned kRowBytes>
+__device__ __forceinline__ void advance_cursor(unsigned& af, double& tf, double& vf,
+                                               unsigned& ag, double& tg, double& vg)
+{
+    const long long bf = __double_as_longlong(tf), bg = __double_as_longlong(tg);
+    asm volatile("{\n\t"
+                 ".reg .pred p;\n\t"
+                 "setp.le.s64 p, %6, %7;\n\t"
+                 "@p add.u32 %0, %0, %8;\n\t"
+                 "@p ld.shared.v2.f64 {%1, %2}, [%0];\n\t"
+                 "@!p add.u32 %3, %3, %8;\n\t"
+                 "@!p ld.shared.v2.f64 {%4, %5}, [%3];\n\t"
+                 "}"
+                 : "+r"(af), "+d"(tf), "+d"(vf), "+r"(ag), "+d"(tg), "+d"(vg)
+                 : "l"(bf), "l"(bg), "n"(kRowBytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ float first_end(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double first_end(double a, double b)
+{
+    return __double_as_longlong(a) <= __double_as_longlong(b) ? a : b;
+}
+
 __device__ __forceinline__ double finalize_root(int metric, int root, double p, double I)
 {
     if (!root || metric == PCF_GRAM) return I;
@@ -177,6 +225,7 @@ __global__ void __launch_bounds__(kWalkThreads, 1) walk_kernel(const WalkArgs a)
     const int pg = 32 + my_c;       // tile PCF index of the column side
     const unsigned base_f = (unsigned)(pf >> 4) * regionBytes + (unsigned)(pf & 15) * sizeof(E);
     const unsigned base_g = (unsigned)(pg >> 4) * regionBytes + (unsigned)(pg & 15) * sizeof(E);
+    const unsigned smem_base = (unsigned)__cvta_generic_to_shared(smem);
 
     for (;;) {
         if (tid == 0) sTile = (int64_t)atomicAdd(&a.hdr->tiles, 1ull);
@@ -276,28 +325,19 @@ __global__ void __launch_bounds__(kWalkThreads, 1) walk_kernel(const WalkArgs a)
             // ---- walk this window ----
             if (lane_valid) {
                 int cnt = (sNext[pf] - sS[pf]) + (sNext[pg] - sS[pg]);
-                unsigned af = base_f, ag = base_g;
-                const E ef = *reinterpret_cast<const E*>(smem + af);
-                const E eg = *reinterpret_cast<const E*>(smem + ag);
+                unsigned af = smem_base + base_f, ag = smem_base + base_g;
+                const E ef = *reinterpret_cast<const E*>(smem + base_f);
+                const E eg = *reinterpret_cast<const E*>(smem + base_g);
                 T tf = ef.x, tg = eg.x;
                 vA = ef.y;
                 vB = eg.y;
 #define PCF_WALK_STEP()                                                           \
                 {                                                                 \
-                    const bool adv_f = !ends_after(tf, tg);                       \
-                    const T tn = adv_f ? tf : tg;                                 \
+                    const T tn = first_end(tf, tg);                               \
                     const T dt = tn - tc;                                         \
                     tc = tn;                                                      \
                     accumulate<COMBO, PREC, T>(acc, vA, vB, dt, p0);              \
-                    if (adv_f) {                                                  \
-                        af += kRow;                                               \
-                        const E e = *reinterpret_cast<const E*>(smem + af);       \
-                        tf = e.x; vA = e.y;                                       \
-                    } else {                                                      \
-                        ag += kRow;                                               \
-                        const E e = *reinterpret_cast<const E*>(smem + ag);       \
-                        tg = e.x; vB = e.y;                                       \
-                    }                                                             \
+                    advance_cursor<kRow>(af, tf, vA, ag, tg, vB);                 \
                 }
 #pragma unroll 1
                 for (; cnt >= 8; cnt -= 8) {
