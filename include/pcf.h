@@ -204,6 +204,32 @@ int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root
  */
 int pcf_check(const void* workspace, cudaStream_t stream, int* detail, int64_t* index);
 
+/* Bytes of the fixed device scratch array behind pcf_pairwise_noalloc. */
+#define PCF_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/*
+ * pcf_pairwise without a workspace argument and without any device
+ * allocation, for callers that cannot allocate device memory where they
+ * need the matrices (an operator interface that only hands over input and
+ * output buffers, a service whose device memory budget is fully reserved up
+ * front, code that must not call into the allocator after start-up).  The
+ * paper has no counterpart; this is an interface convenience.
+ *   Same arguments and results as pcf_pairwise with flags = 0, except that
+ *   the scratch is a file-scope device array of PCF_NOALLOC_SCRATCH_BYTES
+ *   inside the library (held on every GPU that loads the library until the
+ *   process exits).  Inputs whose pcf_workspace_size exceeds it return
+ *   PCF_ENOWS before any device work.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current) and caches it; make
+ *   that first call before any stream capture.
+ *   All calls on a device share the array: each call re-initializes what it
+ *   uses, but calls whose GPU work overlaps in time (other streams, other
+ *   host threads) race and give wrong results.  Device-side input errors are
+ *   recorded in the array and are not reported by this entry point.
+ */
+int pcf_pairwise_noalloc(const pcf_csr* x, const pcf_integral* F, int nF, int precision,
+                         int layout, int out_dtype, cudaStream_t stream);
+
 /* Static text for a status code. */
 const char* pcf_status_string(int status);
 

@@ -32,7 +32,8 @@ ERR_DETAIL = {
 }
 
 SYMBOLS = ("pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross", "pcf_pairwise_backward",
-           "pcf_check", "pcf_status_string", "pcf_version")
+           "pcf_check", "pcf_status_string", "pcf_version", "pcf_pairwise_noalloc")
+PCF_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class PcfCsr(ctypes.Structure):
@@ -87,6 +88,8 @@ def load(build_if_missing: bool = False):
         lib.pcf_check.argtypes = [P, P, ctypes.POINTER(I), ctypes.POINTER(I64)]
         lib.pcf_status_string.restype = ctypes.c_char_p
         lib.pcf_status_string.argtypes = [I]
+        lib.pcf_pairwise_noalloc.restype = I
+        lib.pcf_pairwise_noalloc.argtypes = [CSR, INT, I, I, I, I, P]
         lib.pcf_version.restype = ctypes.c_char_p
         lib.pcf_version.argtypes = []
         _lib = lib
