@@ -218,7 +218,14 @@ def run_ours(args):
         return [torch.empty((N, N), dtype=torch.float32, device=f"cuda:{local}") for _ in METRICS]
 
     results = {}
+    tuned = {}
     for prec in (args.precision, "f64") if not args.no_fp64 else (args.precision,):
+        if args.schedule:
+            sched = args.schedule
+        else:
+            from paper_2404_07183_gb300 import autotune
+            sched, timings = autotune.tune_pairwise(x, METRICS, prec, repeats=1)
+            tuned[prec] = {"schedule": sched, "timings_ms": timings}
         outs = make_outs()
         ws = torch.empty(P.pcf_workspace_size(x, None, prec), dtype=torch.uint8,
                          device=f"cuda:{local}")
@@ -228,7 +235,7 @@ def run_ours(args):
             e_mid = torch.cuda.Event(enable_timing=True)
             e_mid.record(stream)
             P.pcf_pairwise(x, METRICS, precision=prec, out=outs, workspace=ws, prepared=True,
-                           check=False)
+                           check=False, schedule=sched)
             return e_mid
 
         steps = args.steps if prec == args.precision else max(1, min(args.steps, 2))
@@ -265,7 +272,8 @@ def run_ours(args):
             t = torch.tensor([tot], device=f"cuda:{local}", dtype=torch.float64)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             tot = float(t.item())
-        results[prec] = {"ms_per_step": tot / steps, "walk_ms": float(np.mean(walk_ms)),
+        results[prec] = {"schedule": sched, "ms_per_step": tot / steps,
+                         "walk_ms": float(np.mean(walk_ms)),
                          "prepare_ms": float(np.mean([a.elapsed_time(b) for a, b, c in evs])),
                          "steps": steps, "wall_s": t_wall, "clocks": clocks}
         del outs, ws
@@ -290,7 +298,8 @@ def run_ours(args):
         for d, h in zip(dev_in, host_in):
             d.copy_(h, non_blocking=True)
         xd = P.PcfTensors(*dev_in)
-        P.pcf_pairwise(xd, METRICS, precision=prec, out=outs, workspace=ws, check=False)
+        P.pcf_pairwise(xd, METRICS, precision=prec, out=outs, workspace=ws, check=False,
+                       schedule=results[prec]["schedule"])
         for h, o in zip(host_out, outs):
             h.copy_(o, non_blocking=True)
 
@@ -329,7 +338,8 @@ def run_ours(args):
                    "layout": "full N x N", "out_dtype": "f32",
                    "pair_integrals_per_step": pairs, "merge_steps_per_step": walk_steps + diag_steps,
                    "l2": "flushed by a 256 MiB write before each timed step (outside the timing)",
-                   "parallelism": f"{world} independent replicas (one per GPU)"},
+                   "parallelism": f"{world} independent replicas (one per GPU)",
+                   "schedule": head["schedule"], "autotune": tuned or None},
         "merge_steps_per_s": world * (walk_steps + diag_steps) / (head["ms_per_step"] * 1e-3),
         "walk": {"ms": head["walk_ms"], "prepare_ms": head["prepare_ms"],
                  "merge_steps_per_s": walk_rate},
@@ -476,6 +486,8 @@ def run_workload(name, args):
         pairs = N * (N + 1) // 2
         o = [torch.empty((pairs,), dtype=torch.float32, device=dev)]
         res = {}
+        from paper_2404_07183_gb300 import autotune
+        sched, tune_ms = autotune.tune_pairwise(x, ["gram"], "f32c", layout="upper", repeats=1)
         for prec in ("f32c", "f32"):
             ws = torch.empty(P.pcf_workspace_size(x, None, prec), dtype=torch.uint8, device=dev)
             mids = []
@@ -486,7 +498,7 @@ def run_workload(name, args):
                 e.record(stream)
                 mids.append(e)
                 P.pcf_pairwise(x, ["gram"], precision=prec, layout="upper", out=o, workspace=ws,
-                               prepared=True, check=False)
+                               prepared=True, check=False, schedule=sched)
             ms = _timed(step, max(1, min(args.steps, 2)), 1, flush, stream)
             P.pcf_check(ws)
             res[prec] = float(np.mean(ms))
@@ -499,7 +511,8 @@ def run_workload(name, args):
                      {"workload": "lognormal N=100000 n=clip(round(LogNormal(ln100,1)),2,10000) "
                                   "Exp(1) N(0,1) float32, L2 Gram upper triangle (packed, f32)",
                       "N": N, "nnz": s.nnz, "max_len": int(s.lengths().max()), "pairs": pairs,
-                      "merge_steps": steps_walk + diag, "l2": "flushed between steps"},
+                      "merge_steps": steps_walk + diag, "l2": "flushed between steps",
+                      "schedule": sched, "autotune_ms": tune_ms},
                      merge_steps_per_s=rate,
                      roofline={"bound": "alu", "achieved": rate, "peak": issue(tally),
                                "unit": "merge-steps/s", "frac": rate / issue(tally),
@@ -604,6 +617,9 @@ def main():
     ap.add_argument("--n", type=int, default=None,
                     help="smaller stable-rank collection (profiling runs); default 20000")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--schedule", default=None,
+                    choices=["tile1024", "tile512x2", "mergepath", "auto"],
+                    help="force a walk schedule instead of autotuning it")
     ap.add_argument("--workload", default="stable_rank",
                     choices=["stable_rank", "uniform_small", "lognormal", "gradient", "euler", "all"])
     args = ap.parse_args()

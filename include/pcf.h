@@ -100,6 +100,32 @@ enum pcf_cross_flags {
                               the same B, precision and workspace */
 };
 
+/* Work decomposition of the walk (pcf_pairwise_ex / pcf_cross_ex).
+ *   PCF_SCHED_TILE_1024   32 x 32 pair tiles, one 1024-thread CTA per SM
+ *   PCF_SCHED_TILE_512X2  32 x 32 pair tiles, two 512-thread CTAs per SM
+ *                         (half the shared memory each: smaller windows)
+ *   PCF_SCHED_MERGEPATH   one warp per pair, the pair's merge split across
+ *                         the 32 lanes (for few, long pairs)
+ *   PCF_SCHED_AUTO        merge path when there are fewer tiles than half the
+ *                         SMs, else TILE_1024 */
+enum pcf_sched_kernel {
+    PCF_SCHED_AUTO = 0, PCF_SCHED_TILE_1024 = 1, PCF_SCHED_TILE_512X2 = 2,
+    PCF_SCHED_MERGEPATH = 3
+};
+
+typedef struct pcf_schedule {
+    int32_t kernel;       /* enum pcf_sched_kernel */
+    int32_t window;       /* tile kernels: elements staged per PCF per window,
+                             8 <= window <= the shared-memory maximum; 0 = max */
+    int32_t shard_index;  /* multi-GPU split of one call: this call computes
+                             only work units u (tiles; pairs for the merge
+                             path, in the queue order) with
+                             u % shard_count == shard_index and writes only
+                             their entries; 0 <= shard_index < shard_count */
+    int32_t shard_count;  /* 0 or 1: the whole matrix */
+    int32_t reserved[4];  /* must be 0 */
+} pcf_schedule;
+
 /* A collection of N PCFs in CSR form (device arrays, read only).
  *   offsets[N+1] (int64): PCF i owns entries [offsets[i], offsets[i+1]);
  *                         offsets[0] = 0, offsets[N] = nnz, every PCF n_i >= 1.
@@ -157,6 +183,16 @@ int pcf_pairwise(const pcf_csr* x, const pcf_integral* F, int nF, int precision,
                  size_t workspace_bytes, cudaStream_t stream);
 
 /*
+ * pcf_pairwise with an explicit work decomposition (NULL = PCF_SCHED_AUTO).
+ * Results are identical for every schedule up to the summation order of the
+ * merge-path kernel (which combines 32 partial sums).  An unknown kernel or a
+ * window outside its range returns PCF_EINVAL.
+ */
+int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precision,
+                    int layout, int out_dtype, int flags, const pcf_schedule* schedule,
+                    void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/*
  * Cross matrices between rows [row_begin, row_end) of collection a and all of
  * collection b (the pairwise matrix of Sec. 3.1 taken between two sets).
  * Output k is a (row_end - row_begin) x b->n row-major block with leading
@@ -168,6 +204,12 @@ int pcf_cross(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row
               const pcf_integral* F, int nF, int precision, int64_t ld_out,
               int out_dtype, int flags, void* workspace, size_t workspace_bytes,
               cudaStream_t stream);
+
+/* pcf_cross with an explicit work decomposition (NULL = PCF_SCHED_AUTO). */
+int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row_end,
+                 const pcf_integral* F, int nF, int precision, int64_t ld_out,
+                 int out_dtype, int flags, const pcf_schedule* schedule, void* workspace,
+                 size_t workspace_bytes, cudaStream_t stream);
 
 /*
  * Gradient of L = sum_{i,j} G_ij F_ij, F the FULL pairwise matrix of `metric`

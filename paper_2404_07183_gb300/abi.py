@@ -32,7 +32,9 @@ ERR_DETAIL = {
 }
 
 SYMBOLS = ("pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross", "pcf_pairwise_backward",
-           "pcf_check", "pcf_status_string", "pcf_version", "pcf_pairwise_noalloc")
+           "pcf_check", "pcf_status_string", "pcf_version", "pcf_pairwise_noalloc",
+           "pcf_pairwise_ex", "pcf_cross_ex")
+PCF_SCHED_AUTO, PCF_SCHED_TILE_1024, PCF_SCHED_TILE_512X2, PCF_SCHED_MERGEPATH = 0, 1, 2, 3
 PCF_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -41,6 +43,12 @@ class PcfCsr(ctypes.Structure):
                 ("offsets", ctypes.c_void_p), ("times", ctypes.c_void_p),
                 ("values", ctypes.c_void_p), ("dtype", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class PcfSchedule(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("window", ctypes.c_int32),
+                ("shard_index", ctypes.c_int32), ("shard_count", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class PcfIntegral(ctypes.Structure):
@@ -78,6 +86,11 @@ def load(build_if_missing: bool = False):
         lib.pcf_workspace_size.argtypes = [CSR, CSR, I, I, ctypes.POINTER(SZ)]
         lib.pcf_pairwise.restype = I
         lib.pcf_pairwise.argtypes = [CSR, INT, I, I, I, I, I, P, SZ, P]
+        SCH = ctypes.POINTER(PcfSchedule)
+        lib.pcf_pairwise_ex.restype = I
+        lib.pcf_pairwise_ex.argtypes = [CSR, INT, I, I, I, I, I, SCH, P, SZ, P]
+        lib.pcf_cross_ex.restype = I
+        lib.pcf_cross_ex.argtypes = [CSR, CSR, I64, I64, INT, I, I, I64, I, I, SCH, P, SZ, P]
         lib.pcf_prepare.restype = I
         lib.pcf_prepare.argtypes = [CSR, I, P, SZ, P]
         lib.pcf_cross.restype = I

@@ -97,6 +97,27 @@ def parse_metric(m):
     return code, p, root
 
 
+SCHEDULES = {"auto": abi.PCF_SCHED_AUTO, "tile1024": abi.PCF_SCHED_TILE_1024,
+             "tile512x2": abi.PCF_SCHED_TILE_512X2, "mergepath": abi.PCF_SCHED_MERGEPATH}
+
+
+def _schedule(schedule, shard=None):
+    """None | name | (name, window), plus an optional (shard_index,
+    shard_count) -> PcfSchedule pointer or None."""
+    if schedule is None and shard is None:
+        return None
+    if schedule is None:
+        schedule = ("auto", 0)
+    if isinstance(schedule, str):
+        schedule = (schedule, 0)
+    sc = abi.PcfSchedule()
+    sc.kernel = SCHEDULES[schedule[0]]
+    sc.window = int(schedule[1])
+    if shard is not None:
+        sc.shard_index, sc.shard_count = int(shard[0]), int(shard[1])
+    return ctypes.byref(sc)
+
+
 def _stream_handle(stream):
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
@@ -164,7 +185,7 @@ def pcf_prepare(x: PcfTensors, precision="f32c", workspace=None, stream=None):
 
 def pcf_pairwise(x: PcfTensors, metrics=("l1",), precision="f32c", layout="full",
                  out_dtype=torch.float32, out=None, workspace=None, stream=None,
-                 check=True, prepared=False):
+                 check=True, prepared=False, schedule=None, shard=None):
     """Pairwise matrices F(C) (Sec. 3.1) of ``x`` for each requested metric.
 
     Returns a list of tensors: N x N (layout "full") or N(N+1)/2 ("upper")."""
@@ -184,9 +205,10 @@ def pcf_pairwise(x: PcfTensors, metrics=("l1",), precision="f32c", layout="full"
     od = abi.PCF_F64 if out[0].dtype == torch.float64 else abi.PCF_F32
     if prepared and workspace is None:
         raise ValueError("prepared=True needs the workspace returned by pcf_prepare")
-    rc = lib.pcf_pairwise(ctypes.byref(cx), req, len(metrics), _prec(precision), lay, od,
-                          abi.PCF_PAIRWISE_PREPARED if prepared else 0,
-                          ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream))
+    rc = lib.pcf_pairwise_ex(ctypes.byref(cx), req, len(metrics), _prec(precision), lay, od,
+                             abi.PCF_PAIRWISE_PREPARED if prepared else 0,
+                             _schedule(schedule, shard),
+                             ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream))
     if rc != abi.PCF_OK:
         raise PcfError(rc, "pcf_pairwise")
     if check:
@@ -196,7 +218,8 @@ def pcf_pairwise(x: PcfTensors, metrics=("l1",), precision="f32c", layout="full"
 
 def pcf_cross(a: PcfTensors, b: PcfTensors, row_begin=0, row_end=None, metrics=("l1",),
               precision="f32c", out_dtype=torch.float32, out=None, ld_out=None,
-              reuse_b=False, workspace=None, stream=None, check=True):
+              reuse_b=False, workspace=None, stream=None, check=True, schedule=None,
+              shard=None):
     """Rows [row_begin, row_end) of the cross matrices a x b."""
     lib = abi.load()
     if isinstance(metrics, (str, tuple)):
@@ -212,10 +235,10 @@ def pcf_cross(a: PcfTensors, b: PcfTensors, row_begin=0, row_end=None, metrics=(
     ca, cb = a.csr(), b.csr()
     req = _requests(metrics, out)
     od = abi.PCF_F64 if out[0].dtype == torch.float64 else abi.PCF_F32
-    rc = lib.pcf_cross(ctypes.byref(ca), ctypes.byref(cb), int(row_begin), int(row_end), req,
-                       len(metrics), _prec(precision), int(ld), od,
-                       abi.PCF_CROSS_REUSE_B if reuse_b else 0,
-                       ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream))
+    rc = lib.pcf_cross_ex(ctypes.byref(ca), ctypes.byref(cb), int(row_begin), int(row_end), req,
+                          len(metrics), _prec(precision), int(ld), od,
+                          abi.PCF_CROSS_REUSE_B if reuse_b else 0, _schedule(schedule, shard),
+                          ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream))
     if rc != abi.PCF_OK:
         raise PcfError(rc, "pcf_cross")
     if check:

@@ -141,18 +141,56 @@ int check_requests(const pcf_integral* F, int nF, bool need_out)
     return PCF_OK;
 }
 
-int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int elem_bytes,
-              cudaStream_t s)
+int check_schedule(const pcf_schedule* sc)
 {
-    const int optin = device_smem_optin();
-    int W = (int)((optin - 4096) / (4 * kGroup * elem_bytes));
-    if (W > 4096) W = 4096;
-    if (W < 8) return PCF_ECUDA;
-    wa.window = W;
-    const size_t smem = walk_smem_bytes(W, elem_bytes);
-    int64_t grid = device_sm_count();
-    if (grid > wa.ntiles) grid = wa.ntiles;
-    if (grid < 1) return PCF_OK;
+    if (!sc) return PCF_OK;
+    if (sc->kernel < PCF_SCHED_AUTO || sc->kernel > PCF_SCHED_MERGEPATH) return PCF_EINVAL;
+    if (sc->window != 0 && sc->window < 8) return PCF_EINVAL;
+    if (sc->shard_count < 0 || sc->shard_index < 0) return PCF_EINVAL;
+    if (sc->shard_count > 1 && sc->shard_index >= sc->shard_count) return PCF_EINVAL;
+    if (sc->shard_count <= 1 && sc->shard_index != 0) return PCF_EINVAL;
+    for (int k = 0; k < 4; ++k) if (sc->reserved[k] != 0) return PCF_EINVAL;
+    return PCF_OK;
+}
+
+int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int elem_bytes,
+              const pcf_schedule* sched, cudaStream_t s)
+{
+    const int sms = device_sm_count();
+    wa.shard_count = (sched && sched->shard_count > 1) ? sched->shard_count : 1;
+    wa.shard_index = (sched && sched->shard_count > 1) ? sched->shard_index : 0;
+    int kernel = sched ? sched->kernel : PCF_SCHED_AUTO;
+    if (kernel == PCF_SCHED_AUTO)
+        kernel = (wa.ntiles * 2 < sms) ? PCF_SCHED_MERGEPATH : PCF_SCHED_TILE_1024;
+
+    int64_t grid = 0;
+    size_t smem = 0;
+    int64_t npairs = 0;
+    if (kernel == PCF_SCHED_MERGEPATH) {
+        npairs = wa.symmetric ? wa.n_r * (wa.n_r + 1) / 2 : wa.n_r * wa.n_c;
+        grid = (int64_t)sms * 4;
+        const int64_t need = (npairs + 7) / 8;    // 8 warps per block
+        if (grid > need) grid = need;
+        if (grid < 1) return PCF_OK;
+    } else {
+        const int ctas = kernel == PCF_SCHED_TILE_512X2 ? 2 : 1;
+        int dev = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        long budget = (long)per_sm / ctas - 1024 - 2048;       // per-CTA reserve + static
+        const long optin = (long)device_smem_optin() - 2048;
+        if (budget > optin) budget = optin;
+        int Wmax = (int)(budget / (4L * kGroup * elem_bytes));
+        if (Wmax > 4096) Wmax = 4096;
+        int W = (sched && sched->window) ? sched->window : Wmax;
+        if (W > Wmax) return PCF_EINVAL;
+        if (W < 8) return PCF_ECUDA;
+        wa.window = W;
+        smem = walk_smem_bytes(W, elem_bytes);
+        grid = (int64_t)sms * ctas;
+        if (grid > wa.ntiles) grid = wa.ntiles;
+        if (grid < 1) return PCF_OK;
+    }
     for (const Launch& L : plan(F, nF)) {
         wa.nout = L.n;
         for (int k = 0; k < L.n; ++k) {
@@ -164,9 +202,20 @@ int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int el
         }
         reset_tiles_kernel<<<1, 1, 0, s>>>(wa.hdr);
         cudaError_t e;
-        if (precision == PCF_PREC_F64) e = launch_walk_f64(L.combo, wa, (int)grid, smem, s);
-        else if (precision == PCF_PREC_F32_COMP) e = launch_walk_f32c(L.combo, wa, (int)grid, smem, s);
-        else e = launch_walk_f32(L.combo, wa, (int)grid, smem, s);
+        const int g = (int)grid;
+        if (kernel == PCF_SCHED_MERGEPATH) {
+            if (precision == PCF_PREC_F64) e = launch_mergepath_f64(L.combo, wa, npairs, g, s);
+            else if (precision == PCF_PREC_F32_COMP) e = launch_mergepath_f32c(L.combo, wa, npairs, g, s);
+            else e = launch_mergepath_f32(L.combo, wa, npairs, g, s);
+        } else if (kernel == PCF_SCHED_TILE_512X2) {
+            if (precision == PCF_PREC_F64) e = launch_walk_f64_t512(L.combo, wa, g, smem, s);
+            else if (precision == PCF_PREC_F32_COMP) e = launch_walk_f32c_t512(L.combo, wa, g, smem, s);
+            else e = launch_walk_f32_t512(L.combo, wa, g, smem, s);
+        } else {
+            if (precision == PCF_PREC_F64) e = launch_walk_f64_t1024(L.combo, wa, g, smem, s);
+            else if (precision == PCF_PREC_F32_COMP) e = launch_walk_f32c_t1024(L.combo, wa, g, smem, s);
+            else e = launch_walk_f32_t1024(L.combo, wa, g, smem, s);
+        }
         if (e != cudaSuccess) return PCF_ECUDA;
     }
     return PCF_OK;
@@ -226,11 +275,20 @@ int pcf_pairwise(const pcf_csr* x, const pcf_integral* F, int nF, int precision,
                  int out_dtype, int flags, void* workspace, size_t workspace_bytes,
                  cudaStream_t stream)
 {
+    return pcf_pairwise_ex(x, F, nF, precision, layout, out_dtype, flags, nullptr, workspace,
+                           workspace_bytes, stream);
+}
+
+int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precision, int layout,
+                    int out_dtype, int flags, const pcf_schedule* schedule, void* workspace,
+                    size_t workspace_bytes, cudaStream_t stream)
+{
     if (!csr_ok(x)) return PCF_EINVAL;
     if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32) return PCF_EINVAL;
     if (layout != PCF_OUT_FULL && layout != PCF_OUT_UPPER_PACKED) return PCF_EINVAL;
     if (out_dtype != PCF_F32 && out_dtype != PCF_F64) return PCF_EINVAL;
     if (flags & ~PCF_PAIRWISE_PREPARED) return PCF_EINVAL;
+    if (check_schedule(schedule) != PCF_OK) return PCF_EINVAL;
     int rc = check_requests(F, nF, x->n > 0);
     if (rc != PCF_OK) return rc;
     Header* hdr;
@@ -260,12 +318,21 @@ int pcf_pairwise(const pcf_csr* x, const pcf_integral* F, int nF, int precision,
     wa.layout = layout;
     wa.out_f64 = out_dtype == PCF_F64;
     wa.ld_out = x->n;
-    return run_walks(wa, F, nF, precision, es, stream);
+    return run_walks(wa, F, nF, precision, es, schedule, stream);
 }
 
 int pcf_cross(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row_end,
               const pcf_integral* F, int nF, int precision, int64_t ld_out, int out_dtype,
               int flags, void* workspace, size_t workspace_bytes, cudaStream_t stream)
+{
+    return pcf_cross_ex(a, b, row_begin, row_end, F, nF, precision, ld_out, out_dtype, flags,
+                        nullptr, workspace, workspace_bytes, stream);
+}
+
+int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row_end,
+                 const pcf_integral* F, int nF, int precision, int64_t ld_out, int out_dtype,
+                 int flags, const pcf_schedule* schedule, void* workspace,
+                 size_t workspace_bytes, cudaStream_t stream)
 {
     if (!csr_ok(a) || !csr_ok(b)) return PCF_EINVAL;
     if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32) return PCF_EINVAL;
@@ -273,6 +340,7 @@ int pcf_cross(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row
     if (row_begin < 0 || row_end < row_begin || row_end > a->n) return PCF_EINVAL;
     if (ld_out < b->n) return PCF_EINVAL;
     if (flags & ~PCF_CROSS_REUSE_B) return PCF_EINVAL;
+    if (check_schedule(schedule) != PCF_OK) return PCF_EINVAL;
     const int64_t rows = row_end - row_begin;
     int rc = check_requests(F, nF, rows > 0 && b->n > 0);
     if (rc != PCF_OK) return rc;
@@ -313,7 +381,7 @@ int pcf_cross(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row
     wa.layout = PCF_OUT_FULL;
     wa.out_f64 = out_dtype == PCF_F64;
     wa.ld_out = ld_out;
-    return run_walks(wa, F, nF, precision, es, stream);
+    return run_walks(wa, F, nF, precision, es, schedule, stream);
 }
 
 int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root,

@@ -103,6 +103,8 @@ struct WalkArgs {
     int layout;              // pcf_layout (pairwise) ; cross always dense block
     int out_f64;
     int64_t ld_out;          // cross: leading dimension; pairwise: N
+    int64_t shard_index;     // this launch owns units u with u % shard_count == shard_index
+    int64_t shard_count;     // >= 1
 };
 
 // Metric combination codes compiled into the walk kernels.
@@ -111,10 +113,16 @@ enum Combo : int {
     kComboL1L2Gram = 5, kComboL1L2L3 = 6, kComboCount = 7
 };
 
-// Launch the persistent tile walk for one precision and metric combination.
-cudaError_t launch_walk_f64(int combo, const WalkArgs& a, int grid, size_t smem, cudaStream_t s);
-cudaError_t launch_walk_f32c(int combo, const WalkArgs& a, int grid, size_t smem, cudaStream_t s);
-cudaError_t launch_walk_f32(int combo, const WalkArgs& a, int grid, size_t smem, cudaStream_t s);
+// Launch the persistent tile walk for one precision, CTA size and metric
+// combination, or the warp-per-pair merge-path walk over `npairs` pairs.
+#define PCF_DECL_WALK(name)                                                                     \
+    cudaError_t launch_walk_##name##_t1024(int, const WalkArgs&, int, size_t, cudaStream_t);    \
+    cudaError_t launch_walk_##name##_t512(int, const WalkArgs&, int, size_t, cudaStream_t);     \
+    cudaError_t launch_mergepath_##name(int, const WalkArgs&, int64_t, int, cudaStream_t);
+PCF_DECL_WALK(f64)
+PCF_DECL_WALK(f32c)
+PCF_DECL_WALK(f32)
+#undef PCF_DECL_WALK
 size_t walk_smem_bytes(int window, int elem_bytes);
 
 // Adjoint.

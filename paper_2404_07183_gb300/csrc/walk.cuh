@@ -198,12 +198,18 @@ __device__ __forceinline__ void decode_tile(const WalkArgs& a, int64_t t, int64_
     }
 }
 
-template <typename T, int PREC, int COMBO>
-__global__ void __launch_bounds__(kWalkThreads, 1) walk_kernel(const WalkArgs a)
+// THREADS = 1024: one CTA per SM, warp w walks diagonal w of each tile.
+// THREADS = 512: two CTAs per SM (each with half the shared memory, so a
+// smaller window), warp w walks diagonals w and w + 16 one after the other.
+template <typename T, int PREC, int COMBO, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const WalkArgs a)
 {
     using E = typename ElemOf<T>::type;
     constexpr int NM = combo_n(COMBO);
+    constexpr int NWARPS = THREADS / 32;
+    constexpr int PAIRS = 32 / NWARPS;              // diagonals per warp
     constexpr unsigned kRow = kGroup * sizeof(E);   // bytes between element k and k+1 of a PCF
+    static_assert(THREADS % 64 == 0 && THREADS <= 1024, "thread count");
 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int32_t sS[kTilePcfs], sNext[kTilePcfs], sLen[kTilePcfs];
@@ -217,18 +223,13 @@ __global__ void __launch_bounds__(kWalkThreads, 1) walk_kernel(const WalkArgs a)
     const int W = a.window;
     const unsigned regionBytes = (unsigned)W * kRow;
     const T p0 = (T)a.p[0];
-
-    // this lane's pair inside every tile: row (lane + warp) & 31, column lane
-    const int my_r = (lane + warp) & 31;
-    const int my_c = lane;
-    const int pf = my_r;            // tile PCF index of the row side
-    const int pg = 32 + my_c;       // tile PCF index of the column side
-    const unsigned base_f = (unsigned)(pf >> 4) * regionBytes + (unsigned)(pf & 15) * sizeof(E);
-    const unsigned base_g = (unsigned)(pg >> 4) * regionBytes + (unsigned)(pg & 15) * sizeof(E);
     const unsigned smem_base = (unsigned)__cvta_generic_to_shared(smem);
+    const E* packR = reinterpret_cast<const E*>(a.pack_r);
+    const E* packC = reinterpret_cast<const E*>(a.pack_c);
 
     for (;;) {
-        if (tid == 0) sTile = (int64_t)atomicAdd(&a.hdr->tiles, 1ull);
+        if (tid == 0)
+            sTile = a.shard_index + (int64_t)atomicAdd(&a.hdr->tiles, 1ull) * a.shard_count;
         __syncthreads();
         const int64_t t = sTile;
         if (t >= a.ntiles) break;
@@ -249,12 +250,12 @@ __global__ void __launch_bounds__(kWalkThreads, 1) walk_kernel(const WalkArgs a)
             }
             sS[tid] = 0;
         }
-        const bool lane_valid = (bi * kTile + my_r < a.n_r) && (bj * kTile + my_c < a.n_c);
 
-        Acc<PREC> acc[NM];
+        Acc<PREC> acc[PAIRS][NM];
+        T tcq[PAIRS];
+#pragma unroll
+        for (int q = 0; q < PAIRS; ++q) tcq[q] = T(0);
         T T0 = T(0);            // start of the current window (block-uniform)
-        T tc = T(0);
-        T vA = T(0), vB = T(0);
         __syncthreads();
 
         for (;;) {
@@ -265,8 +266,7 @@ __global__ void __launch_bounds__(kWalkThreads, 1) walk_kernel(const WalkArgs a)
                 if (len > 0) {
                     int idx = sS[tid] + W - 1;
                     if (idx > len - 1) idx = len - 1;
-                    const E* src = reinterpret_cast<const E*>(tid < 32 ? a.pack_r : a.pack_c);
-                    cand = src[sOff[tid] + idx].x;
+                    cand = (tid < 32 ? packR : packC)[sOff[tid] + idx].x;
                 }
                 for (int o = 16; o > 0; o >>= 1) {
                     T other = __shfl_xor_sync(0xffffffffu, cand, o);
@@ -284,20 +284,21 @@ __global__ void __launch_bounds__(kWalkThreads, 1) walk_kernel(const WalkArgs a)
             }
 
             // ---- stage elements [S, S + min(W, len - S)) of all 64 PCFs ----
+            // THREADS is a multiple of 16, so a thread always serves the same
+            // slot (tid & 15) of each region and walks k in steps of THREADS/16.
             {
-                const int per_region = W * kGroup;
-                for (int q = tid; q < 4 * per_region; q += kWalkThreads) {
-                    const int region = q / per_region;
-                    const int r = q - region * per_region;
-                    const int k = r >> 4;
-                    const int p = region * kGroup + (r & 15);
+                const int slot = tid & 15;
+#pragma unroll 1
+                for (int region = 0; region < 4; ++region) {
+                    const int p = region * kGroup + slot;
                     const int len = sLen[p];
                     const int S = sS[p];
-                    if (S + k < len) {
-                        const E* src = reinterpret_cast<const E*>(p < 32 ? a.pack_r : a.pack_c);
-                        E e = src[sOff[p] + S + k];
-                        *reinterpret_cast<E*>(smem + (unsigned)region * regionBytes + (unsigned)r * sizeof(E)) = e;
-                    }
+                    int kend = len - S;
+                    if (kend > W) kend = W;
+                    const E* src = (region < 2 ? packR : packC) + sOff[p] + S;
+                    unsigned char* dst = smem + (unsigned)region * regionBytes + (unsigned)slot * sizeof(E);
+                    for (int k = tid >> 4; k < kend; k += THREADS / 16)
+                        *reinterpret_cast<E*>(dst + (unsigned)k * kRow) = src[k];
                 }
             }
             __syncthreads();
@@ -322,31 +323,40 @@ __global__ void __launch_bounds__(kWalkThreads, 1) walk_kernel(const WalkArgs a)
             }
             __syncthreads();
 
-            // ---- walk this window ----
-            if (lane_valid) {
+            // ---- walk this window: this lane's PAIRS pairs, one after the other ----
+#pragma unroll
+            for (int q = 0; q < PAIRS; ++q) {
+                const int my_r = (lane + warp + q * NWARPS) & 31;
+                const int pf = my_r, pg = 32 + lane;
+                if (bi * kTile + my_r >= a.n_r || bj * kTile + lane >= a.n_c) continue;
                 int cnt = (sNext[pf] - sS[pf]) + (sNext[pg] - sS[pg]);
+                const unsigned base_f = (unsigned)(pf >> 4) * regionBytes + (unsigned)(pf & 15) * sizeof(E);
+                const unsigned base_g = (unsigned)(pg >> 4) * regionBytes + (unsigned)(pg & 15) * sizeof(E);
                 unsigned af = smem_base + base_f, ag = smem_base + base_g;
                 const E ef = *reinterpret_cast<const E*>(smem + base_f);
                 const E eg = *reinterpret_cast<const E*>(smem + base_g);
-                T tf = ef.x, tg = eg.x;
-                vA = ef.y;
-                vB = eg.y;
+                T tf = ef.x, tg = eg.x, vf = ef.y, vg = eg.y;
+                T tc = tcq[q];
+                Acc<PREC>* ac = acc[q];
 #define PCF_WALK_STEP()                                                           \
                 {                                                                 \
                     const T tn = first_end(tf, tg);                               \
                     const T dt = tn - tc;                                         \
                     tc = tn;                                                      \
-                    accumulate<COMBO, PREC, T>(acc, vA, vB, dt, p0);              \
-                    advance_cursor<kRow>(af, tf, vA, ag, tg, vB);                 \
+                    accumulate<COMBO, PREC, T>(ac, vf, vg, dt, p0);               \
+                    advance_cursor<kRow>(af, tf, vf, ag, tg, vg);                 \
                 }
 #pragma unroll 1
-                for (; cnt >= 8; cnt -= 8) {
+                for (; cnt >= 16; cnt -= 16) {
+                    PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
+                    PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
                     PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
                     PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
                 }
 #pragma unroll 1
                 for (; cnt > 0; --cnt) PCF_WALK_STEP()
 #undef PCF_WALK_STEP
+                tcq[q] = tc;
             }
             const bool last = !(T1 < T(INFINITY));
             __syncthreads();
@@ -357,17 +367,20 @@ __global__ void __launch_bounds__(kWalkThreads, 1) walk_kernel(const WalkArgs a)
         }
 
         // ---- tail, root, output ----
-        if (lane_valid) {
-            const int64_t gi = bi * kTile + my_r, gj = bj * kTile + my_c;
+#pragma unroll
+        for (int q = 0; q < PAIRS; ++q) {
+            const int my_r = (lane + warp + q * NWARPS) & 31;
+            const int64_t gi = bi * kTile + my_r, gj = bj * kTile + lane;
+            if (gi >= a.n_r || gj >= a.n_c) continue;
             const int64_t i = a.perm_r[gi], j = a.perm_c[gj];
-            const T dlast = vA - vB;
+            // values on the last intervals [t_last, inf) of both PCFs
+            const T vlf = packR[sOff[my_r] + sLen[my_r] - 1].y;
+            const T vlg = packC[sOff[32 + lane] + sLen[32 + lane] - 1].y;
 #pragma unroll
             for (int m = 0; m < NM; ++m) {
                 const int MI = combo_metric(COMBO, m);
-                double I = acc[m].value();
-                T h;
-                if (MI == MI_GRAM) h = vA * vB;
-                else h = fabs(dlast);
+                double I = acc[q][m].value();
+                const T h = (MI == MI_GRAM) ? vlf * vlg : fabs(vlf - vlg);
                 if (h != T(0)) I = (h > T(0)) ? (double)INFINITY : -(double)INFINITY;
                 const double F = finalize_root(a.metric[m], a.root[m], a.p[m], I);
                 void* out = a.out[m];
@@ -391,23 +404,23 @@ __global__ void __launch_bounds__(kWalkThreads, 1) walk_kernel(const WalkArgs a)
     }
 }
 
-template <typename T, int PREC>
-cudaError_t launch_walk_t(int combo, const WalkArgs& a, int grid, size_t smem, cudaStream_t s)
+template <typename T, int PREC, int THREADS>
+cudaError_t launch_walk_tt(int combo, const WalkArgs& a, int grid, size_t smem, cudaStream_t s)
 {
     auto go = [&](auto kern) -> cudaError_t {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        kern<<<grid, kWalkThreads, smem, s>>>(a);
+        kern<<<grid, THREADS, smem, s>>>(a);
         return cudaGetLastError();
     };
     switch (combo) {
-    case kComboL1: return go(walk_kernel<T, PREC, kComboL1>);
-    case kComboL2: return go(walk_kernel<T, PREC, kComboL2>);
-    case kComboGram: return go(walk_kernel<T, PREC, kComboGram>);
-    case kComboLP: return go(walk_kernel<T, PREC, kComboLP>);
-    case kComboL3: return go(walk_kernel<T, PREC, kComboL3>);
-    case kComboL1L2Gram: return go(walk_kernel<T, PREC, kComboL1L2Gram>);
-    case kComboL1L2L3: return go(walk_kernel<T, PREC, kComboL1L2L3>);
+    case kComboL1: return go(walk_kernel<T, PREC, kComboL1, THREADS>);
+    case kComboL2: return go(walk_kernel<T, PREC, kComboL2, THREADS>);
+    case kComboGram: return go(walk_kernel<T, PREC, kComboGram, THREADS>);
+    case kComboLP: return go(walk_kernel<T, PREC, kComboLP, THREADS>);
+    case kComboL3: return go(walk_kernel<T, PREC, kComboL3, THREADS>);
+    case kComboL1L2Gram: return go(walk_kernel<T, PREC, kComboL1L2Gram, THREADS>);
+    case kComboL1L2L3: return go(walk_kernel<T, PREC, kComboL1L2L3, THREADS>);
     default: return cudaErrorInvalidValue;
     }
 }
