@@ -41,6 +41,21 @@ TALLY = {"f32c": 5 + 1 + (1 + 3) + (2 + 3) + (2 + 3), "f32": 5 + 1 + 1 + 2 + 2,
          "f64": 5 + 1 + 1 + 2 + 2}
 FP64_OPS_PER_STEP = 1 + 1 + 1 + 2 + 2   # dt, d, L1 fma, L2 mul+fma, Gram mul+fma
 
+# DRAM bytes (read + write) per launch of the benchmark's compensated walk,
+# from one ncu capture (profiles/walk_f32c_dram_traffic_stable_rank_n20000.md),
+# valid only while the walk's source is the one that was measured.
+TRAFFIC_RECORD = {"source_sha256_16": "c1f75f782d911231+5d31ddd65b7eaf43",
+                  "schedule": "tile512x2", "bytes": 32118315776 + 26655318528}
+
+
+def walk_source_id():
+    import hashlib
+    parts = []
+    for f in ("walk.cuh", "internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2404_07183_gb300", "csrc", f), "rb") as fh:
+            parts.append(hashlib.sha256(fh.read()).hexdigest()[:16])
+    return "+".join(parts)
+
 
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
@@ -344,7 +359,12 @@ def run_ours(args):
         "walk": {"ms": head["walk_ms"], "prepare_ms": head["prepare_ms"],
                  "merge_steps_per_s": walk_rate},
         "roofline": {"bound": "alu", "achieved": walk_rate, "peak": issue_peak,
-                     "unit": "merge-steps/s", "frac": walk_rate / issue_peak, "traffic": None,
+                     "unit": "merge-steps/s", "frac": walk_rate / issue_peak,
+                     "traffic": (TRAFFIC_RECORD["bytes"]
+                                 if (walk_source_id() == TRAFFIC_RECORD["source_sha256_16"]
+                                     and head["schedule"] == TRAFFIC_RECORD["schedule"]
+                                     and N == 20000) else None),
+                     "traffic_unit": "DRAM bytes per walk launch (ncu)",
                      "peak_basis": f"{sms} SMs x 128 lanes x {fmax/1e6:.0f} MHz / {TALLY[prec]} "
                                    "ops per merge step (fused L1+L2+Gram tally)"},
         "gpu_launches": head["steps"] * (4 + 2),

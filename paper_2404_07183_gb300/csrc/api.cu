@@ -174,21 +174,23 @@ int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int el
         if (grid < 1) return PCF_OK;
     } else {
         const int ctas = kernel == PCF_SCHED_TILE_512X2 ? 2 : 1;
+        const int regions = kernel == PCF_SCHED_TILE_512X2 ? 3 : 4;   // 32 x 16 or 32 x 32 units
         int dev = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         long budget = (long)per_sm / ctas - 1024 - 2048;       // per-CTA reserve + static
         const long optin = (long)device_smem_optin() - 2048;
         if (budget > optin) budget = optin;
-        int Wmax = (int)(budget / (4L * kGroup * elem_bytes));
+        int Wmax = (int)(budget / ((long)regions * kGroup * elem_bytes));
         if (Wmax > 4096) Wmax = 4096;
         int W = (sched && sched->window) ? sched->window : Wmax;
         if (W > Wmax) return PCF_EINVAL;
         if (W < 8) return PCF_ECUDA;
         wa.window = W;
-        smem = walk_smem_bytes(W, elem_bytes);
+        smem = (size_t)regions * (size_t)W * kGroup * (size_t)elem_bytes;
         grid = (int64_t)sms * ctas;
-        if (grid > wa.ntiles) grid = wa.ntiles;
+        const int64_t units = wa.ntiles * (kernel == PCF_SCHED_TILE_512X2 ? 2 : 1);
+        if (grid > units) grid = units;
         if (grid < 1) return PCF_OK;
     }
     for (const Launch& L : plan(F, nF)) {

@@ -198,18 +198,23 @@ __device__ __forceinline__ void decode_tile(const WalkArgs& a, int64_t t, int64_
     }
 }
 
-// THREADS = 1024: one CTA per SM, warp w walks diagonal w of each tile.
-// THREADS = 512: two CTAs per SM (each with half the shared memory, so a
-// smaller window), warp w walks diagonals w and w + 16 one after the other.
+// THREADS = 1024: one CTA per SM; a work unit is a whole 32 x 32 tile and
+// warp w walks its diagonal w (lane l: row (l + w) mod 32, column l).
+// THREADS = 512: two CTAs per SM, each with half the shared memory; a work
+// unit is half a tile, 32 rows x 16 columns (three staged regions instead of
+// four, so the window stays larger), and warp w walks lane l's pair
+// (row (l + w) mod 32, column l mod 16).  Both halves of a tile belong to the
+// same shard.
 template <typename T, int PREC, int COMBO, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const WalkArgs a)
 {
     using E = typename ElemOf<T>::type;
     constexpr int NM = combo_n(COMBO);
-    constexpr int NWARPS = THREADS / 32;
-    constexpr int PAIRS = 32 / NWARPS;              // diagonals per warp
+    constexpr int TCOLS = THREADS / 32;             // columns per work unit (32 or 16)
+    constexpr int UNITS = kTile / TCOLS;            // work units per 32 x 32 tile
+    constexpr int NPCF = kTile + TCOLS;             // staged PCFs: 32 rows + TCOLS columns
     constexpr unsigned kRow = kGroup * sizeof(E);   // bytes between element k and k+1 of a PCF
-    static_assert(THREADS % 64 == 0 && THREADS <= 1024, "thread count");
+    static_assert(THREADS == 1024 || THREADS == 512, "thread count");
 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int32_t sS[kTilePcfs], sNext[kTilePcfs], sLen[kTilePcfs];
@@ -227,19 +232,31 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const Wal
     const E* packR = reinterpret_cast<const E*>(a.pack_r);
     const E* packC = reinterpret_cast<const E*>(a.pack_c);
 
+    // this lane's pair inside every work unit
+    const int my_r = (lane + warp) & 31;
+    const int my_c = lane & (TCOLS - 1);
+    const int pf = my_r, pg = kTile + my_c;        // staged PCF indices
+    const unsigned base_f = (unsigned)(pf >> 4) * regionBytes + (unsigned)(pf & 15) * sizeof(E);
+    const unsigned base_g = (unsigned)(pg >> 4) * regionBytes + (unsigned)(pg & 15) * sizeof(E);
+
     for (;;) {
-        if (tid == 0)
-            sTile = a.shard_index + (int64_t)atomicAdd(&a.hdr->tiles, 1ull) * a.shard_count;
+        if (tid == 0) {
+            const int64_t k = (int64_t)atomicAdd(&a.hdr->tiles, 1ull);
+            sTile = (a.shard_index + (k / UNITS) * a.shard_count) * UNITS + (k % UNITS);
+        }
         __syncthreads();
-        const int64_t t = sTile;
+        const int64_t unit = sTile;
+        const int64_t t = unit / UNITS;
         if (t >= a.ntiles) break;
+        const int half = (int)(unit - t * UNITS);
         int64_t bi, bj;
         decode_tile(a, t, bi, bj);
+        const int64_t col0 = bj * kTile + half * TCOLS;   // first column of this unit
 
-        // tile metadata
-        if (tid < kTilePcfs) {
-            const bool is_row = tid < 32;
-            const int64_t g = is_row ? bi * kTile + tid : bj * kTile + (tid - 32);
+        // unit metadata
+        if (tid < NPCF) {
+            const bool is_row = tid < kTile;
+            const int64_t g = is_row ? bi * kTile + tid : col0 + (tid - kTile);
             const int64_t nset = is_row ? a.n_r : a.n_c;
             if (g < nset) {
                 sLen[tid] = is_row ? a.slen_r[g] : a.slen_c[g];
@@ -250,23 +267,22 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const Wal
             }
             sS[tid] = 0;
         }
+        const bool lane_valid = (bi * kTile + my_r < a.n_r) && (col0 + my_c < a.n_c);
 
-        Acc<PREC> acc[PAIRS][NM];
-        T tcq[PAIRS];
-#pragma unroll
-        for (int q = 0; q < PAIRS; ++q) tcq[q] = T(0);
+        Acc<PREC> acc[NM];
+        T tc = T(0);
         T T0 = T(0);            // start of the current window (block-uniform)
         __syncthreads();
 
         for (;;) {
             // ---- window end T1 = min over PCFs of te[S + W - 1] (clamped) ----
-            if (tid < kTilePcfs) {
+            if (tid < 64) {
                 T cand = T(INFINITY);
-                const int len = sLen[tid];
+                const int len = tid < NPCF ? sLen[tid] : 0;
                 if (len > 0) {
                     int idx = sS[tid] + W - 1;
                     if (idx > len - 1) idx = len - 1;
-                    cand = (tid < 32 ? packR : packC)[sOff[tid] + idx].x;
+                    cand = (tid < kTile ? packR : packC)[sOff[tid] + idx].x;
                 }
                 for (int o = 16; o > 0; o >>= 1) {
                     T other = __shfl_xor_sync(0xffffffffu, cand, o);
@@ -283,19 +299,19 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const Wal
                 return;
             }
 
-            // ---- stage elements [S, S + min(W, len - S)) of all 64 PCFs ----
+            // ---- stage elements [S, S + min(W, len - S)) of the unit's PCFs ----
             // THREADS is a multiple of 16, so a thread always serves the same
             // slot (tid & 15) of each region and walks k in steps of THREADS/16.
             {
                 const int slot = tid & 15;
 #pragma unroll 1
-                for (int region = 0; region < 4; ++region) {
+                for (int region = 0; region < NPCF / kGroup; ++region) {
                     const int p = region * kGroup + slot;
                     const int len = sLen[p];
                     const int S = sS[p];
                     int kend = len - S;
                     if (kend > W) kend = W;
-                    const E* src = (region < 2 ? packR : packC) + sOff[p] + S;
+                    const E* src = (p < kTile ? packR : packC) + sOff[p] + S;
                     unsigned char* dst = smem + (unsigned)region * regionBytes + (unsigned)slot * sizeof(E);
                     for (int k = tid >> 4; k < kend; k += THREADS / 16)
                         *reinterpret_cast<E*>(dst + (unsigned)k * kRow) = src[k];
@@ -304,7 +320,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const Wal
             __syncthreads();
 
             // ---- per PCF: first staged element whose interval ends at/after T1 ----
-            if (tid < kTilePcfs) {
+            if (tid < NPCF) {
                 const int len = sLen[tid];
                 int next = 0;
                 if (len > 0) {
@@ -323,27 +339,19 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const Wal
             }
             __syncthreads();
 
-            // ---- walk this window: this lane's PAIRS pairs, one after the other ----
-#pragma unroll
-            for (int q = 0; q < PAIRS; ++q) {
-                const int my_r = (lane + warp + q * NWARPS) & 31;
-                const int pf = my_r, pg = 32 + lane;
-                if (bi * kTile + my_r >= a.n_r || bj * kTile + lane >= a.n_c) continue;
+            // ---- walk this window ----
+            if (lane_valid) {
                 int cnt = (sNext[pf] - sS[pf]) + (sNext[pg] - sS[pg]);
-                const unsigned base_f = (unsigned)(pf >> 4) * regionBytes + (unsigned)(pf & 15) * sizeof(E);
-                const unsigned base_g = (unsigned)(pg >> 4) * regionBytes + (unsigned)(pg & 15) * sizeof(E);
                 unsigned af = smem_base + base_f, ag = smem_base + base_g;
                 const E ef = *reinterpret_cast<const E*>(smem + base_f);
                 const E eg = *reinterpret_cast<const E*>(smem + base_g);
                 T tf = ef.x, tg = eg.x, vf = ef.y, vg = eg.y;
-                T tc = tcq[q];
-                Acc<PREC>* ac = acc[q];
 #define PCF_WALK_STEP()                                                           \
                 {                                                                 \
                     const T tn = first_end(tf, tg);                               \
                     const T dt = tn - tc;                                         \
                     tc = tn;                                                      \
-                    accumulate<COMBO, PREC, T>(ac, vf, vg, dt, p0);               \
+                    accumulate<COMBO, PREC, T>(acc, vf, vg, dt, p0);              \
                     advance_cursor<kRow>(af, tf, vf, ag, tg, vg);                 \
                 }
 #pragma unroll 1
@@ -356,30 +364,26 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const Wal
 #pragma unroll 1
                 for (; cnt > 0; --cnt) PCF_WALK_STEP()
 #undef PCF_WALK_STEP
-                tcq[q] = tc;
             }
             const bool last = !(T1 < T(INFINITY));
             __syncthreads();
             if (last) break;
             T0 = T1;
-            if (tid < kTilePcfs) sS[tid] = sNext[tid];
+            if (tid < NPCF) sS[tid] = sNext[tid];
             __syncthreads();
         }
 
         // ---- tail, root, output ----
-#pragma unroll
-        for (int q = 0; q < PAIRS; ++q) {
-            const int my_r = (lane + warp + q * NWARPS) & 31;
-            const int64_t gi = bi * kTile + my_r, gj = bj * kTile + lane;
-            if (gi >= a.n_r || gj >= a.n_c) continue;
+        if (lane_valid) {
+            const int64_t gi = bi * kTile + my_r, gj = col0 + my_c;
             const int64_t i = a.perm_r[gi], j = a.perm_c[gj];
             // values on the last intervals [t_last, inf) of both PCFs
-            const T vlf = packR[sOff[my_r] + sLen[my_r] - 1].y;
-            const T vlg = packC[sOff[32 + lane] + sLen[32 + lane] - 1].y;
+            const T vlf = packR[sOff[pf] + sLen[pf] - 1].y;
+            const T vlg = packC[sOff[pg] + sLen[pg] - 1].y;
 #pragma unroll
             for (int m = 0; m < NM; ++m) {
                 const int MI = combo_metric(COMBO, m);
-                double I = acc[q][m].value();
+                double I = acc[m].value();
                 const T h = (MI == MI_GRAM) ? vlf * vlg : fabs(vlf - vlg);
                 if (h != T(0)) I = (h > T(0)) ? (double)INFINITY : -(double)INFINITY;
                 const double F = finalize_root(a.metric[m], a.root[m], a.p[m], I);
