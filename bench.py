@@ -38,7 +38,9 @@ METRICS = ["l1", "l2", "gram"]
 # L1 |d|*dt fma 1, L2 d*d + fma 2, Gram a*b + fma 2; compensated (Kahan): each
 # accumulate is the fma that subtracts the compensation plus 3 additions.
 TALLY = {"f32c": 5 + 1 + (1 + 3) + (2 + 3) + (2 + 3), "f32": 5 + 1 + 1 + 2 + 2,
-         "f64": 5 + 1 + 1 + 2 + 2}
+         "f64": 5 + 1 + 1 + 2 + 2,
+         # block-compensated: plain FMA terms + one 4-op Kahan add per metric per 16 steps
+         "f32b": 5 + 1 + 1 + 2 + 2 + 3 * 4 / 16}
 FP64_OPS_PER_STEP = 1 + 1 + 1 + 2 + 2   # dt, d, L1 fma, L2 mul+fma, Gram mul+fma
 
 # DRAM bytes (read + write) per launch of the benchmark's compensated walk,
@@ -234,7 +236,10 @@ def run_ours(args):
 
     results = {}
     tuned = {}
-    for prec in (args.precision, "f64") if not args.no_fp64 else (args.precision,):
+    forms = [args.precision]
+    if not args.no_fp64:
+        forms += [f for f in ("f32b", "f64") if f != args.precision]
+    for prec in forms:
         if args.schedule:
             sched = args.schedule
         else:
@@ -374,6 +379,18 @@ def run_ours(args):
         "pipe_peaks": pp,
         "clocks": head["clocks"],
     }
+    if "f32b" in results and prec != "f32b":
+        f = results["f32b"]
+        wr = walk_steps / (f["walk_ms"] * 1e-3)
+        pk = sms * 128 * fmax / TALLY["f32b"]
+        line["f32b"] = {"value": pairs / (f["ms_per_step"] * 1e-3), "unit": "pair-integrals/s",
+                        "ms_per_step": f["ms_per_step"], "walk_ms": f["walk_ms"],
+                        "merge_steps_per_s": wr, "schedule": f["schedule"],
+                        "roofline": {"bound": "alu", "achieved": wr, "peak": pk,
+                                     "unit": "merge-steps/s", "frac": wr / pk,
+                                     "peak_basis": f"tally {TALLY['f32b']} ops per merge step"},
+                        "note": "float32 walk, FMA block sums of <= 16 rectangles, Kahan across "
+                                "blocks (error <= ~18u sum|terms|)"}
     if "f64" in results:
         f = results["f64"]
         r64 = pp["fp64"]["lane_ops_per_clk_per_sm"]
@@ -541,6 +558,45 @@ def run_workload(name, args):
                           "frac": (steps_walk + diag) / (res["f32"] * 1e-3) / issue(5 + 2)},
                      cpu_baseline=_cpu_rows(s, ["gram"], seconds_target=8.0, row0=N // 2))
 
+    if name == "appendix_a":
+        s = synth.appendix_a(n_pcfs=args.n or 50000)
+        N = s.n
+        steps_walk, _ = exact_walk_steps(s)
+        x = P.PcfTensors.from_numpy(s, dev)
+        pairs = N * (N - 1) // 2
+        o = [torch.empty((N, N), dtype=torch.float32, device=dev)]
+        from paper_2404_07183_gb300 import autotune
+        res = {}
+        for prec in ("f32c", "f32", "f64"):
+            sched, tune_ms = autotune.tune_pairwise(x, ["l1"], prec, repeats=1,
+                                                    candidates=(("tile1024", 0), ("tile512x2", 0)))
+            ws = torch.empty(P.pcf_workspace_size(x, None, prec), dtype=torch.uint8, device=dev)
+
+            def step():
+                P.pcf_prepare(x, prec, workspace=ws)
+                P.pcf_pairwise(x, ["l1"], precision=prec, out=o, workspace=ws, prepared=True,
+                               check=False, schedule=sched)
+            ms = float(np.mean(_timed(step, 1, 1, flush, stream)))
+            P.pcf_check(ws)
+            res[prec] = {"ms_per_step": ms, "value": pairs / (ms * 1e-3),
+                         "merge_steps_per_s": steps_walk / (ms * 1e-3), "schedule": sched}
+            del ws
+        ms = res["f32c"]["ms_per_step"]
+        rate = steps_walk / (ms * 1e-3)
+        return _line(name, pairs / (ms * 1e-3), "pair-integrals/s", ms, 1, 1, "f32 (compensated)",
+                     {"workload": f"appendix_a N={N}: n~U{{10..1000}}, times |alpha|*sorted|t~|, "
+                                  "N(0,1) values, final 0 (float64 input), L1 distance matrix, "
+                                  "full N x N float32",
+                      "N": N, "pairs": pairs, "merge_steps": steps_walk,
+                      "paper_context": "L1 on 500,000 such PCFs: ~423 s on 8 A100 "
+                                       "(~3.7e7 pair-integrals/s per GPU, precision not stated)"},
+                     merge_steps_per_s=rate,
+                     roofline={"bound": "alu", "achieved": rate, "peak": issue(5 + 1 + 4),
+                               "unit": "merge-steps/s", "frac": rate / issue(5 + 1 + 4),
+                               "note": "whole step; tally 10 ops/step (L1, Kahan)"},
+                     forms=res,
+                     cpu_baseline=_cpu_rows(s, ["l1"], seconds_target=8.0, row0=N // 3))
+
     if name == "gradient":
         s, G = synth.gradient()
         N = s.n
@@ -641,7 +697,8 @@ def main():
                     choices=["tile1024", "tile512x2", "mergepath", "auto"],
                     help="force a walk schedule instead of autotuning it")
     ap.add_argument("--workload", default="stable_rank",
-                    choices=["stable_rank", "uniform_small", "lognormal", "gradient", "euler", "all"])
+                    choices=["stable_rank", "uniform_small", "lognormal", "gradient", "euler",
+                             "appendix_a", "all"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -650,7 +707,8 @@ def main():
     elif args.workload == "stable_rank":
         run_ours(args)
     else:
-        names = (["uniform_small", "gradient", "lognormal", "euler"] if args.workload == "all"
+        names = (["uniform_small", "gradient", "lognormal", "euler", "appendix_a"]
+                 if args.workload == "all"
                  else [args.workload])
         for nm in names:
             print(json.dumps(run_workload(nm, args)), flush=True)

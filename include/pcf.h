@@ -70,7 +70,12 @@ enum pcf_precision {
     PCF_PREC_F32_COMP = 1, /* float32 walk, every rectangle's term added by Kahan's
                               compensated summation into a (sum, compensation)
                               pair; error <= 2u * sum|terms| + O(n u^2)        */
-    PCF_PREC_F32 = 2       /* float32 walk, plain float32 fused multiply-add    */
+    PCF_PREC_F32 = 2,      /* float32 walk, plain float32 fused multiply-add    */
+    PCF_PREC_F32_BLOCK = 3 /* float32 walk, terms summed by FMA over blocks of at
+                              most 16 rectangles, block sums added by Kahan's
+                              compensated summation; error <= about
+                              18u * sum|terms| (a fraction of the work of
+                              PCF_PREC_F32_COMP)                               */
 };
 /* float64 input walked in a float32 precision is rounded to nearest float32
  * when packed (times keep their order; times that round together become one

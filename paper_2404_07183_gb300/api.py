@@ -22,10 +22,12 @@ import torch
 from . import abi
 
 __all__ = ["PcfError", "PcfTensors", "pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross",
-           "pcf_pairwise_backward", "pcf_check", "PairwiseFn", "pdist", "l2_kernel",
+           "pcf_pairwise_backward", "pcf_check", "PairwiseFn", "PairwiseGraph", "pdist",
+           "l2_kernel",
            "parse_metric", "PRECISIONS"]
 
-PRECISIONS = {"f64": abi.PCF_PREC_F64, "f32c": abi.PCF_PREC_F32_COMP, "f32": abi.PCF_PREC_F32}
+PRECISIONS = {"f64": abi.PCF_PREC_F64, "f32c": abi.PCF_PREC_F32_COMP, "f32": abi.PCF_PREC_F32,
+              "f32b": abi.PCF_PREC_F32_BLOCK}
 _METRICS = {"l1": abi.PCF_L1, "l2": abi.PCF_L2, "lp": abi.PCF_LP, "gram": abi.PCF_GRAM}
 
 
@@ -298,6 +300,44 @@ class PairwiseFn(torch.autograd.Function):
         x = PcfTensors(offsets, times.detach(), values.detach())
         gv, gt = pcf_pairwise_backward(x, ctx.metric, grad.to(F.dtype), fwd_out=F)
         return gv, gt, None, None, None
+
+
+class PairwiseGraph:
+    """pcf_prepare + pcf_pairwise captured once into a CUDA graph and replayed.
+
+    For repeated calls on collections of the same shape (same N and nnz,
+    new contents copied into ``x``'s tensors): the validation, sort, pack and
+    walk launches are replayed as one graph, with the workspace and outputs
+    allocated once.  ``replay()`` enqueues on the current stream; call
+    ``check()`` to synchronize and surface invalid input."""
+
+    def __init__(self, x: PcfTensors, metrics, precision="f32c", layout="full",
+                 out_dtype=torch.float32, schedule=None):
+        self.x = x
+        self.metrics = list(metrics) if not isinstance(metrics, (str, tuple)) else [metrics]
+        n = x.n
+        shape = (n, n) if layout == "full" else (n * (n + 1) // 2,)
+        self.outs = [torch.empty(shape, dtype=out_dtype, device=x.times.device)
+                     for _ in self.metrics]
+        self.ws = torch.empty(max(pcf_workspace_size(x, None, precision), 256),
+                              dtype=torch.uint8, device=x.times.device)
+        args = dict(precision=precision, layout=layout, out=self.outs, workspace=self.ws,
+                    check=False, schedule=schedule)
+        # run once outside capture (module loading, kernel attributes)
+        pcf_prepare(x, precision, workspace=self.ws)
+        pcf_pairwise(x, self.metrics, prepared=True, **args)
+        pcf_check(self.ws)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            pcf_prepare(x, precision, workspace=self.ws)
+            pcf_pairwise(x, self.metrics, prepared=True, **args)
+
+    def replay(self):
+        self.graph.replay()
+        return self.outs
+
+    def check(self):
+        pcf_check(self.ws, what="PairwiseGraph")
 
 
 def pdist(x: PcfTensors, p=1.0, precision="f64", out_dtype=torch.float64):

@@ -208,14 +208,17 @@ int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int el
         if (kernel == PCF_SCHED_MERGEPATH) {
             if (precision == PCF_PREC_F64) e = launch_mergepath_f64(L.combo, wa, npairs, g, s);
             else if (precision == PCF_PREC_F32_COMP) e = launch_mergepath_f32c(L.combo, wa, npairs, g, s);
+            else if (precision == PCF_PREC_F32_BLOCK) e = launch_mergepath_f32b(L.combo, wa, npairs, g, s);
             else e = launch_mergepath_f32(L.combo, wa, npairs, g, s);
         } else if (kernel == PCF_SCHED_TILE_512X2) {
             if (precision == PCF_PREC_F64) e = launch_walk_f64_t512(L.combo, wa, g, smem, s);
             else if (precision == PCF_PREC_F32_COMP) e = launch_walk_f32c_t512(L.combo, wa, g, smem, s);
+            else if (precision == PCF_PREC_F32_BLOCK) e = launch_walk_f32b_t512(L.combo, wa, g, smem, s);
             else e = launch_walk_f32_t512(L.combo, wa, g, smem, s);
         } else {
             if (precision == PCF_PREC_F64) e = launch_walk_f64_t1024(L.combo, wa, g, smem, s);
             else if (precision == PCF_PREC_F32_COMP) e = launch_walk_f32c_t1024(L.combo, wa, g, smem, s);
+            else if (precision == PCF_PREC_F32_BLOCK) e = launch_walk_f32b_t1024(L.combo, wa, g, smem, s);
             else e = launch_walk_f32_t1024(L.combo, wa, g, smem, s);
         }
         if (e != cudaSuccess) return PCF_ECUDA;
@@ -232,7 +235,7 @@ int pcf_workspace_size(const pcf_csr* x, const pcf_csr* y, int precision, int pu
 {
     if (!bytes || !x || x->n < 0 || x->nnz < 0 || x->n > 0x7fffffffLL) return PCF_EINVAL;
     if (y && (y->n < 0 || y->nnz < 0 || y->n > 0x7fffffffLL)) return PCF_EINVAL;
-    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32) return PCF_EINVAL;
+    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32_BLOCK) return PCF_EINVAL;
     if (purpose != PCF_WS_FORWARD && purpose != PCF_WS_BACKWARD) return PCF_EINVAL;
     const int es = purpose == PCF_WS_BACKWARD ? 16 : elem_bytes_for(precision);
     size_t b = sizeof(Header);
@@ -260,7 +263,7 @@ int pcf_prepare(const pcf_csr* x, int precision, void* workspace, size_t workspa
                 cudaStream_t stream)
 {
     if (!csr_ok(x)) return PCF_EINVAL;
-    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32) return PCF_EINVAL;
+    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32_BLOCK) return PCF_EINVAL;
     Header* hdr;
     SetView sv;
     int rc = pairwise_common(x, precision, workspace, workspace_bytes, &hdr, &sv);
@@ -286,7 +289,7 @@ int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precisi
                     size_t workspace_bytes, cudaStream_t stream)
 {
     if (!csr_ok(x)) return PCF_EINVAL;
-    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32) return PCF_EINVAL;
+    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32_BLOCK) return PCF_EINVAL;
     if (layout != PCF_OUT_FULL && layout != PCF_OUT_UPPER_PACKED) return PCF_EINVAL;
     if (out_dtype != PCF_F32 && out_dtype != PCF_F64) return PCF_EINVAL;
     if (flags & ~PCF_PAIRWISE_PREPARED) return PCF_EINVAL;
@@ -337,7 +340,7 @@ int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t 
                  size_t workspace_bytes, cudaStream_t stream)
 {
     if (!csr_ok(a) || !csr_ok(b)) return PCF_EINVAL;
-    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32) return PCF_EINVAL;
+    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32_BLOCK) return PCF_EINVAL;
     if (out_dtype != PCF_F32 && out_dtype != PCF_F64) return PCF_EINVAL;
     if (row_begin < 0 || row_end < row_begin || row_end > a->n) return PCF_EINVAL;
     if (ld_out < b->n) return PCF_EINVAL;

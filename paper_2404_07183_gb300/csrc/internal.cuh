@@ -3,9 +3,11 @@
 // Data layout in HBM (all inside the caller's workspace):
 //   header   : device error key, max lengths, tile counter            (256 B)
 //   per set  : lens[N] int32      lengths in input order
-//              perm[N] int32      input index of the s-th shortest PCF
+//              perm[N] int32      input index of the s-th PCF in sort order
+//                                 (by length, then by time scale for long PCFs)
 //              slen[N] int32      lengths in sorted order
-//              tmpk/tmpv[N] int32 radix-sort ping-pong buffers
+//              skey[N] uint32     time-scale key (last breakpoint, float bits)
+//              khi/klo/kv[2][N]   radix-sort ping-pong buffers
 //              poff[N+1] int64    packed offsets (exclusive scan of slen)
 //              packed[nnz]        "interval elements" in sorted order:
 //                                 element k of PCF s = (te_k, v_k), the value
@@ -63,8 +65,10 @@ struct SetView {
     int32_t* lens = nullptr;
     int32_t* perm = nullptr;
     int32_t* slen = nullptr;
-    int32_t* tmpk = nullptr;
-    int32_t* tmpv = nullptr;
+    uint32_t* skey = nullptr;
+    uint32_t* khi[2] = {nullptr, nullptr};
+    uint32_t* klo[2] = {nullptr, nullptr};
+    int32_t* kv[2] = {nullptr, nullptr};
     int64_t* poff = nullptr;
     void* packed = nullptr;
     int elem_bytes = 8;     // 8 (float pairs) or 16 (double pairs)
@@ -122,6 +126,7 @@ enum Combo : int {
 PCF_DECL_WALK(f64)
 PCF_DECL_WALK(f32c)
 PCF_DECL_WALK(f32)
+PCF_DECL_WALK(f32b)
 #undef PCF_DECL_WALK
 size_t walk_smem_bytes(int window, int elem_bytes);
 

@@ -88,6 +88,10 @@ __global__ void __launch_bounds__(256, 4) mergepath_kernel(const WalkArgs a, int
             if (kg > 0) { const T y = ldg_elem<T>(G + kg - 1).x; tc = ends_after(y, tc) ? y : tc; }
             E ef = ldg_elem<T>(F + kf), eg = ldg_elem<T>(G + kg);
             for (int64_t s = s0; s < s1; ++s) {
+                if (((s - s0) & 15) == 0) {
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) acc[m].flush();
+                }
                 const bool adv_f = !ends_after(ef.x, eg.x);
                 const T tn = adv_f ? ef.x : eg.x;
                 const T dt = tn - tc;
@@ -97,6 +101,8 @@ __global__ void __launch_bounds__(256, 4) mergepath_kernel(const WalkArgs a, int
                 else eg = ldg_elem<T>(G + (++kg));
             }
         }
+#pragma unroll
+        for (int m = 0; m < NM; ++m) acc[m].flush();
         // fixed-order float64 combine of the lane partials
         double I[NM];
 #pragma unroll

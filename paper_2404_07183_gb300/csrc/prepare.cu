@@ -22,7 +22,8 @@ template <typename T>
 __global__ void validate_kernel(const int64_t* __restrict__ offsets,
                                 const T* __restrict__ times, const T* __restrict__ values,
                                 int64_t n, int64_t nnz_total, int whole, int walk_f32,
-                                int32_t* __restrict__ lens, Header* hdr, int slot)
+                                int32_t* __restrict__ lens, uint32_t* __restrict__ skey,
+                                Header* hdr, int slot)
 {
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -35,10 +36,16 @@ __global__ void validate_kernel(const int64_t* __restrict__ offsets,
         if (whole && i == n - 1 && o1 != nnz_total) bad = true;
         if (bad) {
             if (lane == 0) record_error(hdr, kErrOffsets, i);
-            if (lane == 0) lens[i] = 1;
+            if (lane == 0) { lens[i] = 1; skey[i] = 0; }
             continue;
         }
-        if (lane == 0) lens[i] = (int32_t)(o1 - o0);
+        if (lane == 0) {
+            lens[i] = (int32_t)(o1 - o0);
+            // time scale of the PCF: its last breakpoint, as float32 bits
+            // (non-negative floats order like their bit patterns)
+            const float tl = (float)times[o1 - 1];
+            skey[i] = (tl > 0.f && tl < INFINITY) ? __float_as_uint(tl) : 0u;
+        }
         local_max = max(local_max, (unsigned int)(o1 - o0));
         for (int64_t k = o0 + lane; k < o1; k += 32) {
             T t = times[k];
@@ -62,14 +69,27 @@ __global__ void validate_kernel(const int64_t* __restrict__ offsets,
     if (lane == 0 && local_max) atomicMax(&hdr->maxlen[slot], local_max);
 }
 
-// Single-CTA stable LSD radix sort of (length, index) by length, 8-bit digits,
-// followed by the exclusive scan of the sorted lengths.  Stability makes the
-// permutation a function of the input alone.
+// Single-CTA stable LSD radix sort with 8-bit digits by a composite key:
+// high word = length bucket (the length itself up to 256, then buckets of 32),
+// low word = time scale (last breakpoint time, float bits) for PCFs longer
+// than 256.  Lengths group the pairs of a tile by work; among long PCFs, the
+// time scale groups PCFs whose breakpoints cover similar time ranges, so the
+// shared-memory windows of a tile advance all of them together.  Stability
+// makes the permutation a function of the input alone.  Followed by the
+// sorted lengths and their exclusive scan.
 constexpr int kSortThreads = 1024;
+constexpr int kScaleSortMin = 256;
+
+__device__ __forceinline__ uint32_t length_bucket(int32_t len)
+{
+    return len <= kScaleSortMin ? (uint32_t)len
+                                : (uint32_t)kScaleSortMin + (uint32_t)((len - kScaleSortMin) >> 5);
+}
 
 __global__ void __launch_bounds__(kSortThreads)
-sort_scan_kernel(const int32_t* __restrict__ lens, int64_t n, Header* hdr, int slot,
-                 int32_t* perm, int32_t* slen, int32_t* tmpk, int32_t* tmpv,
+sort_scan_kernel(const int32_t* __restrict__ lens, const uint32_t* __restrict__ skey, int64_t n,
+                 Header* hdr, int slot, int32_t* perm, int32_t* slen, uint32_t* khi0,
+                 uint32_t* klo0, int32_t* kv0, uint32_t* khi1, uint32_t* klo1, int32_t* kv1,
                  int64_t* __restrict__ poff)
 {
     __shared__ unsigned int hist[256];
@@ -80,52 +100,67 @@ sort_scan_kernel(const int32_t* __restrict__ lens, int64_t n, Header* hdr, int s
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (hdr->err != kNoError) return;
 
-    unsigned int maxlen = hdr->maxlen[slot];
-    int passes = 1;
-    while (passes < 4 && (maxlen >> (8 * passes)) != 0) ++passes;
+    const unsigned int maxlen = hdr->maxlen[slot];
+    const bool use_scale = maxlen > (unsigned)kScaleSortMin;
+    const int nlo = use_scale ? 4 : 0;
+    const uint32_t maxb = length_bucket((int32_t)maxlen);
+    int nhi = 1;
+    while (nhi < 4 && (maxb >> (8 * nhi)) != 0) ++nhi;
+    const int passes = nlo + nhi;
 
     for (int i = tid; i < 32 * 256; i += kSortThreads) (&wcnt[0][0])[i] = 0;
 
-    // ping-pong: pass 0 reads (lens, index), writes A; then alternate A <-> B.
-    // Choose buffers so that the last pass writes (slen, perm).
-    int32_t* bufk[2];
-    int32_t* bufv[2];
-    if (passes % 2 == 1) { bufk[0] = slen; bufv[0] = perm; bufk[1] = tmpk; bufv[1] = tmpv; }
-    else                 { bufk[0] = tmpk; bufv[0] = tmpv; bufk[1] = slen; bufv[1] = perm; }
+    uint32_t* bhi[2] = {khi0, khi1};
+    uint32_t* blo[2] = {klo0, klo1};
+    int32_t* bv[2] = {kv0, kv1};
 
     for (int pass = 0; pass < passes; ++pass) {
-        const int shift = 8 * pass;
-        const int32_t* inK = (pass == 0) ? lens : bufk[(pass - 1) & 1];
-        const int32_t* inV = (pass == 0) ? nullptr : bufv[(pass - 1) & 1];
-        int32_t* outK = bufk[pass & 1];
-        int32_t* outV = bufv[pass & 1];
+        const bool lo_digit = pass < nlo;
+        const int shift = 8 * (lo_digit ? pass : pass - nlo);
+        const int src = (pass - 1) & 1, dst = pass & 1;
+        auto load = [&](int64_t i, uint32_t& hi, uint32_t& lo, int32_t& v) {
+            if (pass == 0) {
+                const int32_t len = lens[i];
+                hi = length_bucket(len);
+                lo = (use_scale && len > kScaleSortMin) ? skey[i] : 0u;
+                v = (int32_t)i;
+            } else {
+                hi = bhi[src][i];
+                lo = blo[src][i];
+                v = bv[src][i];
+            }
+        };
         if (tid < 256) hist[tid] = 0;
         __syncthreads();
-        for (int64_t i = tid; i < n; i += kSortThreads)
-            atomicAdd(&hist[((unsigned)inK[i] >> shift) & 255u], 1u);
+        for (int64_t i = tid; i < n; i += kSortThreads) {
+            uint32_t hi, lo;
+            int32_t v;
+            load(i, hi, lo, v);
+            atomicAdd(&hist[((lo_digit ? lo : hi) >> shift) & 255u], 1u);
+        }
         __syncthreads();
         if (warp == 0) {
             // exclusive scan of 256 counters by one warp (8 per lane)
-            unsigned int v[8], s = 0;
-            for (int q = 0; q < 8; ++q) { v[q] = hist[lane * 8 + q]; s += v[q]; }
-            unsigned int incl = s;
+            unsigned int c[8], sum = 0;
+            for (int q = 0; q < 8; ++q) { c[q] = hist[lane * 8 + q]; sum += c[q]; }
+            unsigned int incl = sum;
             for (int o = 1; o < 32; o <<= 1) {
                 unsigned int y = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += y;
             }
-            unsigned int run = incl - s;
-            for (int q = 0; q < 8; ++q) { base[lane * 8 + q] = run; run += v[q]; }
+            unsigned int run = incl - sum;
+            for (int q = 0; q < 8; ++q) { base[lane * 8 + q] = run; run += c[q]; }
         }
         __syncthreads();
         for (int64_t c0 = 0; c0 < n; c0 += kSortThreads) {
             const int64_t i = c0 + tid;
             const bool valid = i < n;
-            int32_t key = 0, val = 0;
+            uint32_t hi = 0, lo = 0;
+            int32_t v = 0;
             unsigned int d = 256u + lane;   // unique dummy digit for idle lanes
             if (valid) {
-                key = inK[i];
-                val = (pass == 0) ? (int32_t)i : inV[i];
-                d = ((unsigned)key >> shift) & 255u;
+                load(i, hi, lo, v);
+                d = ((lo_digit ? lo : hi) >> shift) & 255u;
             }
             unsigned int peers = __match_any_sync(0xffffffffu, d);
             unsigned int rank = __popc(peers & ((1u << lane) - 1u));
@@ -136,8 +171,9 @@ sort_scan_kernel(const int32_t* __restrict__ lens, int64_t n, Header* hdr, int s
                 unsigned int off = 0;
                 for (int w = 0; w < warp; ++w) off += wcnt[w][d];
                 unsigned int pos = base[d] + off + rank;
-                outK[pos] = key;
-                outV[pos] = val;
+                bhi[dst][pos] = hi;
+                blo[dst][pos] = lo;
+                bv[dst][pos] = v;
             }
             __syncthreads();
             if (tid < 256) {
@@ -148,6 +184,13 @@ sort_scan_kernel(const int32_t* __restrict__ lens, int64_t n, Header* hdr, int s
             __syncthreads();
         }
     }
+    const int32_t* order = bv[(passes - 1) & 1];
+    for (int64_t s = tid; s < n; s += kSortThreads) {
+        const int32_t v = order[s];
+        perm[s] = v;
+        slen[s] = lens[v];
+    }
+    __syncthreads();
 
     // exclusive scan of sorted lengths -> poff[0..n]
     if (tid == 0) carry_s = 0;
@@ -218,7 +261,7 @@ __global__ void pack_kernel(const int64_t* __restrict__ offsets, const Tin* __re
 size_t set_bytes(int64_t n, int64_t nnz, int elem_bytes)
 {
     size_t b = 0;
-    b += 5 * align_up(sizeof(int32_t) * (size_t)n);
+    b += 10 * align_up(sizeof(int32_t) * (size_t)n);
     b += align_up(sizeof(int64_t) * (size_t)(n + 1));
     b += align_up((size_t)elem_bytes * (size_t)nnz);
     return b;
@@ -232,8 +275,12 @@ SetView carve_set(char*& cur, int64_t n, int64_t nnz, int elem_bytes, int slot)
     v.lens = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (size_t)n));
     v.perm = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (size_t)n));
     v.slen = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (size_t)n));
-    v.tmpk = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (size_t)n));
-    v.tmpv = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (size_t)n));
+    v.skey = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)n));
+    for (int k = 0; k < 2; ++k) {
+        v.khi[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)n));
+        v.klo[k] = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * (size_t)n));
+        v.kv[k] = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * (size_t)n));
+    }
     v.poff = reinterpret_cast<int64_t*>(take(sizeof(int64_t) * (size_t)(n + 1)));
     v.packed = take((size_t)elem_bytes * (size_t)nnz);
     return v;
@@ -256,13 +303,14 @@ cudaError_t prepare_set(const int64_t* offsets, const void* times, const void* v
     const int g = grid_for_warps(n);
     if (in_dtype == PCF_F64) {
         validate_kernel<double><<<g, 256, 0, s>>>(offsets, (const double*)times,
-            (const double*)values, n, nnz_total, whole, !walk_f64, sv.lens, hdr, sv.slot);
+            (const double*)values, n, nnz_total, whole, !walk_f64, sv.lens, sv.skey, hdr, sv.slot);
     } else {
         validate_kernel<float><<<g, 256, 0, s>>>(offsets, (const float*)times,
-            (const float*)values, n, nnz_total, whole, !walk_f64, sv.lens, hdr, sv.slot);
+            (const float*)values, n, nnz_total, whole, !walk_f64, sv.lens, sv.skey, hdr, sv.slot);
     }
-    sort_scan_kernel<<<1, kSortThreads, 0, s>>>(sv.lens, n, hdr, sv.slot, sv.perm, sv.slen,
-                                                 sv.tmpk, sv.tmpv, sv.poff);
+    sort_scan_kernel<<<1, kSortThreads, 0, s>>>(sv.lens, sv.skey, n, hdr, sv.slot, sv.perm, sv.slen,
+                                                 sv.khi[0], sv.klo[0], sv.kv[0], sv.khi[1],
+                                                 sv.klo[1], sv.kv[1], sv.poff);
     if (in_dtype == PCF_F64) {
         if (walk_f64)
             pack_kernel<double, double><<<g, 256, 0, s>>>(offsets, (const double*)times,

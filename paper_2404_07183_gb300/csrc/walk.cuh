@@ -40,7 +40,7 @@
 
 namespace pcfgb {
 
-constexpr int kF64 = 0, kF32C = 1, kF32 = 2;
+constexpr int kF64 = 0, kF32C = 1, kF32 = 2, kF32B = 3;
 constexpr int MI_NONE = 0, MI_L1 = 1, MI_L2 = 2, MI_L3 = 3, MI_LP = 4, MI_GRAM = 5;
 
 __host__ __device__ constexpr int combo_n(int c)
@@ -78,11 +78,13 @@ template <int PREC> struct Acc;
 template <> struct Acc<kF64> {
     double s = 0.0;
     __device__ __forceinline__ void add(double h, double dt) { s = fma(h, dt, s); }
+    __device__ __forceinline__ void flush() {}
     __device__ __forceinline__ double value() const { return s; }
 };
 template <> struct Acc<kF32> {
     float s = 0.f;
     __device__ __forceinline__ void add(float h, float dt) { s = fmaf(h, dt, s); }
+    __device__ __forceinline__ void flush() {}
     __device__ __forceinline__ double value() const { return (double)s; }
 };
 // Kahan's compensated summation, one rectangle term per add.  The term
@@ -100,6 +102,28 @@ template <> struct Acc<kF32C> {
         c = __fsub_rn(__fsub_rn(t, s), y);
         s = t;
     }
+    __device__ __forceinline__ void flush() {}
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// Block-compensated float32: the rectangle terms are summed by FMA into a
+// float32 partial over a block of at most 16 rectangles (one unrolled body
+// of the walk loop, or the loop's remainder), and each block partial is
+// added into a Kahan (sum, compensation) pair.  A block of k terms adds at
+// most k*u*sum|terms| to the error, the Kahan stage 2u*sum|blocks|, so the
+// total stays below about 18u * sum|terms| (1.1e-6 relative for the L_p
+// integrands) at a quarter of the per-rectangle compensation work.
+template <> struct Acc<kF32B> {
+    float part = 0.f, s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float h, float dt) { part = fmaf(h, dt, part); }
+    __device__ __forceinline__ void flush()
+    {
+        const float y = __fsub_rn(part, c);
+        const float t = __fadd_rn(s, y);
+        c = __fsub_rn(__fsub_rn(t, s), y);
+        s = t;
+        part = 0.f;
+    }
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
@@ -111,6 +135,24 @@ __device__ __forceinline__ void accumulate(Acc<PREC>* acc, T a, T b, T dt, T p)
     if constexpr (combo_n(COMBO) > 1) acc[1].add(term_h<combo_metric(COMBO, 1)>(a, b, d, p), dt);
     if constexpr (combo_n(COMBO) > 2) acc[2].add(term_h<combo_metric(COMBO, 2)>(a, b, d, p), dt);
 }
+
+// Accumulators of one walk.  The generic form keeps one Acc per metric.
+template <int PREC, int COMBO>
+struct AccSet {
+    static constexpr int NM = combo_n(COMBO);
+    Acc<PREC> a[NM];
+    template <typename T>
+    __device__ __forceinline__ void add(T va, T vb, T dt, T p) { accumulate<COMBO, PREC>(a, va, vb, dt, p); }
+    __device__ __forceinline__ void flush()
+    {
+#pragma unroll
+        for (int m = 0; m < NM; ++m) a[m].flush();
+    }
+    __device__ __forceinline__ double value(int m) const { return a[m].value(); }
+};
+
+template <int PREC, int COMBO>
+struct AccFor { using type = AccSet<PREC, COMBO>; };
 
 // Exact "x ends after y" for interval ends (non-negative, +inf allowed).
 // float64 compares go to the integer pipe through the bit patterns, which
@@ -217,7 +259,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const Wal
     static_assert(THREADS == 1024 || THREADS == 512, "thread count");
 
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int32_t sS[kTilePcfs], sNext[kTilePcfs], sLen[kTilePcfs];
+    __shared__ int32_t sS[kTilePcfs], sNext[kTilePcfs], sLen[kTilePcfs], sStaged[kTilePcfs];
     __shared__ int64_t sOff[kTilePcfs];
     __shared__ T sT1part[2];
     __shared__ int64_t sTile;
@@ -266,20 +308,24 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const Wal
                 sOff[tid] = 0;
             }
             sS[tid] = 0;
+            sNext[tid] = 0;
+            sStaged[tid] = -1;   // window start of what is in shared memory
         }
         const bool lane_valid = (bi * kTile + my_r < a.n_r) && (col0 + my_c < a.n_c);
 
-        Acc<PREC> acc[NM];
+        typename AccFor<PREC, COMBO>::type acc;
         T tc = T(0);
         T T0 = T(0);            // start of the current window (block-uniform)
         __syncthreads();
 
-        for (;;) {
-            // ---- window end T1 = min over PCFs of te[S + W - 1] (clamped) ----
+        for (bool first = true;; first = false) {
+            // ---- advance the window starts; window end T1 = min over PCFs of
+            //      te[S + W - 1] (clamped to the last element) ----
             if (tid < 64) {
                 T cand = T(INFINITY);
                 const int len = tid < NPCF ? sLen[tid] : 0;
                 if (len > 0) {
+                    if (!first) sS[tid] = sNext[tid];
                     int idx = sS[tid] + W - 1;
                     if (idx > len - 1) idx = len - 1;
                     cand = (tid < kTile ? packR : packC)[sOff[tid] + idx].x;
@@ -299,7 +345,8 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const Wal
                 return;
             }
 
-            // ---- stage elements [S, S + min(W, len - S)) of the unit's PCFs ----
+            // ---- stage elements [S, S + min(W, len - S)) of the PCFs whose
+            //      window start moved (the others are still in place) ----
             // THREADS is a multiple of 16, so a thread always serves the same
             // slot (tid & 15) of each region and walks k in steps of THREADS/16.
             {
@@ -307,8 +354,9 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const Wal
 #pragma unroll 1
                 for (int region = 0; region < NPCF / kGroup; ++region) {
                     const int p = region * kGroup + slot;
-                    const int len = sLen[p];
                     const int S = sS[p];
+                    if (S == sStaged[p]) continue;
+                    const int len = sLen[p];
                     int kend = len - S;
                     if (kend > W) kend = W;
                     const E* src = (p < kTile ? packR : packC) + sOff[p] + S;
@@ -336,6 +384,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const Wal
                     next = sS[tid] + lo;
                 }
                 sNext[tid] = next;
+                sStaged[tid] = sS[tid];
             }
             __syncthreads();
 
@@ -351,7 +400,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const Wal
                     const T tn = first_end(tf, tg);                               \
                     const T dt = tn - tc;                                         \
                     tc = tn;                                                      \
-                    accumulate<COMBO, PREC, T>(acc, vf, vg, dt, p0);              \
+                    acc.add(vf, vg, dt, p0);                                      \
                     advance_cursor<kRow>(af, tf, vf, ag, tg, vg);                 \
                 }
 #pragma unroll 1
@@ -360,17 +409,17 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const Wal
                     PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
                     PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
                     PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
+                    acc.flush();
                 }
 #pragma unroll 1
                 for (; cnt > 0; --cnt) PCF_WALK_STEP()
+                acc.flush();
 #undef PCF_WALK_STEP
             }
             const bool last = !(T1 < T(INFINITY));
             __syncthreads();
             if (last) break;
             T0 = T1;
-            if (tid < NPCF) sS[tid] = sNext[tid];
-            __syncthreads();
         }
 
         // ---- tail, root, output ----
@@ -383,7 +432,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const Wal
 #pragma unroll
             for (int m = 0; m < NM; ++m) {
                 const int MI = combo_metric(COMBO, m);
-                double I = acc[m].value();
+                double I = acc.value(m);
                 const T h = (MI == MI_GRAM) ? vlf * vlg : fabs(vlf - vlg);
                 if (h != T(0)) I = (h > T(0)) ? (double)INFINITY : -(double)INFINITY;
                 const double F = finalize_root(a.metric[m], a.root[m], a.p[m], I);

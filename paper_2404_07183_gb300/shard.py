@@ -18,9 +18,29 @@ import numpy as np
 TILE = 32
 
 
-def sorted_order(lengths) -> np.ndarray:
-    """Input index of the s-th shortest PCF (stable, as the device sort)."""
-    return np.argsort(np.asarray(lengths), kind="stable")
+SCALE_SORT_MIN = 256
+
+
+def sort_keys(lengths, last_times=None):
+    """(length bucket, time-scale key) of the device's stable sort: lengths up
+    to 256 as they are, longer ones in buckets of 32, ordered among
+    themselves by the float32 bits of their last breakpoint time when the
+    collection has any PCF longer than 256."""
+    lengths = np.asarray(lengths, dtype=np.int64)
+    hi = np.where(lengths <= SCALE_SORT_MIN, lengths,
+                  SCALE_SORT_MIN + ((lengths - SCALE_SORT_MIN) >> 5))
+    lo = np.zeros(lengths.size, dtype=np.uint32)
+    if last_times is not None and lengths.size and lengths.max() > SCALE_SORT_MIN:
+        tl = np.asarray(last_times, dtype=np.float64).astype(np.float32)
+        bits = np.where((tl > 0) & np.isfinite(tl), tl, np.float32(0)).view(np.uint32)
+        lo = np.where(lengths > SCALE_SORT_MIN, bits, np.uint32(0)).astype(np.uint32)
+    return hi, lo
+
+
+def sorted_order(lengths, last_times=None) -> np.ndarray:
+    """Input index of the s-th PCF in the device's sort order (stable)."""
+    hi, lo = sort_keys(lengths, last_times)
+    return np.lexsort((lo, hi))
 
 
 def tile_order(n: int):
@@ -42,11 +62,12 @@ def shard_units(nunits: int, index: int, count: int) -> range:
     return range(index, nunits, count)
 
 
-def shard_pairs(lengths, index: int, count: int):
+def shard_pairs(lengths, index: int, count: int, last_times=None):
     """Unordered pairs (i, j), i <= j, in input indices, owned by a shard of
-    the tile kernels."""
+    the tile kernels (``last_times``: each PCF's last breakpoint time, needed
+    when some PCF is longer than 256)."""
     n = len(lengths)
-    perm = sorted_order(lengths)
+    perm = sorted_order(lengths, last_times)
     tiles = tile_order(n)
     owned = set()
     for u in shard_units(len(tiles), index, count):

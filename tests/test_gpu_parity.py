@@ -17,7 +17,7 @@ from conftest import gpu_available, max_rel_error, read_golden
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32c": 1e-5, "f32": 5e-4}
+TOL = {"f64": 1e-12, "f32c": 1e-5, "f32b": 1e-5, "f32": 5e-4}
 
 
 @pytest.fixture(scope="module")
@@ -75,7 +75,7 @@ def test_worked_example_sec5_2(pcf):
 METRICS = ["l1", "l2", "gram", ("lp", 3.0), ("lp", 3.5), ("l2", False), ("lp", 2.5, False)]
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32c", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32c", "f32b", "f32"])
 @pytest.mark.parametrize("m", METRICS, ids=str)
 def test_random_sets_vs_oracle(pcf, prec, m):
     import torch
@@ -87,7 +87,7 @@ def test_random_sets_vs_oracle(pcf, prec, m):
     assert err <= tol, (err, tol)
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32c"])
+@pytest.mark.parametrize("prec", ["f64", "f32c", "f32b"])
 @pytest.mark.parametrize("m", ["l1", "l2", "gram", ("lp", 3.0, False), ("l2", False)], ids=str)
 def test_dyadic_bitwise(pcf, prec, m):
     """Integer gaps/values with many shared breakpoints: every integral is an
@@ -140,7 +140,7 @@ def test_upper_packed_layout(pcf, prec):
         np.testing.assert_array_equal(u.cpu().numpy(), f[iu])
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32c"])
+@pytest.mark.parametrize("prec", ["f64", "f32c", "f32b"])
 def test_long_pcfs_use_several_windows(pcf, prec):
     """Lengths well beyond one shared-memory window (about 450 float32 or 220
     float64 elements per PCF) so that the time-window staging is exercised."""
@@ -240,7 +240,7 @@ def test_float32_input_all_precisions(pcf):
     s = synth.lognormal(400, max_len=1200)
     x = _dev(pcf, s)
     want = _oracle(s, "gram")
-    for prec in ("f64", "f32c", "f32"):
+    for prec in ("f64", "f32c", "f32b", "f32"):
         got = pcf.pcf_pairwise(x, ["gram"], precision=prec, out_dtype=torch.float64)[0]
         err = max_rel_error("gram", got.cpu().numpy(), want, _gram_diag(s))
         assert err <= TOL[prec], (prec, err)
@@ -275,7 +275,7 @@ def _sampled_check(s, mats, metrics, prec, npairs, seed, layout="full", gram_dia
             assert abs(got - want) / scale <= TOL[prec], (name, i, j, got, want)
 
 
-@pytest.mark.parametrize("prec", ["f32c", "f64"])
+@pytest.mark.parametrize("prec", ["f32c", "f32b", "f64"])
 def test_stable_rank_full_size_sampled(pcf, prec):
     """N = 20,000 stable-rank-like PCFs, L1 + L2 + Gram in one fused walk."""
     import torch
@@ -284,7 +284,7 @@ def test_stable_rank_full_size_sampled(pcf, prec):
     mats = pcf.pcf_pairwise(x, ["l1", "l2", "gram"], precision=prec, out_dtype=torch.float32)
     mats = [m.cpu().numpy() for m in mats]
     diag = np.array([oracle.segment_sq(*s.pcf(i)) for i in range(s.n)])
-    _sampled_check(s, mats, ["l1", "l2", "gram"], prec if prec != "f64" else "f32c", 300, 7,
+    _sampled_check(s, mats, ["l1", "l2", "gram"], "f32c", 300, 7,
                    gram_diag=diag)
     for M in mats[:2]:
         assert np.all(np.diag(M) == 0)
@@ -301,3 +301,20 @@ def test_lognormal_sampled_upper_packed(pcf):
                          out_dtype=torch.float32)[0].cpu().numpy()
     diag = np.array([oracle.segment_sq(*s.pcf(i)) for i in range(s.n)])
     _sampled_check(s, [M], ["gram"], "f32c", 300, 8, layout="upper", gram_diag=diag)
+
+
+def test_cuda_graph_replay_with_new_contents(pcf):
+    """One captured graph, replayed after new PCF contents of the same shape
+    are copied into the input tensors."""
+    import torch
+    a = synth.random_set(80, seed=61, min_len=3, max_len=30)
+    b = synth.PcfSet(a.offsets, a.times * 2.0, -a.values)
+    x = _dev(pcf, a)
+    g = pcf.PairwiseGraph(x, ["l1", "gram"], precision="f64", out_dtype=torch.float64)
+    for s in (a, b, a):
+        x.times.copy_(torch.from_numpy(s.times))
+        x.values.copy_(torch.from_numpy(s.values))
+        l1, gram = [o.clone() for o in g.replay()]
+        g.check()
+        assert max_rel_error("l1", l1.cpu().numpy(), _oracle(s, "l1")) <= 1e-12
+        assert max_rel_error("gram", gram.cpu().numpy(), _oracle(s, "gram"), _gram_diag(s)) <= 1e-12

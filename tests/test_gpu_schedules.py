@@ -14,7 +14,7 @@ from conftest import gpu_available, max_rel_error
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"f64": 1e-12, "f32c": 1e-5, "f32": 5e-4}
+TOL = {"f64": 1e-12, "f32c": 1e-5, "f32b": 1e-5, "f32": 5e-4}
 SCHEDULES = ["tile1024", "tile512x2", "mergepath", ("tile1024", 8), ("tile512x2", 24),
              ("tile1024", 0)]
 
@@ -41,7 +41,7 @@ def data():
     return s, want, diag
 
 
-@pytest.mark.parametrize("prec", ["f64", "f32c", "f32"])
+@pytest.mark.parametrize("prec", ["f64", "f32c", "f32b", "f32"])
 @pytest.mark.parametrize("sched", SCHEDULES, ids=str)
 def test_schedule_parity(pcf, data, prec, sched):
     import torch

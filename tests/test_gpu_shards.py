@@ -29,3 +29,31 @@ def test_shards_sum_to_the_whole(sched, world):
             t += p_
     for t, w in zip(total, whole):
         np.testing.assert_array_equal(t.cpu().numpy(), w.cpu().numpy())
+
+
+def test_host_mirror_matches_device_ownership():
+    """The host mirror of the sort (length, then time scale for PCFs longer
+    than 256 points) and of the tile order names exactly the entries the
+    device writes for a shard."""
+    if not gpu_available():
+        pytest.skip("no CUDA device")
+    import torch
+    import paper_2404_07183_gb300 as P
+    rng = np.random.default_rng(7)
+    lens = np.concatenate([rng.integers(2, 60, 60), rng.integers(257, 700, 40)])
+    scales = np.exp(rng.normal(0, 1.5, lens.size))
+    s = synth.from_lengths(lens, lambda r, m: r.exponential(1.0, m),
+                           lambda r, o: r.standard_normal(o[-1]) + 3.0, rng, np.float64, "scaled")
+    t = s.times.copy()
+    for i in range(s.n):
+        a, b = int(s.offsets[i]), int(s.offsets[i + 1])
+        t[a:b] *= scales[i]
+    s = synth.PcfSet(s.offsets, t, s.values)
+    x = P.PcfTensors.from_numpy(s, "cuda")
+    last = s.times[s.offsets[1:] - 1]
+    for r in range(3):
+        part = shard.pairwise_shard(x, ["gram"], r, 3, precision="f64",
+                                    out_dtype=torch.float64, schedule="tile1024")[0].cpu().numpy()
+        got = {(i, j) for i, j in zip(*np.nonzero(part)) if i <= j}
+        want = shard.shard_pairs(s.lengths(), r, 3, last_times=last)
+        assert got == want
