@@ -516,7 +516,7 @@ def run_workload(name, args):
                      cpu_baseline=_cpu_rows(s, ["l1"], seconds_target=4.0))
 
     if name == "lognormal":
-        s = synth.lognormal()
+        s = synth.lognormal(n_pcfs=args.n or 100000)
         N = s.n
         steps_walk, diag = exact_walk_steps(s)
         x = P.PcfTensors.from_numpy(s, dev)
@@ -524,7 +524,10 @@ def run_workload(name, args):
         o = [torch.empty((pairs,), dtype=torch.float32, device=dev)]
         res = {}
         from paper_2404_07183_gb300 import autotune
-        sched, tune_ms = autotune.tune_pairwise(x, ["gram"], "f32c", layout="upper", repeats=1)
+        if args.schedule:
+            sched, tune_ms = args.schedule, None
+        else:
+            sched, tune_ms = autotune.tune_pairwise(x, ["gram"], "f32c", layout="upper", repeats=1)
         for prec in ("f32c", "f32"):
             ws = torch.empty(P.pcf_workspace_size(x, None, prec), dtype=torch.uint8, device=dev)
             mids = []
@@ -556,7 +559,8 @@ def run_workload(name, args):
                                "note": f"whole step; tally {tally} ops/step (Gram, Kahan)"},
                      f32={"ms_per_step": res["f32"], "value": pairs / (res["f32"] * 1e-3),
                           "frac": (steps_walk + diag) / (res["f32"] * 1e-3) / issue(5 + 2)},
-                     cpu_baseline=_cpu_rows(s, ["gram"], seconds_target=8.0, row0=N // 2))
+                     cpu_baseline=(None if args.no_cpu else
+                                   _cpu_rows(s, ["gram"], seconds_target=8.0, row0=N // 2)))
 
     if name == "appendix_a":
         s = synth.appendix_a(n_pcfs=args.n or 50000)
@@ -568,8 +572,11 @@ def run_workload(name, args):
         from paper_2404_07183_gb300 import autotune
         res = {}
         for prec in ("f32c", "f32", "f64"):
-            sched, tune_ms = autotune.tune_pairwise(x, ["l1"], prec, repeats=1,
-                                                    candidates=(("tile1024", 0), ("tile512x2", 0)))
+            if args.schedule:
+                sched = args.schedule
+            else:
+                sched, _ = autotune.tune_pairwise(x, ["l1"], prec, repeats=1,
+                                                  candidates=(("tile1024", 0), ("tile512x2", 0)))
             ws = torch.empty(P.pcf_workspace_size(x, None, prec), dtype=torch.uint8, device=dev)
 
             def step():
@@ -598,7 +605,7 @@ def run_workload(name, args):
                      cpu_baseline=_cpu_rows(s, ["l1"], seconds_target=8.0, row0=N // 3))
 
     if name == "gradient":
-        s, G = synth.gradient()
+        s, G = synth.gradient(n_pcfs=args.n or 4096)
         N = s.n
         steps_walk, diag = exact_walk_steps(s)
         x = P.PcfTensors.from_numpy(s, dev)
@@ -612,8 +619,9 @@ def run_workload(name, args):
         import oracle
         sub = synth.subset(s, np.arange(300))
         t0 = time.perf_counter()
-        oracle.backward(sub, G[:300, :300], metric="l2", p=2.0)
-        dt = time.perf_counter() - t0
+        if not args.no_cpu:
+            oracle.backward(sub, G[:300, :300], metric="l2", p=2.0)
+        dt = max(time.perf_counter() - t0, 1e-9)
         return _line(name, pairs / (ms * 1e-3), "pair-gradients/s", ms, args.steps, args.warmup,
                      "f64", {"workload": "gradient N=4096 n~U{20..200} Exp(1) N(0,1) float64, "
                              "d(sum G*D2^2)/d(values, times)", "N": N, "pairs": pairs,
@@ -686,7 +694,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f32c", choices=["f32c", "f32", "f64"])
+    ap.add_argument("--precision", default="f32c", choices=["f32c", "f32b", "f32", "f64"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=48)

@@ -107,15 +107,18 @@ enum pcf_cross_flags {
 
 /* Work decomposition of the walk (pcf_pairwise_ex / pcf_cross_ex).
  *   PCF_SCHED_TILE_1024   32 x 32 pair tiles, one 1024-thread CTA per SM
- *   PCF_SCHED_TILE_512X2  32 x 32 pair tiles, two 512-thread CTAs per SM
+ *   PCF_SCHED_TILE_512X2  32 x 16 half tiles, two 512-thread CTAs per SM
  *                         (half the shared memory each: smaller windows)
+ *   PCF_SCHED_TILE_512X3  32 x 16 half tiles, three 512-thread CTAs per SM
+ *                         (at most 40 registers per thread, a third of the
+ *                         shared memory each)
  *   PCF_SCHED_MERGEPATH   one warp per pair, the pair's merge split across
  *                         the 32 lanes (for few, long pairs)
  *   PCF_SCHED_AUTO        merge path when there are fewer tiles than half the
  *                         SMs, else TILE_1024 */
 enum pcf_sched_kernel {
     PCF_SCHED_AUTO = 0, PCF_SCHED_TILE_1024 = 1, PCF_SCHED_TILE_512X2 = 2,
-    PCF_SCHED_MERGEPATH = 3
+    PCF_SCHED_MERGEPATH = 3, PCF_SCHED_TILE_512X3 = 4
 };
 
 typedef struct pcf_schedule {

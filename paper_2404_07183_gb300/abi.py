@@ -35,6 +35,7 @@ SYMBOLS = ("pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross", "pc
            "pcf_check", "pcf_status_string", "pcf_version", "pcf_pairwise_noalloc",
            "pcf_pairwise_ex", "pcf_cross_ex")
 PCF_SCHED_AUTO, PCF_SCHED_TILE_1024, PCF_SCHED_TILE_512X2, PCF_SCHED_MERGEPATH = 0, 1, 2, 3
+PCF_SCHED_TILE_512X3 = 4
 PCF_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 

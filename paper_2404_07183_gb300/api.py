@@ -22,6 +22,7 @@ import torch
 from . import abi
 
 __all__ = ["PcfError", "PcfTensors", "pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross",
+           "pcf_cross_to_host",
            "pcf_pairwise_backward", "pcf_check", "PairwiseFn", "PairwiseGraph", "pdist",
            "l2_kernel",
            "parse_metric", "PRECISIONS"]
@@ -100,7 +101,8 @@ def parse_metric(m):
 
 
 SCHEDULES = {"auto": abi.PCF_SCHED_AUTO, "tile1024": abi.PCF_SCHED_TILE_1024,
-             "tile512x2": abi.PCF_SCHED_TILE_512X2, "mergepath": abi.PCF_SCHED_MERGEPATH}
+             "tile512x2": abi.PCF_SCHED_TILE_512X2, "tile512x3": abi.PCF_SCHED_TILE_512X3,
+             "mergepath": abi.PCF_SCHED_MERGEPATH}
 
 
 def _schedule(schedule, shard=None):
@@ -277,6 +279,55 @@ def pcf_pairwise_backward(x: PcfTensors, metric, grad_out: torch.Tensor, fwd_out
     if check:
         pcf_check(ws, stream, "pcf_pairwise_backward")
     return gv, gt
+
+
+def pcf_cross_to_host(a: PcfTensors, b: PcfTensors, metrics=("l1",), precision="f32c",
+                      block_rows=2048, out_dtype=torch.float32, host_out=None, schedule=None,
+                      check=True):
+    """Cross matrices a x b streamed to pinned host memory block by block.
+
+    Row blocks of ``a`` are computed with ``pcf_cross`` into two alternating
+    device buffers; while block k+1 is computed, block k is copied to the
+    host on a separate stream (b is validated and packed once, then reused).
+    Returns the host tensors (``a.n`` x ``b.n`` per metric)."""
+    if isinstance(metrics, (str, tuple)):
+        metrics = [metrics]
+    metrics = list(metrics)
+    dev = b.times.device
+    na, nb = a.n, b.n
+    if host_out is None:
+        host_out = [torch.empty((na, nb), dtype=out_dtype).pin_memory() for _ in metrics]
+    if na == 0 or nb == 0:
+        return host_out
+    rows = max(1, min(block_rows, na))
+    bufs = [[torch.empty((rows, nb), dtype=out_dtype, device=dev) for _ in metrics]
+            for _ in range(2)]
+    ws = torch.empty(max(pcf_workspace_size(a, b, precision), 256), dtype=torch.uint8, device=dev)
+    compute = torch.cuda.current_stream(dev)
+    copy = torch.cuda.Stream(dev)
+    freed = [None, None]
+    for k, r0 in enumerate(range(0, na, rows)):
+        r1 = min(na, r0 + rows)
+        slot = k % 2
+        if freed[slot] is not None:
+            compute.wait_event(freed[slot])
+        views = [t[: r1 - r0] for t in bufs[slot]]
+        pcf_cross(a, b, r0, r1, metrics, precision=precision, out=views, workspace=ws,
+                  reuse_b=k > 0, check=False, schedule=schedule)
+        done = torch.cuda.Event()
+        done.record(compute)
+        copy.wait_event(done)
+        with torch.cuda.stream(copy):
+            for h, v in zip(host_out, views):
+                h[r0:r1].copy_(v, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(copy)
+        freed[slot] = ev
+    compute.wait_stream(copy)
+    if check:
+        pcf_check(ws, what="pcf_cross_to_host")
+        copy.synchronize()
+    return host_out
 
 
 class PairwiseFn(torch.autograd.Function):

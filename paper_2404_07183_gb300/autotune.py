@@ -19,7 +19,7 @@ import torch
 
 from . import api
 
-CANDIDATES = (("tile1024", 0), ("tile512x2", 0), ("mergepath", 0))
+CANDIDATES = (("tile1024", 0), ("tile512x2", 0), ("tile512x3", 0), ("mergepath", 0))
 _lock = threading.Lock()
 
 
@@ -81,6 +81,11 @@ def tune_pairwise(x: api.PcfTensors, metrics, precision="f32c", layout="full",
     ws = api.pcf_prepare(x, precision)
     api.pcf_check(ws)
     n = x.n
+    # the merge path only pays when the tiles cannot occupy the GPU
+    nb = (n + 31) // 32
+    sms = torch.cuda.get_device_properties(x.times.device).multi_processor_count
+    if nb * (nb + 1) // 2 >= 2 * sms:
+        candidates = tuple(c for c in candidates if c[0] != "mergepath") or candidates
     shape = (n, n) if layout == "full" else (n * (n + 1) // 2,)
     outs = [torch.empty(shape, dtype=out_dtype, device=x.times.device) for _ in metrics]
     stream = torch.cuda.current_stream()

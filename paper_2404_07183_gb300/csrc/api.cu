@@ -144,7 +144,7 @@ int check_requests(const pcf_integral* F, int nF, bool need_out)
 int check_schedule(const pcf_schedule* sc)
 {
     if (!sc) return PCF_OK;
-    if (sc->kernel < PCF_SCHED_AUTO || sc->kernel > PCF_SCHED_MERGEPATH) return PCF_EINVAL;
+    if (sc->kernel < PCF_SCHED_AUTO || sc->kernel > PCF_SCHED_TILE_512X3) return PCF_EINVAL;
     if (sc->window != 0 && sc->window < 8) return PCF_EINVAL;
     if (sc->shard_count < 0 || sc->shard_index < 0) return PCF_EINVAL;
     if (sc->shard_count > 1 && sc->shard_index >= sc->shard_count) return PCF_EINVAL;
@@ -173,8 +173,9 @@ int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int el
         if (grid > need) grid = need;
         if (grid < 1) return PCF_OK;
     } else {
-        const int ctas = kernel == PCF_SCHED_TILE_512X2 ? 2 : 1;
-        const int regions = kernel == PCF_SCHED_TILE_512X2 ? 3 : 4;   // 32 x 16 or 32 x 32 units
+        const bool half = kernel == PCF_SCHED_TILE_512X2 || kernel == PCF_SCHED_TILE_512X3;
+        const int ctas = kernel == PCF_SCHED_TILE_512X3 ? 3 : (half ? 2 : 1);
+        const int regions = half ? 3 : 4;   // 32 x 16 or 32 x 32 units
         int dev = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
@@ -189,7 +190,7 @@ int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int el
         wa.window = W;
         smem = (size_t)regions * (size_t)W * kGroup * (size_t)elem_bytes;
         grid = (int64_t)sms * ctas;
-        const int64_t units = wa.ntiles * (kernel == PCF_SCHED_TILE_512X2 ? 2 : 1);
+        const int64_t units = wa.ntiles * (half ? 2 : 1);
         if (grid > units) grid = units;
         if (grid < 1) return PCF_OK;
     }
@@ -210,6 +211,11 @@ int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int el
             else if (precision == PCF_PREC_F32_COMP) e = launch_mergepath_f32c(L.combo, wa, npairs, g, s);
             else if (precision == PCF_PREC_F32_BLOCK) e = launch_mergepath_f32b(L.combo, wa, npairs, g, s);
             else e = launch_mergepath_f32(L.combo, wa, npairs, g, s);
+        } else if (kernel == PCF_SCHED_TILE_512X3) {
+            if (precision == PCF_PREC_F64) e = launch_walk_f64_t512x3(L.combo, wa, g, smem, s);
+            else if (precision == PCF_PREC_F32_COMP) e = launch_walk_f32c_t512x3(L.combo, wa, g, smem, s);
+            else if (precision == PCF_PREC_F32_BLOCK) e = launch_walk_f32b_t512x3(L.combo, wa, g, smem, s);
+            else e = launch_walk_f32_t512x3(L.combo, wa, g, smem, s);
         } else if (kernel == PCF_SCHED_TILE_512X2) {
             if (precision == PCF_PREC_F64) e = launch_walk_f64_t512(L.combo, wa, g, smem, s);
             else if (precision == PCF_PREC_F32_COMP) e = launch_walk_f32c_t512(L.combo, wa, g, smem, s);

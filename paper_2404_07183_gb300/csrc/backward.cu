@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BackArgs a)
         if (bi == bj && r > c) continue;
         const int64_t i = a.perm[gi], j = a.perm[gj];
         const int64_t of = a.poff[gi], og = a.poff[gj];
-        const int nf = a.slen[gi], ng = a.slen[gj];
+        const int nf = a.slen[gi];
 
         if (gi == gj) {
             if (METRIC != PCF_GRAM) continue;

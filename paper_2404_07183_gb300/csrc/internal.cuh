@@ -122,6 +122,7 @@ enum Combo : int {
 #define PCF_DECL_WALK(name)                                                                     \
     cudaError_t launch_walk_##name##_t1024(int, const WalkArgs&, int, size_t, cudaStream_t);    \
     cudaError_t launch_walk_##name##_t512(int, const WalkArgs&, int, size_t, cudaStream_t);     \
+    cudaError_t launch_walk_##name##_t512x3(int, const WalkArgs&, int, size_t, cudaStream_t);   \
     cudaError_t launch_mergepath_##name(int, const WalkArgs&, int64_t, int, cudaStream_t);
 PCF_DECL_WALK(f64)
 PCF_DECL_WALK(f32c)

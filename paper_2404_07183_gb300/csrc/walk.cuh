@@ -240,6 +240,8 @@ __device__ __forceinline__ void decode_tile(const WalkArgs& a, int64_t t, int64_
     }
 }
 
+// CTAS: resident CTAs per SM the launch is built for (1 for 1024 threads; 2 or
+// 3 for 512 threads, which caps the registers at 64 or 40 per thread).
 // THREADS = 1024: one CTA per SM; a work unit is a whole 32 x 32 tile and
 // warp w walks its diagonal w (lane l: row (l + w) mod 32, column l).
 // THREADS = 512: two CTAs per SM, each with half the shared memory; a work
@@ -247,8 +249,8 @@ __device__ __forceinline__ void decode_tile(const WalkArgs& a, int64_t t, int64_
 // four, so the window stays larger), and warp w walks lane l's pair
 // (row (l + w) mod 32, column l mod 16).  Both halves of a tile belong to the
 // same shard.
-template <typename T, int PREC, int COMBO, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const WalkArgs a)
+template <typename T, int PREC, int COMBO, int THREADS, int CTAS>
+__global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
 {
     using E = typename ElemOf<T>::type;
     constexpr int NM = combo_n(COMBO);
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS) walk_kernel(const Wal
     }
 }
 
-template <typename T, int PREC, int THREADS>
+template <typename T, int PREC, int THREADS, int CTAS = 1024 / THREADS>
 cudaError_t launch_walk_tt(int combo, const WalkArgs& a, int grid, size_t smem, cudaStream_t s)
 {
     auto go = [&](auto kern) -> cudaError_t {
@@ -467,13 +469,13 @@ cudaError_t launch_walk_tt(int combo, const WalkArgs& a, int grid, size_t smem, 
         return cudaGetLastError();
     };
     switch (combo) {
-    case kComboL1: return go(walk_kernel<T, PREC, kComboL1, THREADS>);
-    case kComboL2: return go(walk_kernel<T, PREC, kComboL2, THREADS>);
-    case kComboGram: return go(walk_kernel<T, PREC, kComboGram, THREADS>);
-    case kComboLP: return go(walk_kernel<T, PREC, kComboLP, THREADS>);
-    case kComboL3: return go(walk_kernel<T, PREC, kComboL3, THREADS>);
-    case kComboL1L2Gram: return go(walk_kernel<T, PREC, kComboL1L2Gram, THREADS>);
-    case kComboL1L2L3: return go(walk_kernel<T, PREC, kComboL1L2L3, THREADS>);
+    case kComboL1: return go(walk_kernel<T, PREC, kComboL1, THREADS, CTAS>);
+    case kComboL2: return go(walk_kernel<T, PREC, kComboL2, THREADS, CTAS>);
+    case kComboGram: return go(walk_kernel<T, PREC, kComboGram, THREADS, CTAS>);
+    case kComboLP: return go(walk_kernel<T, PREC, kComboLP, THREADS, CTAS>);
+    case kComboL3: return go(walk_kernel<T, PREC, kComboL3, THREADS, CTAS>);
+    case kComboL1L2Gram: return go(walk_kernel<T, PREC, kComboL1L2Gram, THREADS, CTAS>);
+    case kComboL1L2L3: return go(walk_kernel<T, PREC, kComboL1L2L3, THREADS, CTAS>);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -1,0 +1,9 @@
+// walk_f64_t512x3.cu -- tile walk instantiations: F64 precision, 512-thread CTAs, 3 per SM.
+#include "walk.cuh"
+
+namespace pcfgb {
+cudaError_t launch_walk_f64_t512x3(int combo, const WalkArgs& a, int grid, size_t smem, cudaStream_t s)
+{
+    return launch_walk_tt<double, kF64, 512, 3>(combo, a, grid, smem, s);
+}
+}  // namespace pcfgb

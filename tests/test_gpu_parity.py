@@ -318,3 +318,26 @@ def test_cuda_graph_replay_with_new_contents(pcf):
         g.check()
         assert max_rel_error("l1", l1.cpu().numpy(), _oracle(s, "l1")) <= 1e-12
         assert max_rel_error("gram", gram.cpu().numpy(), _oracle(s, "gram"), _gram_diag(s)) <= 1e-12
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32c"])
+def test_cross_streamed_to_host(pcf, prec):
+    """Row blocks double-buffered on the device and copied to pinned host
+    memory; the host result is the whole cross matrix."""
+    import torch
+    a = synth.random_set(131, seed=62, max_len=70)
+    b = synth.random_set(57, seed=63, max_len=90)
+    xa, xb = _dev(pcf, a), _dev(pcf, b)
+    host = pcf.pcf_cross_to_host(xa, xb, ["l1", "gram"], precision=prec, block_rows=40,
+                                 out_dtype=torch.float64)
+    assert host[0].is_pinned()
+    for m, h in zip(("l1", "gram"), host):
+        want = _oracle(a, m, b)
+        if m == "gram":
+            da = np.array([oracle.segment_sq(*a.pcf(i)) for i in range(a.n)])
+            db = np.array([oracle.segment_sq(*b.pcf(j)) for j in range(b.n)])
+            scale = np.sqrt(np.outer(da, db))
+            err = np.max(np.abs(h.numpy() - want) / np.where(scale > 0, scale, 1.0))
+        else:
+            err = max_rel_error(m, h.numpy(), want)
+        assert err <= TOL[prec], (m, err)

@@ -15,8 +15,8 @@ from conftest import gpu_available, max_rel_error
 pytestmark = pytest.mark.gpu
 
 TOL = {"f64": 1e-12, "f32c": 1e-5, "f32b": 1e-5, "f32": 5e-4}
-SCHEDULES = ["tile1024", "tile512x2", "mergepath", ("tile1024", 8), ("tile512x2", 24),
-             ("tile1024", 0)]
+SCHEDULES = ["tile1024", "tile512x2", "tile512x3", "mergepath", ("tile1024", 8),
+             ("tile512x2", 24), ("tile512x3", 40)]
 
 
 @pytest.fixture(scope="module")
@@ -104,7 +104,7 @@ def test_autotune_picks_and_caches(pcf, tmp_path):
     x = pcf.PcfTensors.from_numpy(s, "cuda")
     path = str(tmp_path / "tune.json")
     name, timings = autotune.tune_pairwise(x, ["l1", "gram"], "f32c", path=path)
-    assert name in {"tile1024", "tile512x2", "mergepath"} and set(timings) >= {name}
+    assert name in {"tile1024", "tile512x2", "tile512x3", "mergepath"} and set(timings) >= {name}
     assert autotune.schedule_for(x, ["gram", "l1"], "f32c", path=path, tune=False) == name
     got = pcf.pcf_pairwise(x, ["l1", "gram"], precision="f32c", out_dtype=torch.float64,
                            schedule=name)

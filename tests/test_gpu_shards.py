@@ -10,7 +10,7 @@ from conftest import gpu_available
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("sched", ["tile1024", "tile512x2", "mergepath"])
+@pytest.mark.parametrize("sched", ["tile1024", "tile512x2", "tile512x3", "mergepath"])
 @pytest.mark.parametrize("world", [2, 3])
 def test_shards_sum_to_the_whole(sched, world):
     if not gpu_available():
