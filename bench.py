@@ -255,7 +255,7 @@ def run_ours(args):
             e_mid = torch.cuda.Event(enable_timing=True)
             e_mid.record(stream)
             P.pcf_pairwise(x, METRICS, precision=prec, out=outs, workspace=ws, prepared=True,
-                           check=False, schedule=sched)
+                           check=False, schedule=sched, layout=args.layout)
             return e_mid
 
         steps = args.steps if prec == args.precision else max(1, min(args.steps, 2))
@@ -297,6 +297,24 @@ def run_ours(args):
                          "prepare_ms": float(np.mean([a.elapsed_time(b) for a, b, c in evs])),
                          "steps": steps, "wall_s": t_wall, "clocks": clocks}
         del outs, ws
+
+    # same walk writing the matrices in the library's sort order (tiles land in
+    # contiguous blocks instead of being scattered by the permutation)
+    sorted_walk = None
+    if not args.no_fp64 and args.layout == "full":
+        prec = args.precision
+        outs_s = make_outs()
+        ws_s = torch.empty(P.pcf_workspace_size(x, None, prec), dtype=torch.uint8,
+                           device=f"cuda:{local}")
+        P.pcf_prepare(x, prec, workspace=ws_s)
+
+        def sstep():
+            P.pcf_pairwise(x, METRICS, precision=prec, out=outs_s, workspace=ws_s, prepared=True,
+                           check=False, schedule=results[prec]["schedule"], layout="sorted")
+        sms_ = _timed(sstep, 2, 1, flush, stream)
+        P.pcf_check(ws_s)
+        sorted_walk = float(np.mean(sms_))
+        del outs_s, ws_s
 
     if args.no_e2e:
         if rank == 0:
@@ -379,6 +397,11 @@ def run_ours(args):
         "pipe_peaks": pp,
         "clocks": head["clocks"],
     }
+    if sorted_walk is not None:
+        line["sorted_output"] = {"walk_ms": sorted_walk,
+                                 "merge_steps_per_s": walk_steps / (sorted_walk * 1e-3),
+                                 "note": "layout PCF_OUT_FULL_SORTED: same walk, matrices in "
+                                         "the library's sort order (perm from pcf_sort_order)"}
     if "f32b" in results and prec != "f32b":
         f = results["f32b"]
         wr = walk_steps / (f["walk_ms"] * 1e-3)
@@ -701,8 +724,10 @@ def main():
     ap.add_argument("--n", type=int, default=None,
                     help="smaller stable-rank collection (profiling runs); default 20000")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--layout", default="full", choices=["full", "sorted"],
+                    help="output layout of the timed walk (profiling runs)")
     ap.add_argument("--schedule", default=None,
-                    choices=["tile1024", "tile512x2", "mergepath", "auto"],
+                    choices=["tile1024", "tile512x2", "tile512x3", "mergepath", "auto"],
                     help="force a walk schedule instead of autotuning it")
     ap.add_argument("--workload", default="stable_rank",
                     choices=["stable_rank", "uniform_small", "lognormal", "gradient", "euler",

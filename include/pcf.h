@@ -84,8 +84,14 @@ enum pcf_precision {
 /* Output layout of the pairwise matrix. */
 enum pcf_layout {
     PCF_OUT_FULL = 0,          /* N x N row-major, both triangles written      */
-    PCF_OUT_UPPER_PACKED = 1   /* row-major upper triangle with the diagonal:
+    PCF_OUT_UPPER_PACKED = 1,  /* row-major upper triangle with the diagonal:
                                   (i, j), i <= j, at i*N - i*(i-1)/2 + (j - i) */
+    PCF_OUT_FULL_SORTED = 2    /* N x N row-major in the library's sort order:
+                                  entry (s, t) is F(x[perm[s]], x[perm[t]]) with
+                                  perm from pcf_sort_order.  The tiles then land
+                                  in contiguous blocks instead of being scattered
+                                  by the permutation, which keeps the output
+                                  writes near the output size in DRAM traffic */
 };
 
 /* Workspace purpose for pcf_workspace_size. */
@@ -241,6 +247,15 @@ int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root
                           const void* fwd_out, const void* grad_out, int grad_dtype,
                           void* grad_values, void* grad_times,
                           void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/*
+ * The sort order used by the last pcf_prepare / pcf_pairwise on `workspace`
+ * for collection x at `precision`: perm_out[s] (device, x->n int32) = input
+ * index of the s-th PCF (ascending length bucket, then time scale for PCFs
+ * longer than 256 points; stable).  Stream-ordered copy.
+ */
+int pcf_sort_order(const pcf_csr* x, int precision, const void* workspace,
+                   size_t workspace_bytes, int32_t* perm_out, cudaStream_t stream);
 
 /*
  * Synchronizes `stream` and returns the device-side status recorded in the

@@ -15,7 +15,7 @@ PCF_OK, PCF_EINVAL, PCF_ENOWS, PCF_ECUDA, PCF_ETIMEOUT, PCF_EUNSUPPORTED = range
 PCF_F32, PCF_F64 = 0, 1
 PCF_L1, PCF_L2, PCF_LP, PCF_GRAM = 0, 1, 2, 3
 PCF_PREC_F64, PCF_PREC_F32_COMP, PCF_PREC_F32, PCF_PREC_F32_BLOCK = 0, 1, 2, 3
-PCF_OUT_FULL, PCF_OUT_UPPER_PACKED = 0, 1
+PCF_OUT_FULL, PCF_OUT_UPPER_PACKED, PCF_OUT_FULL_SORTED = 0, 1, 2
 PCF_WS_FORWARD, PCF_WS_BACKWARD = 0, 1
 PCF_CROSS_REUSE_B = 1
 PCF_PAIRWISE_PREPARED = 1
@@ -33,7 +33,7 @@ ERR_DETAIL = {
 
 SYMBOLS = ("pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross", "pcf_pairwise_backward",
            "pcf_check", "pcf_status_string", "pcf_version", "pcf_pairwise_noalloc",
-           "pcf_pairwise_ex", "pcf_cross_ex")
+           "pcf_pairwise_ex", "pcf_cross_ex", "pcf_sort_order")
 PCF_SCHED_AUTO, PCF_SCHED_TILE_1024, PCF_SCHED_TILE_512X2, PCF_SCHED_MERGEPATH = 0, 1, 2, 3
 PCF_SCHED_TILE_512X3 = 4
 PCF_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -92,6 +92,8 @@ def load(build_if_missing: bool = False):
         lib.pcf_pairwise_ex.argtypes = [CSR, INT, I, I, I, I, I, SCH, P, SZ, P]
         lib.pcf_cross_ex.restype = I
         lib.pcf_cross_ex.argtypes = [CSR, CSR, I64, I64, INT, I, I, I64, I, I, SCH, P, SZ, P]
+        lib.pcf_sort_order.restype = I
+        lib.pcf_sort_order.argtypes = [CSR, I, P, SZ, P, P]
         lib.pcf_prepare.restype = I
         lib.pcf_prepare.argtypes = [CSR, I, P, SZ, P]
         lib.pcf_cross.restype = I

@@ -21,7 +21,8 @@ import torch
 
 from . import abi
 
-__all__ = ["PcfError", "PcfTensors", "pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross",
+__all__ = ["PcfError", "PcfTensors", "pcf_workspace_size", "pcf_prepare", "pcf_sort_order",
+           "pcf_pairwise", "pcf_cross",
            "pcf_cross_to_host",
            "pcf_pairwise_backward", "pcf_check", "PairwiseFn", "PairwiseGraph", "pdist",
            "l2_kernel",
@@ -174,6 +175,20 @@ def _requests(metrics, outs):
     return arr
 
 
+def pcf_sort_order(x: PcfTensors, workspace: torch.Tensor, precision="f32c", stream=None):
+    """perm (int32 device tensor): input index of the s-th PCF in the sort
+    order of the collection prepared in ``workspace``."""
+    lib = abi.load()
+    perm = torch.empty(x.n, dtype=torch.int32, device=x.times.device)
+    cx = x.csr()
+    rc = lib.pcf_sort_order(ctypes.byref(cx), _prec(precision), ctypes.c_void_p(workspace.data_ptr()),
+                            workspace.numel(), ctypes.c_void_p(perm.data_ptr()),
+                            _stream_handle(stream))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_sort_order")
+    return perm
+
+
 def pcf_prepare(x: PcfTensors, precision="f32c", workspace=None, stream=None):
     """Validate, sort and pack ``x`` into a workspace (returned) for later
     ``pcf_pairwise(..., prepared=True, workspace=ws)`` calls."""
@@ -192,14 +207,16 @@ def pcf_pairwise(x: PcfTensors, metrics=("l1",), precision="f32c", layout="full"
                  check=True, prepared=False, schedule=None, shard=None):
     """Pairwise matrices F(C) (Sec. 3.1) of ``x`` for each requested metric.
 
-    Returns a list of tensors: N x N (layout "full") or N(N+1)/2 ("upper")."""
+    Returns a list of tensors: N x N (layout "full"), N(N+1)/2 ("upper"), or
+    N x N in the library's sort order ("sorted"; see ``pcf_sort_order``)."""
     lib = abi.load()
     if isinstance(metrics, (str, tuple)):
         metrics = [metrics]
     metrics = list(metrics)
     n = x.n
-    lay = abi.PCF_OUT_FULL if layout == "full" else abi.PCF_OUT_UPPER_PACKED
-    shape = (n, n) if lay == abi.PCF_OUT_FULL else (n * (n + 1) // 2,)
+    lay = {"full": abi.PCF_OUT_FULL, "upper": abi.PCF_OUT_UPPER_PACKED,
+           "sorted": abi.PCF_OUT_FULL_SORTED}[layout]
+    shape = (n * (n + 1) // 2,) if lay == abi.PCF_OUT_UPPER_PACKED else (n, n)
     dev = x.times.device
     if out is None:
         out = [torch.empty(shape, dtype=out_dtype, device=dev) for _ in metrics]
@@ -367,7 +384,7 @@ class PairwiseGraph:
         self.x = x
         self.metrics = list(metrics) if not isinstance(metrics, (str, tuple)) else [metrics]
         n = x.n
-        shape = (n, n) if layout == "full" else (n * (n + 1) // 2,)
+        shape = (n * (n + 1) // 2,) if layout == "upper" else (n, n)
         self.outs = [torch.empty(shape, dtype=out_dtype, device=x.times.device)
                      for _ in self.metrics]
         self.ws = torch.empty(max(pcf_workspace_size(x, None, precision), 256),

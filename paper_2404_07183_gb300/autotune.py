@@ -86,7 +86,7 @@ def tune_pairwise(x: api.PcfTensors, metrics, precision="f32c", layout="full",
     sms = torch.cuda.get_device_properties(x.times.device).multi_processor_count
     if nb * (nb + 1) // 2 >= 2 * sms:
         candidates = tuple(c for c in candidates if c[0] != "mergepath") or candidates
-    shape = (n, n) if layout == "full" else (n * (n + 1) // 2,)
+    shape = (n * (n + 1) // 2,) if layout == "upper" else (n, n)
     outs = [torch.empty(shape, dtype=out_dtype, device=x.times.device) for _ in metrics]
     stream = torch.cuda.current_stream()
     timings = {}

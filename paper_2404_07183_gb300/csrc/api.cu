@@ -296,7 +296,8 @@ int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precisi
 {
     if (!csr_ok(x)) return PCF_EINVAL;
     if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32_BLOCK) return PCF_EINVAL;
-    if (layout != PCF_OUT_FULL && layout != PCF_OUT_UPPER_PACKED) return PCF_EINVAL;
+    if (layout != PCF_OUT_FULL && layout != PCF_OUT_UPPER_PACKED && layout != PCF_OUT_FULL_SORTED)
+        return PCF_EINVAL;
     if (out_dtype != PCF_F32 && out_dtype != PCF_F64) return PCF_EINVAL;
     if (flags & ~PCF_PAIRWISE_PREPARED) return PCF_EINVAL;
     if (check_schedule(schedule) != PCF_OK) return PCF_EINVAL;
@@ -444,6 +445,23 @@ int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root
     if (launch_backward(ba, stream) != cudaSuccess) return PCF_ECUDA;
     if (launch_scatter_grad(sv, x->offsets, gv, gt, grad_values, grad_times,
                             x->dtype == PCF_F64, hdr, stream) != cudaSuccess)
+        return PCF_ECUDA;
+    return PCF_OK;
+}
+
+int pcf_sort_order(const pcf_csr* x, int precision, const void* workspace,
+                   size_t workspace_bytes, int32_t* perm_out, cudaStream_t stream)
+{
+    if (!csr_ok(x)) return PCF_EINVAL;
+    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32_BLOCK) return PCF_EINVAL;
+    if (x->n > 0 && !perm_out) return PCF_EINVAL;
+    Header* hdr;
+    SetView sv;
+    int rc = pairwise_common(x, precision, const_cast<void*>(workspace), workspace_bytes, &hdr, &sv);
+    if (rc != PCF_OK) return rc;
+    if (x->n == 0) return PCF_OK;
+    if (cudaMemcpyAsync(perm_out, sv.perm, sizeof(int32_t) * (size_t)x->n, cudaMemcpyDeviceToDevice,
+                        stream) != cudaSuccess)
         return PCF_ECUDA;
     return PCF_OK;
 }

@@ -341,3 +341,28 @@ def test_cross_streamed_to_host(pcf, prec):
         else:
             err = max_rel_error(m, h.numpy(), want)
         assert err <= TOL[prec], (m, err)
+
+
+@pytest.mark.parametrize("sched", ["tile1024", "tile512x2", "mergepath"])
+def test_sorted_output_layout(pcf, sched):
+    """Layout "sorted": entry (s, t) is F of the s-th and t-th PCFs of the
+    library's sort order, bit-identical to the full layout permuted."""
+    import torch
+    rng = np.random.default_rng(64)
+    lens = np.concatenate([rng.integers(1, 80, 90), rng.integers(257, 400, 10)])
+    s = synth.from_lengths(lens, lambda r, m: r.exponential(1.0, m),
+                           lambda r, o: np.where(np.isin(np.arange(o[-1]), o[1:] - 1), 0.0,
+                                                 r.standard_normal(o[-1])),
+                           rng, np.float64, "mixed")
+    x = _dev(pcf, s)
+    ws = pcf.pcf_prepare(x, "f64")
+    srt = pcf.pcf_pairwise(x, ["l1", "gram"], precision="f64", layout="sorted", workspace=ws,
+                           prepared=True, out_dtype=torch.float64, schedule=sched)
+    perm = pcf.pcf_sort_order(x, ws, "f64").cpu().numpy().astype(np.int64)
+    assert sorted(perm.tolist()) == list(range(s.n))
+    from paper_2404_07183_gb300 import shard
+    np.testing.assert_array_equal(perm, shard.sorted_order(s.lengths(), s.times[s.offsets[1:] - 1]))
+    full = pcf.pcf_pairwise(x, ["l1", "gram"], precision="f64", out_dtype=torch.float64,
+                            schedule=sched)
+    for a_, b_ in zip(srt, full):
+        np.testing.assert_array_equal(a_.cpu().numpy(), b_.cpu().numpy()[np.ix_(perm, perm)])
