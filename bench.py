@@ -46,8 +46,9 @@ FP64_OPS_PER_STEP = 1 + 1 + 1 + 2 + 2   # dt, d, L1 fma, L2 mul+fma, Gram mul+fm
 # DRAM bytes (read + write) per launch of the benchmark's compensated walk,
 # from one ncu capture (profiles/walk_f32c_dram_traffic_stable_rank_n20000.md),
 # valid only while the walk's source is the one that was measured.
-TRAFFIC_RECORD = {"source_sha256_16": "c1f75f782d911231+5d31ddd65b7eaf43",
-                  "schedule": "tile512x2", "bytes": 32118315776 + 26655318528}
+TRAFFIC_RECORD = {"source_sha256_16": "86af3e5fcb7598b3+7bc7a0f5c229a4b9",
+                  "by_schedule_layout": {("tile512x3", "full"): 33909303296 + 31404596224,
+                                         ("tile512x3", "sorted"): 287138048 + 5261150976}}
 
 
 def walk_source_id():
@@ -383,9 +384,9 @@ def run_ours(args):
                  "merge_steps_per_s": walk_rate},
         "roofline": {"bound": "alu", "achieved": walk_rate, "peak": issue_peak,
                      "unit": "merge-steps/s", "frac": walk_rate / issue_peak,
-                     "traffic": (TRAFFIC_RECORD["bytes"]
+                     "traffic": (TRAFFIC_RECORD["by_schedule_layout"].get(
+                                     (head["schedule"], args.layout))
                                  if (walk_source_id() == TRAFFIC_RECORD["source_sha256_16"]
-                                     and head["schedule"] == TRAFFIC_RECORD["schedule"]
                                      and N == 20000) else None),
                      "traffic_unit": "DRAM bytes per walk launch (ncu)",
                      "peak_basis": f"{sms} SMs x 128 lanes x {fmax/1e6:.0f} MHz / {TALLY[prec]} "
@@ -399,6 +400,10 @@ def run_ours(args):
     }
     if sorted_walk is not None:
         line["sorted_output"] = {"walk_ms": sorted_walk,
+                                 "traffic": (TRAFFIC_RECORD["by_schedule_layout"].get(
+                                     (head["schedule"], "sorted"))
+                                     if walk_source_id() == TRAFFIC_RECORD["source_sha256_16"]
+                                     and N == 20000 else None),
                                  "merge_steps_per_s": walk_steps / (sorted_walk * 1e-3),
                                  "note": "layout PCF_OUT_FULL_SORTED: same walk, matrices in "
                                          "the library's sort order (perm from pcf_sort_order)"}

@@ -163,6 +163,12 @@ typedef struct pcf_integral {
     void* out;           /* device output, layout and dtype per call */
 } pcf_integral;
 
+/* Single-PCF functionals (segment iteration, Sec. 3.2). */
+enum pcf_functional {
+    PCF_FN_INTEGRAL = 0,   /* h(v) = v:     int_a^b f dt                         */
+    PCF_FN_LP = 1          /* h(v) = |v|^p: int_a^b |f|^p dt, root -> the L_p norm */
+};
+
 /* Maximum number of pcf_integral entries per call. */
 #define PCF_MAX_INTEGRALS 4
 
@@ -247,6 +253,20 @@ int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root
                           const void* fwd_out, const void* grad_out, int grad_dtype,
                           void* grad_values, void* grad_times,
                           void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/*
+ * Single-PCF integrals by segment iteration (Sec. 3.2, Alg. 3):
+ *   out[i] = r( int_a^b h(f_i(t)) dt ),  0 <= a < b <= inf,
+ * h per pcf_functional; r(x) = x^(1/p) for PCF_FN_LP with apply_root, else x.
+ * A PCF whose last value makes h != 0 integrates to +-inf when b = inf.
+ * out: x->n elements of out_dtype.  The input is validated as for
+ * pcf_pairwise (pcf_check reports invalid data).  Workspace:
+ * pcf_workspace_size(x, NULL, PCF_PREC_F64, PCF_WS_FORWARD).  Accumulation is
+ * float64 in every case.
+ */
+int pcf_segment_integrals(const pcf_csr* x, int functional, double p, int apply_root,
+                          double a, double b, void* out, int out_dtype, void* workspace,
+                          size_t workspace_bytes, cudaStream_t stream);
 
 /*
  * The sort order used by the last pcf_prepare / pcf_pairwise on `workspace`

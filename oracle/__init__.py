@@ -39,7 +39,7 @@ _lock = threading.Lock()
 
 METRICS = {"l1": 0, "l2": 1, "lp": 2, "gram": 3}
 
-__all__ = ["build", "integral", "rectangles", "matrix", "backward",
+__all__ = ["build", "integral", "rectangles", "matrix", "backward", "segment_integral",
            "merge_steps", "total_merge_steps", "segment_sq", "METRICS"]
 
 
@@ -73,6 +73,8 @@ def _load():
                                        ip, dbl, ip, P, ip]
             lib.orc_segment_sq.restype = dbl
             lib.orc_segment_sq.argtypes = [P, P, i64]
+            lib.orc_segment_integral.restype = dbl
+            lib.orc_segment_integral.argtypes = [P, P, i64, ip, dbl, dbl, dbl]
             lib.orc_backward.restype = None
             lib.orc_backward.argtypes = [i64, P, P, P, ip, dbl, ip, P, P, P]
             _lib = lib
@@ -168,6 +170,14 @@ def segment_sq(t, v) -> float:
     """int_0^inf f^2 dt by segment iteration (Alg. 3)."""
     t, v = _f64(t), _f64(v)
     return _load().orc_segment_sq(_ptr(t), _ptr(v), t.size)
+
+
+def segment_integral(t, v, kind="lp", p=1.0, a=0.0, b=float("inf")) -> float:
+    """int_a^b h(f) dt by segment iteration (Alg. 3); kind "integral" uses
+    h(v) = v, kind "lp" uses |v|^p (no root)."""
+    t, v = _f64(t), _f64(v)
+    return _load().orc_segment_integral(_ptr(t), _ptr(v), t.size, 0 if kind == "integral" else 1,
+                                        float(p), float(a), float(b))
 
 
 def backward(a, G, metric="l2", p=2.0, apply_root=False):

@@ -14,6 +14,7 @@
  *                                                             (Sec. 3.1; Sec. 2.2
  *                                                              for r and h)
  *   orc_segment_sq      integral of f^2 by segment iteration  (Sec. 3.2, Alg. 3)
+ *   orc_segment_integral integral of f or |f|^p over [a, b]    (Sec. 3.2, Alg. 3)
  *   orc_backward        gradient of sum_ij G_ij F_ij with respect to the
  *                       breakpoint values and times (not in the paper; derived
  *                       from Eq. simpleint by differentiating each rectangle)
@@ -293,6 +294,33 @@ void orc_matrix(int64_t na, const int64_t* oa, const double* ta, const double* v
     (void)J;
     /* row_begin > 0 reuses the same loop: indices of oa are shifted above, and
      * for the pairwise case the columns still run over all of A. */
+}
+
+/*
+ * Alg. 3 (segment iteration) over [a, b]: start at the segment containing a,
+ * emit segments [l, r) clipped to [a, b], each contributing h(v) (r - l), stop
+ * at b.  kind 0: h(v) = v (the integral of f); kind 1: h(v) = |v|^p.  A last
+ * segment reaching b = inf adds 0 when h = 0 and h * inf otherwise.
+ */
+double orc_segment_integral(const double* t, const double* v, int64_t n, int kind, double p,
+                            double a, double b)
+{
+    int64_t k = 0;
+    while (k + 1 < n && t[k + 1] <= a) k++;          /* k = max{i : t_i <= a} */
+    double l = a, I = 0.0;
+    for (;;) {
+        double h = (kind == 0) ? v[k] : orc_pow_abs(v[k], p);
+        double r = (k + 1 < n) ? t[k + 1] : INFINITY;
+        if (r >= b) r = b;
+        if (isinf(r)) {
+            if (h != 0.0) I += h * INFINITY;
+            return I;
+        }
+        I += h * (r - l);
+        if (r >= b) return I;
+        l = r;
+        k++;
+    }
 }
 
 /* Alg. 3 (segment iteration) for the integral of f^2 over [0, inf). */

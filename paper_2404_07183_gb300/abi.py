@@ -33,7 +33,8 @@ ERR_DETAIL = {
 
 SYMBOLS = ("pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross", "pcf_pairwise_backward",
            "pcf_check", "pcf_status_string", "pcf_version", "pcf_pairwise_noalloc",
-           "pcf_pairwise_ex", "pcf_cross_ex", "pcf_sort_order")
+           "pcf_pairwise_ex", "pcf_cross_ex", "pcf_sort_order", "pcf_segment_integrals")
+PCF_FN_INTEGRAL, PCF_FN_LP = 0, 1
 PCF_SCHED_AUTO, PCF_SCHED_TILE_1024, PCF_SCHED_TILE_512X2, PCF_SCHED_MERGEPATH = 0, 1, 2, 3
 PCF_SCHED_TILE_512X3 = 4
 PCF_NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -92,6 +93,8 @@ def load(build_if_missing: bool = False):
         lib.pcf_pairwise_ex.argtypes = [CSR, INT, I, I, I, I, I, SCH, P, SZ, P]
         lib.pcf_cross_ex.restype = I
         lib.pcf_cross_ex.argtypes = [CSR, CSR, I64, I64, INT, I, I, I64, I, I, SCH, P, SZ, P]
+        lib.pcf_segment_integrals.restype = I
+        lib.pcf_segment_integrals.argtypes = [CSR, I, D, I, D, D, P, I, P, SZ, P]
         lib.pcf_sort_order.restype = I
         lib.pcf_sort_order.argtypes = [CSR, I, P, SZ, P, P]
         lib.pcf_prepare.restype = I

@@ -22,6 +22,7 @@ import torch
 from . import abi
 
 __all__ = ["PcfError", "PcfTensors", "pcf_workspace_size", "pcf_prepare", "pcf_sort_order",
+           "pcf_segment_integrals",
            "pcf_pairwise", "pcf_cross",
            "pcf_cross_to_host",
            "pcf_pairwise_backward", "pcf_check", "PairwiseFn", "PairwiseGraph", "pdist",
@@ -173,6 +174,31 @@ def _requests(metrics, outs):
         arr[k].metric, arr[k].p, arr[k].apply_root = code, p, int(root)
         arr[k].out = o.data_ptr() if o is not None and o.numel() else None
     return arr
+
+
+def pcf_segment_integrals(x: PcfTensors, functional="lp", p=1.0, apply_root=False, a=0.0,
+                          b=float("inf"), out_dtype=torch.float64, out=None, workspace=None,
+                          stream=None, check=True):
+    """Per-PCF integrals over [a, b] by segment iteration (Sec. 3.2, Alg. 3):
+    ``"integral"`` gives int f dt, ``"lp"`` gives int |f|^p dt (the L_p norm
+    with ``apply_root``).  Returns a length-N tensor."""
+    lib = abi.load()
+    fn = abi.PCF_FN_INTEGRAL if functional == "integral" else abi.PCF_FN_LP
+    dev = x.times.device
+    if out is None:
+        out = torch.empty(x.n, dtype=out_dtype, device=dev)
+    ws = _workspace(pcf_workspace_size(x, None, "f64"), dev, workspace)
+    cx = x.csr()
+    rc = lib.pcf_segment_integrals(ctypes.byref(cx), fn, float(p), int(bool(apply_root)),
+                                   float(a), float(b), ctypes.c_void_p(out.data_ptr()),
+                                   abi.PCF_F64 if out.dtype == torch.float64 else abi.PCF_F32,
+                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                   _stream_handle(stream))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_segment_integrals")
+    if check:
+        pcf_check(ws, stream, "pcf_segment_integrals")
+    return out
 
 
 def pcf_sort_order(x: PcfTensors, workspace: torch.Tensor, precision="f32c", stream=None):

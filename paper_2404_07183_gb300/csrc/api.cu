@@ -449,6 +449,31 @@ int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root
     return PCF_OK;
 }
 
+int pcf_segment_integrals(const pcf_csr* x, int functional, double p, int apply_root,
+                          double a, double b, void* out, int out_dtype, void* workspace,
+                          size_t workspace_bytes, cudaStream_t stream)
+{
+    if (!csr_ok(x)) return PCF_EINVAL;
+    if (functional != PCF_FN_INTEGRAL && functional != PCF_FN_LP) return PCF_EINVAL;
+    if (functional == PCF_FN_LP && !(p >= 1.0 && std::isfinite(p))) return PCF_EINVAL;
+    if (!(a >= 0.0) || !(b > a) || std::isnan(b) || std::isinf(a)) return PCF_EINVAL;
+    if (out_dtype != PCF_F32 && out_dtype != PCF_F64) return PCF_EINVAL;
+    if (x->n > 0 && !out) return PCF_EINVAL;
+    Header* hdr;
+    SetView sv;
+    int rc = pairwise_common(x, PCF_PREC_F64, workspace, workspace_bytes, &hdr, &sv);
+    if (rc != PCF_OK) return rc;
+    init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
+    if (x->n == 0) return cudaGetLastError() == cudaSuccess ? PCF_OK : PCF_ECUDA;
+    if (launch_validate(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz, 1, hdr, sv,
+                        stream) != cudaSuccess)
+        return PCF_ECUDA;
+    if (launch_segments(x, functional, p, apply_root, a, b, out, out_dtype == PCF_F64, hdr,
+                        stream) != cudaSuccess)
+        return PCF_ECUDA;
+    return PCF_OK;
+}
+
 int pcf_sort_order(const pcf_csr* x, int precision, const void* workspace,
                    size_t workspace_bytes, int32_t* perm_out, cudaStream_t stream)
 {

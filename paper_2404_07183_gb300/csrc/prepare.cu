@@ -295,6 +295,22 @@ static int grid_for_warps(int64_t warps)
     return (int)blocks;
 }
 
+cudaError_t launch_validate(const int64_t* offsets, const void* times, const void* values,
+                            int in_dtype, int64_t n, int64_t nnz_total, int walk_f64,
+                            Header* hdr, SetView& sv, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const int g = grid_for_warps(n);
+    if (in_dtype == PCF_F64) {
+        validate_kernel<double><<<g, 256, 0, s>>>(offsets, (const double*)times,
+            (const double*)values, n, nnz_total, 1, !walk_f64, sv.lens, sv.skey, hdr, sv.slot);
+    } else {
+        validate_kernel<float><<<g, 256, 0, s>>>(offsets, (const float*)times,
+            (const float*)values, n, nnz_total, 1, !walk_f64, sv.lens, sv.skey, hdr, sv.slot);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t prepare_set(const int64_t* offsets, const void* times, const void* values,
                         int in_dtype, int64_t n, int64_t nnz_total, bool whole,
                         int walk_f64, Header* hdr, SetView& sv, cudaStream_t s)

@@ -1,0 +1,77 @@
+"""Segment iteration on the GPU (single-PCF integrals over [a, b]) against
+the oracle (needs a GPU)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_07183_gb300 import synth
+
+from conftest import gpu_available
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pcf():
+    if not gpu_available():
+        pytest.skip("no CUDA device")
+    import paper_2404_07183_gb300 as P
+    P.build.build()
+    return P
+
+
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+@pytest.mark.parametrize("kind,p,root", [("integral", 1.0, False), ("lp", 1.0, False),
+                                         ("lp", 2.0, True), ("lp", 3.0, False),
+                                         ("lp", 3.5, True)])
+@pytest.mark.parametrize("ab", [(0.0, np.inf), (0.5, 7.25), (3.0, 1e9)])
+def test_segments_vs_oracle(pcf, dtype, kind, p, root, ab):
+    import torch
+    s = synth.random_set(300, seed=101, min_len=1, max_len=90).astype(dtype)
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    got = pcf.pcf_segment_integrals(x, kind, p, root, ab[0], ab[1]).cpu().numpy()
+    for i in range(s.n):
+        t, v = s.pcf(i)
+        want = oracle.segment_integral(t, v, kind, p, ab[0], ab[1])
+        if root and kind == "lp" and np.isfinite(want):
+            want = want ** (1.0 / p)
+        if np.isinf(want):
+            assert got[i] == want
+        else:
+            assert abs(got[i] - want) <= 1e-12 * max(1.0, abs(want)), (i, got[i], want)
+
+
+def test_segments_dyadic_exact_and_edges(pcf):
+    s = synth.dyadic(200, seed=102, max_len=50, min_len=1, final_zero=False)
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    for kind, p in (("integral", 1.0), ("lp", 2.0)):
+        got = pcf.pcf_segment_integrals(x, kind, p, False, 2.0, 40.0).cpu().numpy()
+        want = np.array([oracle.segment_integral(*s.pcf(i), kind, p, 2.0, 40.0)
+                         for i in range(s.n)])
+        np.testing.assert_array_equal(got, want)
+        tail = pcf.pcf_segment_integrals(x, kind, p).cpu().numpy()
+        want = np.array([oracle.segment_integral(*s.pcf(i), kind, p) for i in range(s.n)])
+        np.testing.assert_array_equal(tail, want)     # +-inf where the last value != 0
+
+
+def test_segments_norm_matches_gram_diagonal(pcf):
+    import torch
+    s = synth.stable_rank(500, seed=103)
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    sq = pcf.pcf_segment_integrals(x, "lp", 2.0).cpu().numpy()
+    gram = pcf.pcf_pairwise(x, ["gram"], precision="f64", out_dtype=torch.float64)[0]
+    np.testing.assert_allclose(np.diag(gram.cpu().numpy()), sq, rtol=1e-13)
+
+
+def test_segments_reject_bad_arguments(pcf):
+    s = synth.random_set(5, seed=104)
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    with pytest.raises(pcf.PcfError):
+        pcf.pcf_segment_integrals(x, "lp", 0.5)
+    with pytest.raises(pcf.PcfError):
+        pcf.pcf_segment_integrals(x, "lp", 2.0, a=3.0, b=1.0)
+    t = s.times.copy()
+    t[3] = t[2]
+    bad = pcf.PcfTensors.from_numpy(synth.PcfSet(s.offsets, t, s.values), "cuda")
+    with pytest.raises(pcf.PcfError):
+        pcf.pcf_segment_integrals(bad, "integral")

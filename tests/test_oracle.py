@@ -330,3 +330,38 @@ def test_gradient_dyadic_exact_one_sided(metric):
             left[i] = (t[:k] + [Fraction(t[k]) - h] + t[k + 1:], v)
             lq = (base - _exact_loss(left, G, metric)) / h
             assert float(lq) == gt[s.offsets[i] + k], ("time", i, k)
+
+
+# --------------------------------------------------------------------------
+# Segment iteration (Alg. 3): single-PCF integrals over [a, b]
+# --------------------------------------------------------------------------
+def test_segment_integral_closed_forms():
+    t, v = _indicator(2.5, 1.0, 4.0)          # 2.5 on [1, 4)
+    assert oracle.segment_integral(t, v, "integral") == 7.5
+    assert oracle.segment_integral(t, v, "integral", a=2.0, b=3.5) == 2.5 * 1.5
+    assert oracle.segment_integral(t, v, "integral", a=0.0, b=0.5) == 0.0
+    assert oracle.segment_integral(t, v, "lp", p=3.0, a=0.5, b=10.0) == 2.5 ** 3 * 3.0
+    assert oracle.segment_integral([0.0, 1.0], [1.0, 2.0], "integral") == np.inf
+    assert oracle.segment_integral([0.0, 1.0], [1.0, 2.0], "integral", b=3.0) == 1.0 + 4.0
+
+
+@pytest.mark.parametrize("kind,p", [("integral", 1.0), ("lp", 1.0), ("lp", 2.0), ("lp", 3.5)])
+def test_segment_integral_against_union_grid(kind, p):
+    """The single-PCF integral equals the pair integral against the zero PCF
+    (for |f|^p) and the brute-force sum over the clipped breakpoints."""
+    s = synth.random_set(40, seed=25, min_len=1, max_len=30)
+    rng = np.random.default_rng(2)
+    for i in range(s.n):
+        t, v = s.pcf(i)
+        a = float(rng.uniform(0, t[-1] + 1))
+        b = a + float(rng.exponential(5.0))
+        grid = np.unique(np.concatenate([t[(t > a) & (t < b)], [a, b]]))
+        vals = brute.evaluate(t, v, grid[:-1])
+        h = vals if kind == "integral" else np.abs(vals) ** p
+        want = float(np.sum(h * np.diff(grid)))
+        got = oracle.segment_integral(t, v, kind, p, a, b)
+        assert got == pytest.approx(want, rel=1e-12, abs=1e-12)
+        if kind == "lp":
+            full = oracle.segment_integral(t, v, kind, p)
+            pair = oracle.integral(t, v, [0.0], [0.0], "lp", p)
+            assert full == pytest.approx(pair, rel=1e-13)
