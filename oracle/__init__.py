@@ -39,7 +39,7 @@ _lock = threading.Lock()
 
 METRICS = {"l1": 0, "l2": 1, "lp": 2, "gram": 3}
 
-__all__ = ["build", "integral", "rectangles", "matrix", "backward", "segment_integral",
+__all__ = ["build", "integral", "integral_ab", "rectangles", "matrix", "backward", "segment_integral",
            "merge_steps", "total_merge_steps", "segment_sq", "METRICS"]
 
 
@@ -73,6 +73,8 @@ def _load():
                                        ip, dbl, ip, P, ip]
             lib.orc_segment_sq.restype = dbl
             lib.orc_segment_sq.argtypes = [P, P, i64]
+            lib.orc_integral_ab.restype = dbl
+            lib.orc_integral_ab.argtypes = [P, P, i64, P, P, i64, ip, dbl, dbl, dbl, dbl]
             lib.orc_segment_integral.restype = dbl
             lib.orc_segment_integral.argtypes = [P, P, i64, ip, dbl, dbl, dbl]
             lib.orc_backward.restype = None
@@ -98,6 +100,13 @@ def integral(tf, vf, tg, vg, metric="l1", p=1.0) -> float:
     tf, vf, tg, vg = map(_f64, (tf, vf, tg, vg))
     return _load().orc_integral(_ptr(tf), _ptr(vf), tf.size, _ptr(tg), _ptr(vg),
                                 tg.size, _metric(metric), float(p))
+
+
+def integral_ab(tf, vf, tg, vg, metric="l1", p=1.0, a=0.0, b=float("inf"), lam=0.0) -> float:
+    """int_a^b h(f, g) exp(-lam t) dt (no root)."""
+    tf, vf, tg, vg = map(_f64, (tf, vf, tg, vg))
+    return _load().orc_integral_ab(_ptr(tf), _ptr(vf), tf.size, _ptr(tg), _ptr(vg), tg.size,
+                                   _metric(metric), float(p), float(a), float(b), float(lam))
 
 
 def rectangles(tf, vf, tg, vg):

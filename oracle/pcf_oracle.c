@@ -13,6 +13,11 @@
  *   orc_matrix          pairwise / cross matrices F_ij = r(I_ij)
  *                                                             (Sec. 3.1; Sec. 2.2
  *                                                              for r and h)
+ *   orc_integral_ab     Alg. 1/2 over [a, b], optionally with the exponential
+ *                       weight w(t) = exp(-lambda t) through its antiderivative
+ *                                                             (Sec. 3, Alg. 1
+ *                                                              bounds; Sec. 2.1
+ *                                                              time-dependent h)
  *   orc_segment_sq      integral of f^2 by segment iteration  (Sec. 3.2, Alg. 3)
  *   orc_segment_integral integral of f or |f|^p over [a, b]    (Sec. 3.2, Alg. 3)
  *   orc_backward        gradient of sum_ij G_ij F_ij with respect to the
@@ -199,6 +204,57 @@ double orc_integral(const double* tf, const double* vf, int64_t nf,
     orc_acc A = { metric, p, 0.0 };
     orc_walk(tf, vf, nf, tg, vg, ng, orc_emit_acc, &A);
     return A.I;
+}
+
+/*
+ * Alg. 1 with integration bounds 0 <= a < b <= inf: the cursors start at the
+ * last breakpoints <= a, the scanline starts at a, and every rectangle's right
+ * end is clipped to b; the walk stops once the scanline reaches b.
+ * Accumulation of Alg. 2, or -- for the time-dependent combination
+ * h(x, y, t) = h(x, y) w(t) with w(t) = exp(-lambda t) -- the antiderivative
+ * form of Sec. 3: each rectangle adds H(v_f, v_g, r) - H(v_f, v_g, l) with
+ * H(x, y, t) = h(x, y) W(t), W(t) = -exp(-lambda t) / lambda.  The difference
+ * W(r) - W(l) is evaluated as exp(-lambda l) * (-expm1(-lambda (r - l))) /
+ * lambda, the same quantity without the cancellation of two close
+ * exponentials; lambda = 0 is the unweighted case.
+ */
+double orc_integral_ab(const double* tf, const double* vf, int64_t nf,
+                       const double* tg, const double* vg, int64_t ng,
+                       int metric, double p, double a, double b, double lambda)
+{
+    int64_t k = 0, kg = 0;
+    while (k + 1 < nf && tf[k + 1] <= a) k++;
+    while (kg + 1 < ng && tg[kg + 1] <= a) kg++;
+    double t = a, I = 0.0;
+    while (t < b) {
+        double t_prev = t;
+        double h = orc_h(metric, p, vf[k], vg[kg]);
+        int64_t k_old = k;
+        if (k + 1 < nf && kg + 1 < ng) {
+            if (tf[k + 1] <= tg[kg + 1]) k += 1;
+            if (tg[kg + 1] <= tf[k_old + 1]) kg += 1;
+        } else if (k + 1 < nf) {
+            k += 1;
+        } else if (kg + 1 < ng) {
+            kg += 1;
+        } else {
+            t = b;                            /* last rectangle reaches b */
+            if (isinf(b) && lambda == 0.0) {  /* unweighted tail [t, inf) */
+                if (h != 0.0) I += h * INFINITY;
+                return I;
+            }
+            /* weighted: exp(-lambda t_prev) / lambda for b = inf, finite */
+        }
+        if (t < b) {
+            double nt = (tf[k] > tg[kg]) ? tf[k] : tg[kg];
+            t = nt < b ? nt : b;
+        }
+        double dw;
+        if (lambda == 0.0) dw = t - t_prev;
+        else dw = exp(-lambda * t_prev) * (-expm1(-lambda * (t - t_prev))) / lambda;
+        I += h * dw;
+    }
+    return I;
 }
 
 /* Number of rectangles of the pair = |T_f u T_g| (the merge-step count). */

@@ -365,3 +365,100 @@ def test_segment_integral_against_union_grid(kind, p):
             full = oracle.segment_integral(t, v, kind, p)
             pair = oracle.integral(t, v, [0.0], [0.0], "lp", p)
             assert full == pytest.approx(pair, rel=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Integration bounds and time-dependent (weighted) integrands
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", range(12))
+def test_bounded_weighted_indicator_closed_form(seed):
+    rng = np.random.default_rng(100 + seed)
+    lo, hi = np.sort(rng.uniform(0, 10, 2))
+    lo2, hi2 = np.sort(rng.uniform(0, 10, 2))
+    a, b = np.sort(rng.uniform(0, 12, 2))
+    lam = [0.0, 0.3, 2.0][seed % 3]
+    c, d = rng.normal(size=2) * 2
+    tf, vf = _indicator(c, lo, hi)
+    tg, vg = _indicator(d, lo2, hi2)
+
+    def wint(x, y):             # int_x^y exp(-lam t) dt
+        if y <= x:
+            return 0.0
+        return (y - x) if lam == 0 else (np.exp(-lam * x) - np.exp(-lam * y)) / lam
+
+    ov = wint(max(lo, lo2, a), min(hi, hi2, b))
+    got = oracle.integral_ab(tf, vf, tg, vg, "gram", 1.0, a, b, lam)
+    assert got == pytest.approx(c * d * ov, rel=1e-12, abs=1e-12)
+    # |f - g|: pieces where only f, only g, or both are on
+    f_only = wint(max(lo, a), min(hi, b)) - ov
+    g_only = wint(max(lo2, a), min(hi2, b)) - ov
+    want = abs(c) * f_only + abs(d) * g_only + abs(c - d) * ov
+    assert oracle.integral_ab(tf, vf, tg, vg, "l1", 1.0, a, b, lam) == pytest.approx(
+        want, rel=1e-12, abs=1e-12)
+
+
+@pytest.mark.parametrize("lam", [0.25, 1.0, 3.0])
+def test_weighted_unbounded_tail_closed_form(lam):
+    """f = c on [s, inf), g = d on [0, inf) (neither compact): with the weight
+    exp(-lam t) the integrals over [0, inf) are finite and have closed forms."""
+    s, c, d = 1.75, 2.5, -0.75
+    tf, vf = np.array([0.0, s]), np.array([0.0, c])
+    tg, vg = np.array([0.0]), np.array([d])
+    es = np.exp(-lam * s)
+    got = oracle.integral_ab(tf, vf, tg, vg, "gram", 1.0, 0.0, np.inf, lam)
+    assert got == pytest.approx(c * d * es / lam, rel=1e-14)
+    got = oracle.integral_ab(tf, vf, tg, vg, "l1", 1.0, 0.0, np.inf, lam)
+    assert got == pytest.approx(abs(d) * (1 - es) / lam + abs(c - d) * es / lam, rel=1e-14)
+    got = oracle.integral_ab(tf, vf, tg, vg, "l2", 2.0, 0.5, np.inf, lam)
+    want = d * d * (np.exp(-lam * 0.5) - es) / lam + (c - d) ** 2 * es / lam
+    assert got == pytest.approx(want, rel=1e-14)
+    # lam = 0 keeps the unweighted tail rule (reading 2): +inf, and 0 where h = 0
+    assert oracle.integral_ab(tf, vf, tg, vg, "l1", 1.0, 0.0, np.inf, 0.0) == np.inf
+    assert oracle.integral_ab(tf, vf, tf, vf, "l1", 1.0, 0.0, np.inf, 0.0) == 0.0
+
+
+def test_bounded_reduces_to_whole_line_and_splits_additively():
+    s = synth.random_set(20, seed=26, min_len=1, max_len=30)
+    rng = np.random.default_rng(3)
+    for i in range(s.n - 1):
+        f, g = s.pcf(i), s.pcf(i + 1)
+        for m, p in (("l1", 1), ("lp", 3.5), ("gram", 1)):
+            assert oracle.integral_ab(*f, *g, m, p) == oracle.integral(*f, *g, m, p)
+            c = float(rng.uniform(0.1, 8.0))
+            whole = oracle.integral_ab(*f, *g, m, p, 0.0, 20.0, 0.4)
+            parts = (oracle.integral_ab(*f, *g, m, p, 0.0, c, 0.4)
+                     + oracle.integral_ab(*f, *g, m, p, c, 20.0, 0.4))
+            assert parts == pytest.approx(whole, rel=1e-12, abs=1e-12)
+
+
+def test_weighted_against_quadrature():
+    """Independent pin: adaptive quadrature of h(f(t), g(t)) exp(-lam t) over
+    each cell of the common refinement."""
+    from scipy import integrate
+    s = synth.random_set(6, seed=27, min_len=2, max_len=12)
+    for i in range(s.n - 1):
+        (tf, vf), (tg, vg) = s.pcf(i), s.pcf(i + 1)
+        a, b, lam = 0.3, float(max(tf[-1], tg[-1]) + 1.0), 0.7
+        grid = np.unique(np.concatenate([tf, tg, [a, b]]))
+        grid = grid[(grid >= a) & (grid <= b)]
+        want = 0.0
+        for x, y in zip(grid[:-1], grid[1:]):
+            fv = brute.evaluate(tf, vf, np.array([x]))[0]
+            gv = brute.evaluate(tg, vg, np.array([x]))[0]
+            want += integrate.quad(lambda t: (fv - gv) ** 2 * np.exp(-lam * t), x, y,
+                                   epsabs=1e-14, epsrel=1e-13)[0]
+        got = oracle.integral_ab(tf, vf, tg, vg, "l2", 2.0, a, b, lam)
+        assert got == pytest.approx(want, rel=1e-10)
+        # b = inf: the last cell [t_last, inf) integrated to infinity
+        vf2, vg2 = vf.copy(), vg.copy()
+        vf2[-1], vg2[-1] = 1.5, -0.5
+        grid = np.unique(np.concatenate([tf, tg, [a]]))
+        grid = np.append(grid[grid >= a], np.inf)
+        want = 0.0
+        for x, y in zip(grid[:-1], grid[1:]):
+            fv = brute.evaluate(tf, vf2, np.array([x]))[0]
+            gv = brute.evaluate(tg, vg2, np.array([x]))[0]
+            want += integrate.quad(lambda t: abs(fv - gv) * np.exp(-lam * t), x, y,
+                                   epsabs=1e-14, epsrel=1e-13)[0]
+        got = oracle.integral_ab(tf, vf2, tg, vg2, "l1", 1.0, a, np.inf, lam)
+        assert got == pytest.approx(want, rel=1e-10)
