@@ -14,6 +14,9 @@ h(f(s_k), g(s_k)) (s_{k+1} - s_k)                       (Sec. 3, Eq. simpleint):
 * ``pcf_oracle.c`` (loaded through ctypes): float64 rectangle iteration
   (Alg. 1) with accumulation (Alg. 2), threaded over matrix rows, plus the
   adjoint (gradient of sum G * F with respect to values and times).
+  It also holds the reductions of Sec. 4: ReducePair (Alg. 4) and binary
+  reduction trees (Fig. 2) for sums, means, maxima, minima and the sample
+  standard deviation of Sec. 2.1.
 * ``brute.py``: the common refinement built explicitly (sort + unique), values
   looked up by binary search, summed with numpy; and an exact rational
   version for tiny inputs.
@@ -39,8 +42,12 @@ _lock = threading.Lock()
 
 METRICS = {"l1": 0, "l2": 1, "lp": 2, "gram": 3}
 
+OPS = {"add": 0, "sub": 1, "mul": 2, "max": 3, "min": 4, "sqdiff": 5}
+REDUCTIONS = {"sum": 0, "mean": 1, "max": 2, "min": 3, "std": 4}
+
 __all__ = ["build", "integral", "integral_ab", "rectangles", "matrix", "backward", "segment_integral",
-           "merge_steps", "total_merge_steps", "segment_sq", "METRICS"]
+           "merge_steps", "total_merge_steps", "segment_sq", "reduce_pair", "reduce", "METRICS",
+           "OPS", "REDUCTIONS"]
 
 
 def build(force: bool = False) -> str:
@@ -77,6 +84,10 @@ def _load():
             lib.orc_integral_ab.argtypes = [P, P, i64, P, P, i64, ip, dbl, dbl, dbl, dbl]
             lib.orc_segment_integral.restype = dbl
             lib.orc_segment_integral.argtypes = [P, P, i64, ip, dbl, dbl, dbl]
+            lib.orc_reduce_pair.restype = i64
+            lib.orc_reduce_pair.argtypes = [P, P, i64, P, P, i64, ip, P, P]
+            lib.orc_reduce.restype = i64
+            lib.orc_reduce.argtypes = [i64, i64, P, P, P, ip, P, P, P, i64, ip]
             lib.orc_backward.restype = None
             lib.orc_backward.argtypes = [i64, P, P, P, ip, dbl, ip, P, P, P]
             _lib = lib
@@ -200,3 +211,36 @@ def backward(a, G, metric="l2", p=2.0, apply_root=False):
     lib.orc_backward(a.n, _ptr(oa), _ptr(ta), _ptr(va), _metric(metric),
                      float(p), int(bool(apply_root)), _ptr(G), _ptr(gv), _ptr(gt))
     return gv, gt
+
+
+def reduce_pair(tf, vf, tg, vg, op="add"):
+    """ReducePair (Alg. 4): breakpoints and values of h_*(f, g)."""
+    tf, vf, tg, vg = map(_f64, (tf, vf, tg, vg))
+    out_t = np.empty(tf.size + tg.size)
+    out_v = np.empty(tf.size + tg.size)
+    n = _load().orc_reduce_pair(_ptr(tf), _ptr(vf), tf.size, _ptr(tg), _ptr(vg), tg.size,
+                                OPS[op], _ptr(out_t), _ptr(out_v))
+    return out_t[:n].copy(), out_v[:n].copy()
+
+
+def reduce(a, group_size, red="mean", nthreads=None):
+    """Reduce consecutive groups of ``group_size`` PCFs of ``a`` (a.n must be a
+    multiple) to one PCF each: (offsets, times, values) as numpy arrays."""
+    lib = _load()
+    m = int(group_size)
+    if m < 1 or a.n % m:
+        raise ValueError("group_size must divide the number of PCFs")
+    groups = a.n // m
+    ta, va = _f64(a.times), _f64(a.values)
+    oa = np.ascontiguousarray(a.offsets, dtype=np.int64)
+    if nthreads is None:
+        nthreads = len(os.sched_getaffinity(0))
+    cap = max(int(a.nnz), 1)
+    while True:
+        out_off = np.empty(groups + 1, dtype=np.int64)
+        out_t, out_v = np.empty(cap), np.empty(cap)
+        n = lib.orc_reduce(groups, m, _ptr(oa), _ptr(ta), _ptr(va), REDUCTIONS[red],
+                           _ptr(out_off), _ptr(out_t), _ptr(out_v), cap, int(nthreads))
+        if n >= 0:
+            return out_off, out_t[:n].copy(), out_v[:n].copy()
+        cap = int(out_off[-1])

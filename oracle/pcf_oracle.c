@@ -20,6 +20,11 @@
  *                                                              time-dependent h)
  *   orc_segment_sq      integral of f^2 by segment iteration  (Sec. 3.2, Alg. 3)
  *   orc_segment_integral integral of f or |f|^p over [a, b]    (Sec. 3.2, Alg. 3)
+ *   orc_reduce_pair     ReducePair: the PCF h_*(f, g) with repeated values
+ *                       dropped                               (Sec. 4, Alg. 4)
+ *   orc_reduce          sum / mean / max / min / sample std of groups of PCFs
+ *                       by binary reduction trees      (Sec. 4, Fig. 2; mean
+ *                                                       and std of Sec. 2.1)
  *   orc_backward        gradient of sum_ij G_ij F_ij with respect to the
  *                       breakpoint values and times (not in the paper; derived
  *                       from Eq. simpleint by differentiating each rectangle)
@@ -476,4 +481,237 @@ void orc_backward(int64_t n, const int64_t* off, const double* t, const double* 
             }
         }
     }
+}
+
+/* ===================================================================== */
+/* Reductions (Sec. 4): ReducePair (Alg. 4) and binary reduction trees.   */
+/* ===================================================================== */
+
+/* Combination functions h of the induced operations h_* (Sec. 2.1). */
+enum { ORC_OP_ADD = 0, ORC_OP_SUB = 1, ORC_OP_MUL = 2, ORC_OP_MAX = 3, ORC_OP_MIN = 4,
+       ORC_OP_SQDIFF = 5 };
+
+static double orc_op(int op, double a, double b)
+{
+    switch (op) {
+    case ORC_OP_ADD: return a + b;
+    case ORC_OP_SUB: return a - b;
+    case ORC_OP_MUL: return a * b;
+    case ORC_OP_MAX: return a >= b ? a : b;
+    case ORC_OP_MIN: return a <= b ? a : b;
+    default: { double d = a - b; return d * d; }   /* ORC_OP_SQDIFF */
+    }
+}
+
+/*
+ * Alg. 4 (ReducePair): walk the rectangles of f and g (Alg. 1); for each
+ * rectangle R compute v = h(R.v_f, R.v_g) and append the breakpoint (R.l, v)
+ * when R.l = 0 or v differs from the previous rectangle's v.  The output
+ * holds at most nf + ng rows; the row count is returned.
+ */
+typedef struct { int op; double* t; double* v; int64_t n; double v_last; } orc_rp;
+
+static void orc_emit_rp(void* ctx, double l, double r, double a, double b,
+                        int64_t kf, int64_t kg, int mf, int mg)
+{
+    (void)r; (void)kf; (void)kg; (void)mf; (void)mg;
+    orc_rp* R = (orc_rp*)ctx;
+    double v = orc_op(R->op, a, b);
+    if (l == 0.0 || v != R->v_last) {
+        R->t[R->n] = l;
+        R->v[R->n] = v;
+        R->n += 1;
+    }
+    R->v_last = v;
+}
+
+int64_t orc_reduce_pair(const double* tf, const double* vf, int64_t nf,
+                        const double* tg, const double* vg, int64_t ng, int op,
+                        double* out_t, double* out_v)
+{
+    orc_rp R = { op, out_t, out_v, 0, 0.0 };
+    orc_walk(tf, vf, nf, tg, vg, ng, orc_emit_rp, &R);
+    return R.n;
+}
+
+/* A PCF owned by the tree code. */
+typedef struct { double* t; double* v; int64_t n; } orc_pcf;
+
+static orc_pcf orc_pcf_copy(const double* t, const double* v, int64_t n)
+{
+    orc_pcf p;
+    p.t = (double*)malloc(sizeof(double) * (size_t)n);
+    p.v = (double*)malloc(sizeof(double) * (size_t)n);
+    memcpy(p.t, t, sizeof(double) * (size_t)n);
+    memcpy(p.v, v, sizeof(double) * (size_t)n);
+    p.n = n;
+    return p;
+}
+
+static void orc_pcf_free(orc_pcf* p)
+{
+    free(p->t);
+    free(p->v);
+    p->t = p->v = NULL;
+    p->n = 0;
+}
+
+static orc_pcf orc_pcf_pair(const orc_pcf* f, const orc_pcf* g, int op)
+{
+    orc_pcf p;
+    p.t = (double*)malloc(sizeof(double) * (size_t)(f->n + g->n));
+    p.v = (double*)malloc(sizeof(double) * (size_t)(f->n + g->n));
+    p.n = orc_reduce_pair(f->t, f->v, f->n, g->t, g->v, g->n, op, p.t, p.v);
+    return p;
+}
+
+/*
+ * Binary reduction tree (Fig. 2 with two inputs per node): level by level,
+ * item k of the next level is ReducePair(item 2k, item 2k + 1); an odd last
+ * item moves up unchanged (the No-Op node of Fig. 2).  Consumes `items`
+ * (m >= 1) and returns the root.
+ */
+static orc_pcf orc_tree(orc_pcf* items, int64_t m, int op)
+{
+    while (m > 1) {
+        int64_t half = m / 2;
+        for (int64_t k = 0; k < half; ++k) {
+            orc_pcf r = orc_pcf_pair(&items[2 * k], &items[2 * k + 1], op);
+            orc_pcf_free(&items[2 * k]);
+            orc_pcf_free(&items[2 * k + 1]);
+            items[k] = r;
+        }
+        if (m % 2) {
+            items[half] = items[m - 1];
+            m = half + 1;
+        } else {
+            m = half;
+        }
+    }
+    return items[0];
+}
+
+/* Values mapped by v -> v / s (kind 0) or sqrt(v / s) (kind 1); a breakpoint
+ * is kept when t = 0 or its mapped value differs from the previous one. */
+static orc_pcf orc_map(const orc_pcf* f, int kind, double s)
+{
+    orc_pcf p;
+    p.t = (double*)malloc(sizeof(double) * (size_t)f->n);
+    p.v = (double*)malloc(sizeof(double) * (size_t)f->n);
+    p.n = 0;
+    double last = 0.0;
+    for (int64_t k = 0; k < f->n; ++k) {
+        double w = f->v[k] / s;
+        if (kind == 1) w = sqrt(w);
+        if (k == 0 || w != last) {
+            p.t[p.n] = f->t[k];
+            p.v[p.n] = w;
+            p.n += 1;
+        }
+        last = w;
+    }
+    return p;
+}
+
+enum { ORC_RED_SUM = 0, ORC_RED_MEAN = 1, ORC_RED_MAX = 2, ORC_RED_MIN = 3, ORC_RED_STD = 4 };
+
+/*
+ * One group of m PCFs (rows [0, m) of off/t/v) reduced to one PCF:
+ *   SUM, MAX, MIN: the tree with h = a + b, max, min;
+ *   MEAN: (1/m) times the SUM tree (Sec. 2.1), the factor applied as v / m;
+ *   STD:  the sample standard deviation of Sec. 2.1,
+ *         sqrt( (1/(m-1)) sum_i (f_i - mean)^2 ), each (f_i - mean)^2 a
+ *         ReducePair with h = (a - b)^2, summed by the SUM tree (m >= 2).
+ */
+static orc_pcf orc_reduce_one(int64_t m, const int64_t* off, const double* t, const double* v,
+                              int red)
+{
+    orc_pcf* items = (orc_pcf*)malloc(sizeof(orc_pcf) * (size_t)m);
+    for (int64_t i = 0; i < m; ++i)
+        items[i] = orc_pcf_copy(t + off[i], v + off[i], off[i + 1] - off[i]);
+    int op = red == ORC_RED_MAX ? ORC_OP_MAX : red == ORC_RED_MIN ? ORC_OP_MIN : ORC_OP_ADD;
+    orc_pcf root = orc_tree(items, m, op);
+    if (red == ORC_RED_SUM || red == ORC_RED_MAX || red == ORC_RED_MIN) {
+        free(items);
+        return root;
+    }
+    orc_pcf mean = orc_map(&root, 0, (double)m);
+    orc_pcf_free(&root);
+    if (red == ORC_RED_MEAN) {
+        free(items);
+        return mean;
+    }
+    for (int64_t i = 0; i < m; ++i) {
+        orc_pcf fi = { (double*)(t + off[i]), (double*)(v + off[i]), off[i + 1] - off[i] };
+        items[i] = orc_pcf_pair(&fi, &mean, ORC_OP_SQDIFF);
+    }
+    orc_pcf ss = orc_tree(items, m, ORC_OP_ADD);
+    orc_pcf sd = orc_map(&ss, 1, (double)(m - 1));
+    orc_pcf_free(&ss);
+    orc_pcf_free(&mean);
+    free(items);
+    return sd;
+}
+
+typedef struct {
+    int64_t groups, m;
+    const int64_t* off; const double* t; const double* v;
+    int red;
+    orc_pcf* out;
+    int64_t next;
+    pthread_mutex_t lock;
+} orc_red_job;
+
+static void* orc_red_worker(void* arg)
+{
+    orc_red_job* J = (orc_red_job*)arg;
+    for (;;) {
+        pthread_mutex_lock(&J->lock);
+        int64_t g = J->next++;
+        pthread_mutex_unlock(&J->lock);
+        if (g >= J->groups) return NULL;
+        J->out[g] = orc_reduce_one(J->m, J->off + g * J->m, J->t, J->v, J->red);
+    }
+}
+
+/*
+ * Reduce each of `groups` consecutive groups of m PCFs (CSR off/t/v with
+ * groups * m rows) to one PCF.  Results go to out_off[groups + 1],
+ * out_t/out_v (capacity `cap` rows); returns the total row count, or -1 when
+ * `cap` is too small (out_off is then filled with the needed offsets).
+ */
+int64_t orc_reduce(int64_t groups, int64_t m, const int64_t* off, const double* t,
+                   const double* v, int red, int64_t* out_off, double* out_t, double* out_v,
+                   int64_t cap, int nthreads)
+{
+    orc_red_job J;
+    memset(&J, 0, sizeof J);
+    J.groups = groups; J.m = m; J.off = off; J.t = t; J.v = v; J.red = red;
+    J.out = (orc_pcf*)calloc((size_t)(groups > 0 ? groups : 1), sizeof(orc_pcf));
+    pthread_mutex_init(&J.lock, NULL);
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads == 1 || groups < 2) {
+        orc_red_worker(&J);
+    } else {
+        pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * (size_t)nthreads);
+        for (int i = 0; i < nthreads; ++i) pthread_create(&th[i], NULL, orc_red_worker, &J);
+        for (int i = 0; i < nthreads; ++i) pthread_join(th[i], NULL);
+        free(th);
+    }
+    pthread_mutex_destroy(&J.lock);
+    int64_t total = 0;
+    out_off[0] = 0;
+    for (int64_t g = 0; g < groups; ++g) {
+        total += J.out[g].n;
+        out_off[g + 1] = total;
+    }
+    int64_t rc = total <= cap ? total : -1;
+    if (rc >= 0)
+        for (int64_t g = 0; g < groups; ++g) {
+            memcpy(out_t + out_off[g], J.out[g].t, sizeof(double) * (size_t)J.out[g].n);
+            memcpy(out_v + out_off[g], J.out[g].v, sizeof(double) * (size_t)J.out[g].n);
+        }
+    for (int64_t g = 0; g < groups; ++g) orc_pcf_free(&J.out[g]);
+    free(J.out);
+    return rc;
 }
