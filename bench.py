@@ -46,9 +46,9 @@ FP64_OPS_PER_STEP = 1 + 1 + 1 + 2 + 2   # dt, d, L1 fma, L2 mul+fma, Gram mul+fm
 # DRAM bytes (read + write) per launch of the benchmark's compensated walk,
 # from one ncu capture (profiles/walk_f32c_dram_traffic_stable_rank_n20000.md),
 # valid only while the walk's source is the one that was measured.
-TRAFFIC_RECORD = {"source_sha256_16": "86af3e5fcb7598b3+7bc7a0f5c229a4b9",
-                  "by_schedule_layout": {("tile512x3", "full"): 33909303296 + 31404596224,
-                                         ("tile512x3", "sorted"): 287138048 + 5261150976}}
+TRAFFIC_RECORD = {"source_sha256_16": "987fde111d87bb84+4a2cccd684afe2ca",
+                  "by_schedule_layout": {("tile512x3", "full"): 33749118208 + 30960334080,
+                                         ("tile512x3", "sorted"): 263801856 + 5242910976}}
 
 
 def walk_source_id():
@@ -632,6 +632,53 @@ def run_workload(name, args):
                      forms=res,
                      cpu_baseline=_cpu_rows(s, ["l1"], seconds_target=8.0, row0=N // 3))
 
+    if name == "segments":
+        s = synth.lognormal(n_pcfs=args.n or 100000)
+        N = s.n
+        x = P.PcfTensors.from_numpy(s, dev)
+        out = torch.empty(N, dtype=torch.float64, device=dev)
+        ws = torch.empty(P.pcf_workspace_size(x, None, "f64"), dtype=torch.uint8, device=dev)
+
+        def step(prec):
+            P.pcf_segment_integrals(x, "lp", 2.0, True, precision=prec, out=out, workspace=ws,
+                                    check=False)
+            P.pcf_segment_integrals(x, "integral", precision=prec, out=out, workspace=ws,
+                                    check=False)
+        ms = float(np.mean(_timed(lambda: step("f32c"), args.steps, args.warmup, flush, stream)))
+        ms64 = float(np.mean(_timed(lambda: step("f64"), args.steps, args.warmup, flush, stream)))
+        P.pcf_check(ws)
+        seg_per_s = 2 * s.nnz / (ms * 1e-3)
+        hbm = float(measured_peaks().get("hbm_gbs", 6800.0)) * 1e9
+        bytes_per_call = s.nnz * 2 * 4 + (N + 1) * 8 + N * 8 + N * 8
+        fp64_rate = fp64(3)             # dt, h, fma per segment
+        import oracle
+        t0 = time.perf_counter()
+        k = 0
+        for i in range(0, N, 10):
+            t, v = s.pcf(i)
+            oracle.segment_integral(t, v, "lp", 2.0)
+            oracle.segment_integral(t, v, "integral")
+            k += 2 * t.size
+        dt = time.perf_counter() - t0
+        return _line(name, 2 * N / (ms * 1e-3), "PCF-integrals/s", ms, args.steps, args.warmup,
+                     "f32 (Kahan per segment)",
+                     {"workload": "segment iteration over the lognormal set N=100000 "
+                                  "(16.5M breakpoints): L2 norms and plain integrals over [0, inf)",
+                      "N": N, "nnz": s.nnz, "l2": "flushed between steps"},
+                     segments_per_s=seg_per_s,
+                     roofline={"bound": "hbm", "achieved": 2 * bytes_per_call / (ms * 1e-3) / 1e9,
+                               "peak": hbm / 1e9, "unit": "GB/s",
+                               "frac": (2 * bytes_per_call / (ms * 1e-3)) / hbm,
+                               "traffic": None,
+                               "note": "input bytes (times, values, offsets) + outputs per call; "
+                                       "each call also validates the input (a second read)"},
+                     f64={"ms_per_step": ms64, "segments_per_s": 2 * s.nnz / (ms64 * 1e-3),
+                          "fp64_frac": (2 * s.nnz / (ms64 * 1e-3)) / fp64_rate},
+                     cpu_baseline={"value": k / 2 / dt * (2 * N) / (2 * s.nnz) if dt else None,
+                                   "unit": "PCF-integrals/s", "cores": 1, "kind": "oracle",
+                                   "seconds": dt,
+                                   "sample": "every 10th PCF, both functionals, one thread"})
+
     if name == "gradient":
         s, G = synth.gradient(n_pcfs=args.n or 4096)
         N = s.n
@@ -736,7 +783,7 @@ def main():
                     help="force a walk schedule instead of autotuning it")
     ap.add_argument("--workload", default="stable_rank",
                     choices=["stable_rank", "uniform_small", "lognormal", "gradient", "euler",
-                             "appendix_a", "all"])
+                             "appendix_a", "segments", "all"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -745,7 +792,7 @@ def main():
     elif args.workload == "stable_rank":
         run_ours(args)
     else:
-        names = (["uniform_small", "gradient", "lognormal", "euler", "appendix_a"]
+        names = (["uniform_small", "gradient", "lognormal", "euler", "appendix_a", "segments"]
                  if args.workload == "all"
                  else [args.workload])
         for nm in names:

@@ -140,6 +140,20 @@ typedef struct pcf_schedule {
     int32_t reserved[4];  /* must be 0 */
 } pcf_schedule;
 
+/* Integration window and weight (pcf_pairwise_ex / pcf_cross_ex).
+ * The integrals become int_a^b h(f(t), g(t)) w(t) dt with 0 <= a < b <= inf
+ * (Alg. 1 takes the bounds a, b) and w(t) = exp(-lambda t), lambda >= 0,
+ * integrated per rectangle through its antiderivative (the time-dependent
+ * combinations of Sec. 2.1 and Sec. 3).  For float32 walks a, b and lambda
+ * are rounded to float32.  With b < inf nothing diverges.  Tile schedules
+ * only (PCF_SCHED_AUTO picks TILE_1024); lambda > 0 runs on TILE_1024. */
+typedef struct pcf_window {
+    double a;
+    double b;
+    double lambda;
+    int32_t reserved[4];   /* must be 0 */
+} pcf_window;
+
 /* A collection of N PCFs in CSR form (device arrays, read only).
  *   offsets[N+1] (int64): PCF i owns entries [offsets[i], offsets[i+1]);
  *                         offsets[0] = 0, offsets[N] = nnz, every PCF n_i >= 1.
@@ -203,14 +217,16 @@ int pcf_pairwise(const pcf_csr* x, const pcf_integral* F, int nF, int precision,
                  size_t workspace_bytes, cudaStream_t stream);
 
 /*
- * pcf_pairwise with an explicit work decomposition (NULL = PCF_SCHED_AUTO).
+ * pcf_pairwise with an explicit work decomposition (NULL = PCF_SCHED_AUTO)
+ * and integration window (NULL = [0, inf), no weight; see pcf_window).
  * Results are identical for every schedule up to the summation order of the
  * merge-path kernel (which combines 32 partial sums).  An unknown kernel or a
  * window outside its range returns PCF_EINVAL.
  */
 int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precision,
                     int layout, int out_dtype, int flags, const pcf_schedule* schedule,
-                    void* workspace, size_t workspace_bytes, cudaStream_t stream);
+                    const pcf_window* window, void* workspace, size_t workspace_bytes,
+                    cudaStream_t stream);
 
 /*
  * Cross matrices between rows [row_begin, row_end) of collection a and all of
@@ -225,11 +241,13 @@ int pcf_cross(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row
               int out_dtype, int flags, void* workspace, size_t workspace_bytes,
               cudaStream_t stream);
 
-/* pcf_cross with an explicit work decomposition (NULL = PCF_SCHED_AUTO). */
+/* pcf_cross with an explicit work decomposition (NULL = PCF_SCHED_AUTO) and
+ * integration window (NULL = [0, inf), no weight). */
 int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row_end,
                  const pcf_integral* F, int nF, int precision, int64_t ld_out,
-                 int out_dtype, int flags, const pcf_schedule* schedule, void* workspace,
-                 size_t workspace_bytes, cudaStream_t stream);
+                 int out_dtype, int flags, const pcf_schedule* schedule,
+                 const pcf_window* window, void* workspace, size_t workspace_bytes,
+                 cudaStream_t stream);
 
 /*
  * Gradient of L = sum_{i,j} G_ij F_ij, F the FULL pairwise matrix of `metric`
@@ -261,12 +279,13 @@ int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root
  * A PCF whose last value makes h != 0 integrates to +-inf when b = inf.
  * out: x->n elements of out_dtype.  The input is validated as for
  * pcf_pairwise (pcf_check reports invalid data).  Workspace:
- * pcf_workspace_size(x, NULL, PCF_PREC_F64, PCF_WS_FORWARD).  Accumulation is
- * float64 in every case.
+ * pcf_workspace_size(x, NULL, PCF_PREC_F64, PCF_WS_FORWARD).  precision:
+ * PCF_PREC_F64 (float64 arithmetic) or PCF_PREC_F32_COMP (float32 arithmetic,
+ * Kahan-compensated per segment; float64 input rounded to float32).
  */
 int pcf_segment_integrals(const pcf_csr* x, int functional, double p, int apply_root,
-                          double a, double b, void* out, int out_dtype, void* workspace,
-                          size_t workspace_bytes, cudaStream_t stream);
+                          double a, double b, int precision, void* out, int out_dtype,
+                          void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
 /*
  * The sort order used by the last pcf_prepare / pcf_pairwise on `workspace`

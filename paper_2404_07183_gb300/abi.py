@@ -53,6 +53,11 @@ class PcfSchedule(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 4)]
 
 
+class PcfWindow(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("lam", ctypes.c_double),
+                ("reserved", ctypes.c_int32 * 4)]
+
+
 class PcfIntegral(ctypes.Structure):
     _fields_ = [("metric", ctypes.c_int32), ("apply_root", ctypes.c_int32),
                 ("p", ctypes.c_double), ("out", ctypes.c_void_p)]
@@ -90,11 +95,12 @@ def load(build_if_missing: bool = False):
         lib.pcf_pairwise.argtypes = [CSR, INT, I, I, I, I, I, P, SZ, P]
         SCH = ctypes.POINTER(PcfSchedule)
         lib.pcf_pairwise_ex.restype = I
-        lib.pcf_pairwise_ex.argtypes = [CSR, INT, I, I, I, I, I, SCH, P, SZ, P]
+        WIN = ctypes.POINTER(PcfWindow)
+        lib.pcf_pairwise_ex.argtypes = [CSR, INT, I, I, I, I, I, SCH, WIN, P, SZ, P]
         lib.pcf_cross_ex.restype = I
-        lib.pcf_cross_ex.argtypes = [CSR, CSR, I64, I64, INT, I, I, I64, I, I, SCH, P, SZ, P]
+        lib.pcf_cross_ex.argtypes = [CSR, CSR, I64, I64, INT, I, I, I64, I, I, SCH, WIN, P, SZ, P]
         lib.pcf_segment_integrals.restype = I
-        lib.pcf_segment_integrals.argtypes = [CSR, I, D, I, D, D, P, I, P, SZ, P]
+        lib.pcf_segment_integrals.argtypes = [CSR, I, D, I, D, D, I, P, I, P, SZ, P]
         lib.pcf_sort_order.restype = I
         lib.pcf_sort_order.argtypes = [CSR, I, P, SZ, P, P]
         lib.pcf_prepare.restype = I

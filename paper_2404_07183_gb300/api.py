@@ -124,6 +124,16 @@ def _schedule(schedule, shard=None):
     return ctypes.byref(sc)
 
 
+def _window(window):
+    """None | (a, b) | (a, b, lam) -> PcfWindow pointer or None."""
+    if window is None:
+        return None
+    w = abi.PcfWindow()
+    w.a, w.b = float(window[0]), float(window[1])
+    w.lam = float(window[2]) if len(window) > 2 else 0.0
+    return ctypes.byref(w)
+
+
 def _stream_handle(stream):
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
@@ -177,8 +187,8 @@ def _requests(metrics, outs):
 
 
 def pcf_segment_integrals(x: PcfTensors, functional="lp", p=1.0, apply_root=False, a=0.0,
-                          b=float("inf"), out_dtype=torch.float64, out=None, workspace=None,
-                          stream=None, check=True):
+                          b=float("inf"), precision="f64", out_dtype=torch.float64, out=None,
+                          workspace=None, stream=None, check=True):
     """Per-PCF integrals over [a, b] by segment iteration (Sec. 3.2, Alg. 3):
     ``"integral"`` gives int f dt, ``"lp"`` gives int |f|^p dt (the L_p norm
     with ``apply_root``).  Returns a length-N tensor."""
@@ -190,7 +200,8 @@ def pcf_segment_integrals(x: PcfTensors, functional="lp", p=1.0, apply_root=Fals
     ws = _workspace(pcf_workspace_size(x, None, "f64"), dev, workspace)
     cx = x.csr()
     rc = lib.pcf_segment_integrals(ctypes.byref(cx), fn, float(p), int(bool(apply_root)),
-                                   float(a), float(b), ctypes.c_void_p(out.data_ptr()),
+                                   float(a), float(b), _prec(precision),
+                                   ctypes.c_void_p(out.data_ptr()),
                                    abi.PCF_F64 if out.dtype == torch.float64 else abi.PCF_F32,
                                    ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                    _stream_handle(stream))
@@ -230,8 +241,11 @@ def pcf_prepare(x: PcfTensors, precision="f32c", workspace=None, stream=None):
 
 def pcf_pairwise(x: PcfTensors, metrics=("l1",), precision="f32c", layout="full",
                  out_dtype=torch.float32, out=None, workspace=None, stream=None,
-                 check=True, prepared=False, schedule=None, shard=None):
+                 check=True, prepared=False, schedule=None, shard=None, window=None):
     """Pairwise matrices F(C) (Sec. 3.1) of ``x`` for each requested metric.
+
+    ``window=(a, b)`` or ``(a, b, lam)`` integrates over [a, b] with the
+    weight exp(-lam t) (tile schedules only).
 
     Returns a list of tensors: N x N (layout "full"), N(N+1)/2 ("upper"), or
     N x N in the library's sort order ("sorted"; see ``pcf_sort_order``)."""
@@ -254,7 +268,7 @@ def pcf_pairwise(x: PcfTensors, metrics=("l1",), precision="f32c", layout="full"
         raise ValueError("prepared=True needs the workspace returned by pcf_prepare")
     rc = lib.pcf_pairwise_ex(ctypes.byref(cx), req, len(metrics), _prec(precision), lay, od,
                              abi.PCF_PAIRWISE_PREPARED if prepared else 0,
-                             _schedule(schedule, shard),
+                             _schedule(schedule, shard), _window(window),
                              ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream))
     if rc != abi.PCF_OK:
         raise PcfError(rc, "pcf_pairwise")
@@ -266,7 +280,7 @@ def pcf_pairwise(x: PcfTensors, metrics=("l1",), precision="f32c", layout="full"
 def pcf_cross(a: PcfTensors, b: PcfTensors, row_begin=0, row_end=None, metrics=("l1",),
               precision="f32c", out_dtype=torch.float32, out=None, ld_out=None,
               reuse_b=False, workspace=None, stream=None, check=True, schedule=None,
-              shard=None):
+              shard=None, window=None):
     """Rows [row_begin, row_end) of the cross matrices a x b."""
     lib = abi.load()
     if isinstance(metrics, (str, tuple)):
@@ -285,6 +299,7 @@ def pcf_cross(a: PcfTensors, b: PcfTensors, row_begin=0, row_end=None, metrics=(
     rc = lib.pcf_cross_ex(ctypes.byref(ca), ctypes.byref(cb), int(row_begin), int(row_end), req,
                           len(metrics), _prec(precision), int(ld), od,
                           abi.PCF_CROSS_REUSE_B if reuse_b else 0, _schedule(schedule, shard),
+                          _window(window),
                           ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream))
     if rc != abi.PCF_OK:
         raise PcfError(rc, "pcf_cross")

@@ -153,15 +153,31 @@ int check_schedule(const pcf_schedule* sc)
     return PCF_OK;
 }
 
+int check_window(const pcf_window* w)
+{
+    if (!w) return PCF_OK;
+    if (!(w->a >= 0.0) || std::isinf(w->a) || !(w->b > w->a) || std::isnan(w->b)) return PCF_EINVAL;
+    if (!(w->lambda >= 0.0) || std::isinf(w->lambda)) return PCF_EINVAL;
+    for (int k = 0; k < 4; ++k) if (w->reserved[k] != 0) return PCF_EINVAL;
+    return PCF_OK;
+}
+
 int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int elem_bytes,
-              const pcf_schedule* sched, cudaStream_t s)
+              const pcf_schedule* sched, const pcf_window* win, cudaStream_t s)
 {
     const int sms = device_sm_count();
+    wa.lo = win ? win->a : 0.0;
+    wa.hi = win ? win->b : (double)INFINITY;
+    wa.lambda = win ? win->lambda : 0.0;
+    const bool windowed = wa.lo > 0.0 || !std::isinf(wa.hi) || wa.lambda > 0.0;
+    const bool weighted = wa.lambda > 0.0;
     wa.shard_count = (sched && sched->shard_count > 1) ? sched->shard_count : 1;
     wa.shard_index = (sched && sched->shard_count > 1) ? sched->shard_index : 0;
     int kernel = sched ? sched->kernel : PCF_SCHED_AUTO;
     if (kernel == PCF_SCHED_AUTO)
-        kernel = (wa.ntiles * 2 < sms) ? PCF_SCHED_MERGEPATH : PCF_SCHED_TILE_1024;
+        kernel = (wa.ntiles * 2 < sms && !windowed) ? PCF_SCHED_MERGEPATH : PCF_SCHED_TILE_1024;
+    if (windowed && kernel == PCF_SCHED_MERGEPATH) return PCF_EUNSUPPORTED;
+    if (weighted && kernel != PCF_SCHED_TILE_1024) return PCF_EUNSUPPORTED;
 
     int64_t grid = 0;
     size_t smem = 0;
@@ -221,6 +237,11 @@ int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int el
             else if (precision == PCF_PREC_F32_COMP) e = launch_walk_f32c_t512(L.combo, wa, g, smem, s);
             else if (precision == PCF_PREC_F32_BLOCK) e = launch_walk_f32b_t512(L.combo, wa, g, smem, s);
             else e = launch_walk_f32_t512(L.combo, wa, g, smem, s);
+        } else if (weighted) {
+            if (precision == PCF_PREC_F64) e = launch_walk_f64_t1024w(L.combo, wa, g, smem, s);
+            else if (precision == PCF_PREC_F32_COMP) e = launch_walk_f32c_t1024w(L.combo, wa, g, smem, s);
+            else if (precision == PCF_PREC_F32_BLOCK) e = launch_walk_f32b_t1024w(L.combo, wa, g, smem, s);
+            else e = launch_walk_f32_t1024w(L.combo, wa, g, smem, s);
         } else {
             if (precision == PCF_PREC_F64) e = launch_walk_f64_t1024(L.combo, wa, g, smem, s);
             else if (precision == PCF_PREC_F32_COMP) e = launch_walk_f32c_t1024(L.combo, wa, g, smem, s);
@@ -286,13 +307,14 @@ int pcf_pairwise(const pcf_csr* x, const pcf_integral* F, int nF, int precision,
                  int out_dtype, int flags, void* workspace, size_t workspace_bytes,
                  cudaStream_t stream)
 {
-    return pcf_pairwise_ex(x, F, nF, precision, layout, out_dtype, flags, nullptr, workspace,
-                           workspace_bytes, stream);
+    return pcf_pairwise_ex(x, F, nF, precision, layout, out_dtype, flags, nullptr, nullptr,
+                           workspace, workspace_bytes, stream);
 }
 
 int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precision, int layout,
-                    int out_dtype, int flags, const pcf_schedule* schedule, void* workspace,
-                    size_t workspace_bytes, cudaStream_t stream)
+                    int out_dtype, int flags, const pcf_schedule* schedule,
+                    const pcf_window* window, void* workspace, size_t workspace_bytes,
+                    cudaStream_t stream)
 {
     if (!csr_ok(x)) return PCF_EINVAL;
     if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32_BLOCK) return PCF_EINVAL;
@@ -301,6 +323,7 @@ int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precisi
     if (out_dtype != PCF_F32 && out_dtype != PCF_F64) return PCF_EINVAL;
     if (flags & ~PCF_PAIRWISE_PREPARED) return PCF_EINVAL;
     if (check_schedule(schedule) != PCF_OK) return PCF_EINVAL;
+    if (check_window(window) != PCF_OK) return PCF_EINVAL;
     int rc = check_requests(F, nF, x->n > 0);
     if (rc != PCF_OK) return rc;
     Header* hdr;
@@ -330,7 +353,7 @@ int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precisi
     wa.layout = layout;
     wa.out_f64 = out_dtype == PCF_F64;
     wa.ld_out = x->n;
-    return run_walks(wa, F, nF, precision, es, schedule, stream);
+    return run_walks(wa, F, nF, precision, es, schedule, window, stream);
 }
 
 int pcf_cross(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row_end,
@@ -338,13 +361,13 @@ int pcf_cross(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row
               int flags, void* workspace, size_t workspace_bytes, cudaStream_t stream)
 {
     return pcf_cross_ex(a, b, row_begin, row_end, F, nF, precision, ld_out, out_dtype, flags,
-                        nullptr, workspace, workspace_bytes, stream);
+                        nullptr, nullptr, workspace, workspace_bytes, stream);
 }
 
 int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row_end,
                  const pcf_integral* F, int nF, int precision, int64_t ld_out, int out_dtype,
-                 int flags, const pcf_schedule* schedule, void* workspace,
-                 size_t workspace_bytes, cudaStream_t stream)
+                 int flags, const pcf_schedule* schedule, const pcf_window* window,
+                 void* workspace, size_t workspace_bytes, cudaStream_t stream)
 {
     if (!csr_ok(a) || !csr_ok(b)) return PCF_EINVAL;
     if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32_BLOCK) return PCF_EINVAL;
@@ -353,6 +376,7 @@ int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t 
     if (ld_out < b->n) return PCF_EINVAL;
     if (flags & ~PCF_CROSS_REUSE_B) return PCF_EINVAL;
     if (check_schedule(schedule) != PCF_OK) return PCF_EINVAL;
+    if (check_window(window) != PCF_OK) return PCF_EINVAL;
     const int64_t rows = row_end - row_begin;
     int rc = check_requests(F, nF, rows > 0 && b->n > 0);
     if (rc != PCF_OK) return rc;
@@ -393,7 +417,7 @@ int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t 
     wa.layout = PCF_OUT_FULL;
     wa.out_f64 = out_dtype == PCF_F64;
     wa.ld_out = ld_out;
-    return run_walks(wa, F, nF, precision, es, schedule, stream);
+    return run_walks(wa, F, nF, precision, es, schedule, window, stream);
 }
 
 int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root,
@@ -450,10 +474,11 @@ int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root
 }
 
 int pcf_segment_integrals(const pcf_csr* x, int functional, double p, int apply_root,
-                          double a, double b, void* out, int out_dtype, void* workspace,
-                          size_t workspace_bytes, cudaStream_t stream)
+                          double a, double b, int precision, void* out, int out_dtype,
+                          void* workspace, size_t workspace_bytes, cudaStream_t stream)
 {
     if (!csr_ok(x)) return PCF_EINVAL;
+    if (precision != PCF_PREC_F64 && precision != PCF_PREC_F32_COMP) return PCF_EINVAL;
     if (functional != PCF_FN_INTEGRAL && functional != PCF_FN_LP) return PCF_EINVAL;
     if (functional == PCF_FN_LP && !(p >= 1.0 && std::isfinite(p))) return PCF_EINVAL;
     if (!(a >= 0.0) || !(b > a) || std::isnan(b) || std::isinf(a)) return PCF_EINVAL;
@@ -465,11 +490,11 @@ int pcf_segment_integrals(const pcf_csr* x, int functional, double p, int apply_
     if (rc != PCF_OK) return rc;
     init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
     if (x->n == 0) return cudaGetLastError() == cudaSuccess ? PCF_OK : PCF_ECUDA;
-    if (launch_validate(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz, 1, hdr, sv,
-                        stream) != cudaSuccess)
+    if (launch_validate(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz,
+                        precision == PCF_PREC_F64, hdr, sv, stream) != cudaSuccess)
         return PCF_ECUDA;
-    if (launch_segments(x, functional, p, apply_root, a, b, out, out_dtype == PCF_F64, hdr,
-                        stream) != cudaSuccess)
+    if (launch_segments(x, functional, p, apply_root, a, b, precision, out, out_dtype == PCF_F64,
+                        hdr, stream) != cudaSuccess)
         return PCF_ECUDA;
     return PCF_OK;
 }

@@ -109,6 +109,8 @@ struct WalkArgs {
     int64_t ld_out;          // cross: leading dimension; pairwise: N
     int64_t shard_index;     // this launch owns units u with u % shard_count == shard_index
     int64_t shard_count;     // >= 1
+    double lo, hi;           // integration bounds [lo, hi], 0 <= lo < hi <= inf
+    double lambda;           // weight exp(-lambda t) (weighted kernels only)
 };
 
 // Metric combination codes compiled into the walk kernels.
@@ -123,6 +125,7 @@ enum Combo : int {
     cudaError_t launch_walk_##name##_t1024(int, const WalkArgs&, int, size_t, cudaStream_t);    \
     cudaError_t launch_walk_##name##_t512(int, const WalkArgs&, int, size_t, cudaStream_t);     \
     cudaError_t launch_walk_##name##_t512x3(int, const WalkArgs&, int, size_t, cudaStream_t);   \
+    cudaError_t launch_walk_##name##_t1024w(int, const WalkArgs&, int, size_t, cudaStream_t);   \
     cudaError_t launch_mergepath_##name(int, const WalkArgs&, int64_t, int, cudaStream_t);
 PCF_DECL_WALK(f64)
 PCF_DECL_WALK(f32c)
@@ -146,8 +149,8 @@ cudaError_t launch_scatter_grad(const SetView& sv, const int64_t* offsets, const
                                 int out_f64, Header* hdr, cudaStream_t s);
 
 cudaError_t launch_segments(const pcf_csr* x, int functional, double p, int apply_root,
-                            double lo, double hi, void* out, int out_f64, const Header* hdr,
-                            cudaStream_t s);
+                            double lo, double hi, int precision, void* out, int out_f64,
+                            const Header* hdr, cudaStream_t s);
 cudaError_t launch_validate(const int64_t* offsets, const void* times, const void* values,
                             int in_dtype, int64_t n, int64_t nnz_total, int walk_f64,
                             Header* hdr, SetView& sv, cudaStream_t s);

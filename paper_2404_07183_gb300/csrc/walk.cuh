@@ -220,6 +220,22 @@ __device__ __forceinline__ double finalize_root(int metric, int root, double p, 
     return pow(I, 1.0 / e);
 }
 
+// Integral of the weight over a rectangle [l, l + dt): dt itself (WEIGHT 0),
+// or for w(t) = exp(-lambda t) the antiderivative difference W(l + dt) - W(l)
+// written as exp(-lambda l) * (-expm1(-lambda dt)) / lambda (WEIGHT 1).
+template <int WEIGHT>
+__device__ __forceinline__ float weight_span(float l, float dt, float lam, float inv_lam)
+{
+    if constexpr (WEIGHT == 0) return dt;
+    else return expf(-lam * l) * (-expm1f(-lam * dt)) * inv_lam;
+}
+template <int WEIGHT>
+__device__ __forceinline__ double weight_span(double l, double dt, double lam, double inv_lam)
+{
+    if constexpr (WEIGHT == 0) return dt;
+    else return exp(-lam * l) * (-expm1(-lam * dt)) * inv_lam;
+}
+
 __device__ __forceinline__ void decode_tile(const WalkArgs& a, int64_t t, int64_t& bi, int64_t& bj)
 {
     if (a.symmetric) {
@@ -249,7 +265,9 @@ __device__ __forceinline__ void decode_tile(const WalkArgs& a, int64_t t, int64_
 // four, so the window stays larger), and warp w walks lane l's pair
 // (row (l + w) mod 32, column l mod 16).  Both halves of a tile belong to the
 // same shard.
-template <typename T, int PREC, int COMBO, int THREADS, int CTAS>
+// WEIGHT: 0 = plain integrals, 1 = integrands weighted by exp(-lambda t).
+// Integration bounds [lo, hi] (WalkArgs) apply to every variant.
+template <typename T, int PREC, int COMBO, int THREADS, int CTAS, int WEIGHT = 0>
 __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
 {
     using E = typename ElemOf<T>::type;
@@ -275,6 +293,11 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
     const unsigned smem_base = (unsigned)__cvta_generic_to_shared(smem);
     const E* packR = reinterpret_cast<const E*>(a.pack_r);
     const E* packC = reinterpret_cast<const E*>(a.pack_c);
+    const T lo = (T)a.lo, hi = (T)a.hi;             // bounds in the walk type
+    // the walk closes at hi (no tail rule) when hi is finite or the weight
+    // makes the last rectangle [t_last, inf) finite: exp(-lam t_last) / lam
+    const bool bounded = hi < T(INFINITY) || WEIGHT != 0;
+    const T lam = (T)a.lambda, inv_lam = WEIGHT ? T(1) / (T)a.lambda : T(0);
 
     // this lane's pair inside every work unit
     const int my_r = (lane + warp) & 31;
@@ -309,15 +332,26 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                 sLen[tid] = 0;   // no PCF: never staged, never walked
                 sOff[tid] = 0;
             }
-            sS[tid] = 0;
+            int start = 0;
+            if (lo > T(0) && sLen[tid] > 0) {
+                // first element whose interval ends at or after lo
+                const E* src = (is_row ? packR : packC) + sOff[tid];
+                int l = 0, h = sLen[tid] - 1;
+                while (l < h) {
+                    const int m = (l + h) >> 1;
+                    if (src[m].x < lo) l = m + 1; else h = m;
+                }
+                start = l;
+            }
+            sS[tid] = start;
             sNext[tid] = 0;
             sStaged[tid] = -1;   // window start of what is in shared memory
         }
         const bool lane_valid = (bi * kTile + my_r < a.n_r) && (col0 + my_c < a.n_c);
 
         typename AccFor<PREC, COMBO>::type acc;
-        T tc = T(0);
-        T T0 = T(0);            // start of the current window (block-uniform)
+        T tc = lo;
+        T T0 = lo;              // start of the current window (block-uniform)
         __syncthreads();
 
         for (bool first = true;; first = false) {
@@ -339,7 +373,9 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                 if (lane == 0) sT1part[warp] = cand;
             }
             __syncthreads();
-            const T T1 = sT1part[0] < sT1part[1] ? sT1part[0] : sT1part[1];
+            T T1 = sT1part[0] < sT1part[1] ? sT1part[0] : sT1part[1];
+            if (T1 > hi) T1 = hi;
+            const bool last = !(T1 < hi);
             if (!(T1 > T0)) {
                 // more than W coincident interval ends in one PCF (only possible
                 // when float64 times were rounded to float32): no progress
@@ -400,7 +436,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
 #define PCF_WALK_STEP()                                                           \
                 {                                                                 \
                     const T tn = first_end(tf, tg);                               \
-                    const T dt = tn - tc;                                         \
+                    const T dt = weight_span<WEIGHT>(tc, tn - tc, lam, inv_lam);   \
                     tc = tn;                                                      \
                     acc.add(vf, vg, dt, p0);                                      \
                     advance_cursor<kRow>(af, tf, vf, ag, tg, vg);                 \
@@ -415,10 +451,14 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                 }
 #pragma unroll 1
                 for (; cnt > 0; --cnt) PCF_WALK_STEP()
+                if (last && bounded) {
+                    // closing rectangle [tc, hi) with the values holding at hi
+                    acc.add(vf, vg, weight_span<WEIGHT>(tc, hi - tc, lam, inv_lam), p0);
+                    tc = hi;
+                }
                 acc.flush();
 #undef PCF_WALK_STEP
             }
-            const bool last = !(T1 < T(INFINITY));
             __syncthreads();
             if (last) break;
             T0 = T1;
@@ -436,7 +476,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                 const int MI = combo_metric(COMBO, m);
                 double I = acc.value(m);
                 const T h = (MI == MI_GRAM) ? vlf * vlg : fabs(vlf - vlg);
-                if (h != T(0)) I = (h > T(0)) ? (double)INFINITY : -(double)INFINITY;
+                if (!bounded && h != T(0)) I = (h > T(0)) ? (double)INFINITY : -(double)INFINITY;
                 const double F = finalize_root(a.metric[m], a.root[m], a.p[m], I);
                 void* out = a.out[m];
                 auto put = [&](int64_t idx) {
@@ -462,7 +502,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
     }
 }
 
-template <typename T, int PREC, int THREADS, int CTAS = 1024 / THREADS>
+template <typename T, int PREC, int THREADS, int CTAS = 1024 / THREADS, int WEIGHT = 0>
 cudaError_t launch_walk_tt(int combo, const WalkArgs& a, int grid, size_t smem, cudaStream_t s)
 {
     auto go = [&](auto kern) -> cudaError_t {
@@ -472,13 +512,13 @@ cudaError_t launch_walk_tt(int combo, const WalkArgs& a, int grid, size_t smem, 
         return cudaGetLastError();
     };
     switch (combo) {
-    case kComboL1: return go(walk_kernel<T, PREC, kComboL1, THREADS, CTAS>);
-    case kComboL2: return go(walk_kernel<T, PREC, kComboL2, THREADS, CTAS>);
-    case kComboGram: return go(walk_kernel<T, PREC, kComboGram, THREADS, CTAS>);
-    case kComboLP: return go(walk_kernel<T, PREC, kComboLP, THREADS, CTAS>);
-    case kComboL3: return go(walk_kernel<T, PREC, kComboL3, THREADS, CTAS>);
-    case kComboL1L2Gram: return go(walk_kernel<T, PREC, kComboL1L2Gram, THREADS, CTAS>);
-    case kComboL1L2L3: return go(walk_kernel<T, PREC, kComboL1L2L3, THREADS, CTAS>);
+    case kComboL1: return go(walk_kernel<T, PREC, kComboL1, THREADS, CTAS, WEIGHT>);
+    case kComboL2: return go(walk_kernel<T, PREC, kComboL2, THREADS, CTAS, WEIGHT>);
+    case kComboGram: return go(walk_kernel<T, PREC, kComboGram, THREADS, CTAS, WEIGHT>);
+    case kComboLP: return go(walk_kernel<T, PREC, kComboLP, THREADS, CTAS, WEIGHT>);
+    case kComboL3: return go(walk_kernel<T, PREC, kComboL3, THREADS, CTAS, WEIGHT>);
+    case kComboL1L2Gram: return go(walk_kernel<T, PREC, kComboL1L2Gram, THREADS, CTAS, WEIGHT>);
+    case kComboL1L2L3: return go(walk_kernel<T, PREC, kComboL1L2L3, THREADS, CTAS, WEIGHT>);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -20,16 +20,19 @@ def pcf():
     return P
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32c"])
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 @pytest.mark.parametrize("kind,p,root", [("integral", 1.0, False), ("lp", 1.0, False),
                                          ("lp", 2.0, True), ("lp", 3.0, False),
                                          ("lp", 3.5, True)])
 @pytest.mark.parametrize("ab", [(0.0, np.inf), (0.5, 7.25), (3.0, 1e9)])
-def test_segments_vs_oracle(pcf, dtype, kind, p, root, ab):
+def test_segments_vs_oracle(pcf, prec, dtype, kind, p, root, ab):
     import torch
     s = synth.random_set(300, seed=101, min_len=1, max_len=90).astype(dtype)
     x = pcf.PcfTensors.from_numpy(s, "cuda")
-    got = pcf.pcf_segment_integrals(x, kind, p, root, ab[0], ab[1]).cpu().numpy()
+    got = pcf.pcf_segment_integrals(x, kind, p, root, ab[0], ab[1], precision=prec).cpu().numpy()
+    if prec == "f32c" and dtype == np.float64:
+        s = s.astype(np.float32)      # the float32 walk sees the rounded input
     for i in range(s.n):
         t, v = s.pcf(i)
         want = oracle.segment_integral(t, v, kind, p, ab[0], ab[1])
@@ -37,19 +40,28 @@ def test_segments_vs_oracle(pcf, dtype, kind, p, root, ab):
             want = want ** (1.0 / p)
         if np.isinf(want):
             assert got[i] == want
-        else:
+        elif prec == "f64":
             assert abs(got[i] - want) <= 1e-12 * max(1.0, abs(want)), (i, got[i], want)
+        else:
+            # float32 terms carry a few ulp each: bound by int |h| (its root for norms)
+            scale = oracle.segment_integral(t, v, "lp", 1.0 if kind == "integral" else p,
+                                            ab[0], ab[1])
+            if root and kind == "lp":
+                scale = scale ** (1.0 / p)
+            assert abs(got[i] - want) <= 1e-5 * scale + 1e-30, (i, got[i], want)
 
 
-def test_segments_dyadic_exact_and_edges(pcf):
+@pytest.mark.parametrize("prec", ["f64", "f32c"])
+def test_segments_dyadic_exact_and_edges(pcf, prec):
     s = synth.dyadic(200, seed=102, max_len=50, min_len=1, final_zero=False)
     x = pcf.PcfTensors.from_numpy(s, "cuda")
     for kind, p in (("integral", 1.0), ("lp", 2.0)):
-        got = pcf.pcf_segment_integrals(x, kind, p, False, 2.0, 40.0).cpu().numpy()
+        got = pcf.pcf_segment_integrals(x, kind, p, False, 2.0, 40.0,
+                                        precision=prec).cpu().numpy()
         want = np.array([oracle.segment_integral(*s.pcf(i), kind, p, 2.0, 40.0)
                          for i in range(s.n)])
         np.testing.assert_array_equal(got, want)
-        tail = pcf.pcf_segment_integrals(x, kind, p).cpu().numpy()
+        tail = pcf.pcf_segment_integrals(x, kind, p, precision=prec).cpu().numpy()
         want = np.array([oracle.segment_integral(*s.pcf(i), kind, p) for i in range(s.n)])
         np.testing.assert_array_equal(tail, want)     # +-inf where the last value != 0
 
@@ -70,6 +82,8 @@ def test_segments_reject_bad_arguments(pcf):
         pcf.pcf_segment_integrals(x, "lp", 0.5)
     with pytest.raises(pcf.PcfError):
         pcf.pcf_segment_integrals(x, "lp", 2.0, a=3.0, b=1.0)
+    with pytest.raises(pcf.PcfError):
+        pcf.pcf_segment_integrals(x, "lp", 2.0, precision="f32")
     t = s.times.copy()
     t[3] = t[2]
     bad = pcf.PcfTensors.from_numpy(synth.PcfSet(s.offsets, t, s.values), "cuda")
