@@ -304,9 +304,89 @@ int pcf_sort_order(const pcf_csr* x, int precision, const void* workspace,
  * float32 walk, 7 more coincident float32 times than one window holds) and
  * *index to the offending entry: an offsets error (reason 1, PCF index) is
  * reported before element errors, and among element errors the smallest
- * element index wins.  detail/index may be NULL.
+ * element index wins.  Reductions and combinations also report PCF_ENOWS
+ * with reason 8 when a result or an intermediate needs more rows than the
+ * output capacity or the workspace holds (*index = the rows needed, or the
+ * merge positions of the pass that did not fit).  detail/index may be NULL.
  */
 int pcf_check(const void* workspace, cudaStream_t stream, int* detail, int64_t* index);
+
+/* ------------------------------------------------------------------------
+ * Reductions and combinations of PCFs (Sec. 4; Sec. 2.1)
+ * ------------------------------------------------------------------------ */
+
+/* Reductions of a group of m PCFs (Sec. 2.1: reduction operations induced by
+ * an associative, symmetric h; the mean and the sample standard deviation). */
+enum pcf_reduction {
+    PCF_RED_SUM = 0,   /* f_1 + ... + f_m                                        */
+    PCF_RED_MEAN = 1,  /* (f_1 + ... + f_m) / m                                  */
+    PCF_RED_MAX = 2,   /* pointwise maximum                                      */
+    PCF_RED_MIN = 3,   /* pointwise minimum                                      */
+    PCF_RED_STD = 4    /* sqrt( sum_i (f_i - mean)^2 / (m - 1) ), m >= 2         */
+};
+
+/* Combination functions h of the induced operation h_*(f, g)(t) = h(f(t), g(t)). */
+enum pcf_op {
+    PCF_OP_ADD = 0, PCF_OP_SUB = 1, PCF_OP_MUL = 2, PCF_OP_MAX = 3, PCF_OP_MIN = 4,
+    PCF_OP_SQDIFF = 5  /* (a - b)^2 */
+};
+
+/* A caller-owned output collection (device arrays).  Results are float64.
+ *   offsets:  [n_out + 1] int64, written by the call (offsets[0] = 0).
+ *   times, values: capacity float64 rows each. */
+typedef struct pcf_csr_out {
+    int64_t capacity;
+    int64_t* offsets;
+    double* times;
+    double* values;
+} pcf_csr_out;
+
+/*
+ * Result rows: every reduction and combination builds its output with
+ * ReducePair (Sec. 4, Alg. 4): the merged breakpoints of its inputs, keeping
+ * a breakpoint when t = 0 or when the value changes there (a value equal to
+ * the one before is not repeated).  Arithmetic is float64; float32 input is
+ * widened exactly.
+ */
+
+/*
+ * Workspace bytes for pcf_reduce.  PCF_RED_STD also holds the intermediate
+ * PCFs (f_i - mean)^2; `std_rows` is the row capacity to reserve for them:
+ * 0 = the worst case (m + 1) * x->nnz, or exactly x->nnz + m * (rows of the
+ * group means), which pcf_reduce with PCF_RED_MEAN gives.  Ignored for the
+ * other reductions.  pcf_reduce uses whatever capacity the workspace it is
+ * given holds and checks it on the device (reason 8).
+ */
+int pcf_reduce_workspace_size(const pcf_csr* x, int64_t group_size, int reduction,
+                              int64_t std_rows, size_t* bytes);
+
+/*
+ * Reduce each of the x->n / group_size consecutive groups of group_size PCFs
+ * to one PCF (x->n must be a multiple of group_size).  The group is reduced
+ * by a binary tree of ReducePair nodes (Sec. 4, Fig. 2 with two inputs per
+ * node): on each level node k combines items 2k and 2k + 1, and an odd last
+ * item moves up unchanged.  MEAN divides the values of the sum by m; STD
+ * (m >= 2) reduces the ReducePair results (f_i - mean)^2 by a sum tree and
+ * maps v -> sqrt(v / (m - 1)) (the unbiased factor).  After a division or
+ * root, a value equal to the one before it is dropped as in Alg. 4.
+ * m = 1: SUM, MAX and MIN return the input rows unchanged.
+ *   out: group count + 1 offsets; capacity >= x->nnz always suffices.
+ * Input validated as for pcf_pairwise.  No host synchronization.
+ */
+int pcf_reduce(const pcf_csr* x, int64_t group_size, int reduction, pcf_csr_out* out,
+               void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/* Workspace bytes for pcf_combine(a, b, ...). */
+int pcf_combine_workspace_size(const pcf_csr* a, const pcf_csr* b, size_t* bytes);
+
+/*
+ * Elementwise combination h_*(a_i, b_i) (ReducePair, Sec. 4, Alg. 4) with
+ * h = op, for b->n == a->n, or h_*(a_i, b_0) for every i when b->n == 1.
+ *   out: a->n + 1 offsets; capacity >= a->nnz + b->nnz (pairs), or
+ *   a->nnz + a->n * b->nnz (one b) always suffices.
+ */
+int pcf_combine(const pcf_csr* a, const pcf_csr* b, int op, pcf_csr_out* out,
+                void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
 /* Bytes of the fixed device scratch array behind pcf_pairwise_noalloc. */
 #define PCF_NOALLOC_SCRATCH_BYTES (16u << 20)

@@ -29,11 +29,16 @@ ERR_DETAIL = {
     5: "value not finite",
     6: "time or value outside float32 range for a float32 walk",
     7: "more coincident float32 breakpoints than one window holds",
+    8: "result or intermediate larger than the output capacity or the workspace",
 }
 
 SYMBOLS = ("pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross", "pcf_pairwise_backward",
            "pcf_check", "pcf_status_string", "pcf_version", "pcf_pairwise_noalloc",
-           "pcf_pairwise_ex", "pcf_cross_ex", "pcf_sort_order", "pcf_segment_integrals")
+           "pcf_pairwise_ex", "pcf_cross_ex", "pcf_sort_order", "pcf_segment_integrals",
+           "pcf_reduce_workspace_size", "pcf_reduce", "pcf_combine_workspace_size",
+           "pcf_combine")
+PCF_RED_SUM, PCF_RED_MEAN, PCF_RED_MAX, PCF_RED_MIN, PCF_RED_STD = range(5)
+PCF_OP_ADD, PCF_OP_SUB, PCF_OP_MUL, PCF_OP_MAX, PCF_OP_MIN, PCF_OP_SQDIFF = range(6)
 PCF_FN_INTEGRAL, PCF_FN_LP = 0, 1
 PCF_SCHED_AUTO, PCF_SCHED_TILE_1024, PCF_SCHED_TILE_512X2, PCF_SCHED_MERGEPATH = 0, 1, 2, 3
 PCF_SCHED_TILE_512X3 = 4
@@ -56,6 +61,11 @@ class PcfSchedule(ctypes.Structure):
 class PcfWindow(ctypes.Structure):
     _fields_ = [("a", ctypes.c_double), ("b", ctypes.c_double), ("lam", ctypes.c_double),
                 ("reserved", ctypes.c_int32 * 4)]
+
+
+class PcfCsrOut(ctypes.Structure):
+    _fields_ = [("capacity", ctypes.c_int64), ("offsets", ctypes.c_void_p),
+                ("times", ctypes.c_void_p), ("values", ctypes.c_void_p)]
 
 
 class PcfIntegral(ctypes.Structure):
@@ -115,6 +125,15 @@ def load(build_if_missing: bool = False):
         lib.pcf_status_string.argtypes = [I]
         lib.pcf_pairwise_noalloc.restype = I
         lib.pcf_pairwise_noalloc.argtypes = [CSR, INT, I, I, I, I, P]
+        OUT = ctypes.POINTER(PcfCsrOut)
+        lib.pcf_reduce_workspace_size.restype = I
+        lib.pcf_reduce_workspace_size.argtypes = [CSR, I64, I, I64, ctypes.POINTER(SZ)]
+        lib.pcf_reduce.restype = I
+        lib.pcf_reduce.argtypes = [CSR, I64, I, OUT, P, SZ, P]
+        lib.pcf_combine_workspace_size.restype = I
+        lib.pcf_combine_workspace_size.argtypes = [CSR, CSR, ctypes.POINTER(SZ)]
+        lib.pcf_combine.restype = I
+        lib.pcf_combine.argtypes = [CSR, CSR, I, OUT, P, SZ, P]
         lib.pcf_version.restype = ctypes.c_char_p
         lib.pcf_version.argtypes = []
         _lib = lib

@@ -26,11 +26,15 @@ __all__ = ["PcfError", "PcfTensors", "pcf_workspace_size", "pcf_prepare", "pcf_s
            "pcf_pairwise", "pcf_cross",
            "pcf_cross_to_host",
            "pcf_pairwise_backward", "pcf_check", "PairwiseFn", "PairwiseGraph", "pdist",
-           "l2_kernel",
-           "parse_metric", "PRECISIONS"]
+           "l2_kernel", "pcf_reduce", "pcf_combine", "mean", "std",
+           "parse_metric", "PRECISIONS", "REDUCTIONS", "OPS"]
 
 PRECISIONS = {"f64": abi.PCF_PREC_F64, "f32c": abi.PCF_PREC_F32_COMP, "f32": abi.PCF_PREC_F32,
               "f32b": abi.PCF_PREC_F32_BLOCK}
+REDUCTIONS = {"sum": abi.PCF_RED_SUM, "mean": abi.PCF_RED_MEAN, "max": abi.PCF_RED_MAX,
+              "min": abi.PCF_RED_MIN, "std": abi.PCF_RED_STD}
+OPS = {"add": abi.PCF_OP_ADD, "sub": abi.PCF_OP_SUB, "mul": abi.PCF_OP_MUL, "max": abi.PCF_OP_MAX,
+       "min": abi.PCF_OP_MIN, "sqdiff": abi.PCF_OP_SQDIFF}
 _METRICS = {"l1": abi.PCF_L1, "l2": abi.PCF_L2, "lp": abi.PCF_LP, "gram": abi.PCF_GRAM}
 
 
@@ -457,3 +461,92 @@ def pdist(x: PcfTensors, p=1.0, precision="f64", out_dtype=torch.float64):
 def l2_kernel(x: PcfTensors, precision="f64", out_dtype=torch.float64):
     """L2 inner-product (Gram) matrix (the paper's ``l2_kernel``, Sec. 5.2)."""
     return pcf_pairwise(x, ["gram"], precision=precision, out_dtype=out_dtype)[0]
+
+
+def _csr_out(n_out, capacity, device):
+    off = torch.empty(n_out + 1, dtype=torch.int64, device=device)
+    t = torch.empty(max(capacity, 1), dtype=torch.float64, device=device)
+    v = torch.empty(max(capacity, 1), dtype=torch.float64, device=device)
+    c = abi.PcfCsrOut()
+    c.capacity, c.offsets, c.times, c.values = capacity, off.data_ptr(), t.data_ptr(), v.data_ptr()
+    return c, off, t, v
+
+
+def _trimmed(off, t, v):
+    rows = int(off[-1].item())
+    return PcfTensors(off, t[:rows], v[:rows])
+
+
+def pcf_reduce_workspace_size(x: PcfTensors, group_size, reduction="mean", std_rows=0) -> int:
+    lib = abi.load()
+    out = ctypes.c_size_t(0)
+    cx = x.csr()
+    rc = lib.pcf_reduce_workspace_size(ctypes.byref(cx), int(group_size), REDUCTIONS[reduction],
+                                       int(std_rows), ctypes.byref(out))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_reduce_workspace_size")
+    return int(out.value)
+
+
+def pcf_reduce(x: PcfTensors, group_size=None, reduction="mean", workspace=None, stream=None,
+               check=True, trim=True):
+    """Reduce each run of ``group_size`` consecutive PCFs (default: all of x)
+    to one PCF by a binary tree of ReducePair nodes (Sec. 4, Alg. 4, Fig. 2):
+    ``"sum"``, ``"mean"``, ``"max"``, ``"min"`` or the sample ``"std"``
+    (Sec. 2.1, factor 1/(m - 1)).  Returns float64 PcfTensors with one PCF
+    per group.  With ``trim`` the call synchronizes to size the result."""
+    lib = abi.load()
+    m = x.n if group_size is None else int(group_size)
+    if m < 1 or x.n % m:
+        raise ValueError("group_size must divide the number of PCFs")
+    dev = x.times.device
+    if workspace is None:
+        std_rows = 0
+        if reduction == "std":
+            # exact intermediate size from the means: nnz + m * rows of the means
+            std_rows = x.nnz + m * pcf_reduce(x, m, "mean", stream=stream, check=check).nnz
+        ws = _workspace(pcf_reduce_workspace_size(x, m, reduction, std_rows), dev, None)
+    else:
+        ws = workspace      # its capacity is checked by the library
+    out, off, t, v = _csr_out(x.n // m, x.nnz, dev)
+    cx = x.csr()
+    rc = lib.pcf_reduce(ctypes.byref(cx), m, REDUCTIONS[reduction], ctypes.byref(out),
+                        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_reduce")
+    if check:
+        pcf_check(ws, stream, "pcf_reduce")
+    return _trimmed(off, t, v) if trim else PcfTensors(off, t, v)
+
+
+def pcf_combine(a: PcfTensors, b: PcfTensors, op="add", workspace=None, stream=None, check=True,
+                trim=True):
+    """Elementwise h_*(a_i, b_i) (b with a's count) or h_*(a_i, b_0) (b with
+    one PCF) by ReducePair (Sec. 4, Alg. 4), h one of ``OPS``."""
+    lib = abi.load()
+    ca, cb = a.csr(), b.csr()
+    nbytes = ctypes.c_size_t(0)
+    rc = lib.pcf_combine_workspace_size(ctypes.byref(ca), ctypes.byref(cb), ctypes.byref(nbytes))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_combine_workspace_size")
+    dev = a.times.device
+    ws = _workspace(int(nbytes.value), dev, workspace)
+    cap = a.nnz + b.nnz if b.n == a.n else a.nnz + a.n * b.nnz
+    out, off, t, v = _csr_out(a.n, cap, dev)
+    rc = lib.pcf_combine(ctypes.byref(ca), ctypes.byref(cb), OPS[op], ctypes.byref(out),
+                         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_combine")
+    if check:
+        pcf_check(ws, stream, "pcf_combine")
+    return _trimmed(off, t, v) if trim else PcfTensors(off, t, v)
+
+
+def mean(x: PcfTensors, group_size=None, **kw):
+    """Mean of each group of PCFs (the paper's ``mean``, Sec. 5.1)."""
+    return pcf_reduce(x, group_size, "mean", **kw)
+
+
+def std(x: PcfTensors, group_size=None, **kw):
+    """Sample standard deviation of each group of PCFs (Sec. 2.1)."""
+    return pcf_reduce(x, group_size, "std", **kw)

@@ -530,7 +530,7 @@ int pcf_check(const void* workspace, cudaStream_t stream, int* detail, int64_t* 
     }
     if (detail) *detail = (int)(key & 15ull);
     if (index) *index = (int64_t)((key >> 4) & ((1ull << 58) - 1));
-    return PCF_EINVAL;
+    return (int)(key & 15ull) == kErrCapacity ? PCF_ENOWS : PCF_EINVAL;
 }
 
 const char* pcf_status_string(int status)

@@ -35,7 +35,7 @@ constexpr size_t kAlign = 256;
 //   is reported first, then the smallest offending element.
 enum ErrDetail : int {
     kErrOffsets = 1, kErrT0 = 2, kErrOrder = 3, kErrTimeNaN = 4,
-    kErrValueNaN = 5, kErrRange32 = 6, kErrDense32 = 7
+    kErrValueNaN = 5, kErrRange32 = 6, kErrDense32 = 7, kErrCapacity = 8
 };
 constexpr unsigned long long kNoError = ~0ull;
 
@@ -55,6 +55,14 @@ __device__ __forceinline__ void record_error(Header* h, int detail, long long in
                                    (((unsigned long long)index & ((1ull << 58) - 1)) << 4) |
                                    (unsigned long long)(detail & 15);
     atomicMin(&h->err, key);
+}
+
+// Block-uniform test of the error key, for kernels with block barriers
+// whose own blocks may record an error while other blocks start: one thread
+// reads it and every thread of the block gets the same answer.
+__device__ __forceinline__ bool block_sees_error(const Header* h)
+{
+    return __syncthreads_or(threadIdx.x == 0 && h->err != kNoError) != 0;
 }
 #endif
 

@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
     __shared__ T sT1part[2];
     __shared__ int64_t sTile;
 
-    if (a.hdr->err != kNoError) return;
+    if (block_sees_error(a.hdr)) return;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int W = a.window;
