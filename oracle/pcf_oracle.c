@@ -537,12 +537,14 @@ int64_t orc_reduce_pair(const double* tf, const double* vf, int64_t nf,
 /* A PCF owned by the tree code. */
 typedef struct { double* t; double* v; int64_t n; } orc_pcf;
 
+/* A copy of an input PCF.  A breakpoint at -0.0 (accepted as t_0 = 0) is
+ * stored as +0.0, the t_0 that ReducePair's first rectangle carries. */
 static orc_pcf orc_pcf_copy(const double* t, const double* v, int64_t n)
 {
     orc_pcf p;
     p.t = (double*)malloc(sizeof(double) * (size_t)n);
     p.v = (double*)malloc(sizeof(double) * (size_t)n);
-    memcpy(p.t, t, sizeof(double) * (size_t)n);
+    for (int64_t k = 0; k < n; ++k) p.t[k] = (t[k] == 0.0) ? 0.0 : t[k];
     memcpy(p.v, v, sizeof(double) * (size_t)n);
     p.n = n;
     return p;

@@ -185,3 +185,11 @@ def test_group_size_one():
     np.testing.assert_array_equal(v, s.values)
     with pytest.raises(ValueError):
         oracle.reduce(s, 4, "mean")
+
+
+def test_negative_zero_t0_reads_as_zero():
+    """t_0 = -0.0 is accepted as 0; every result carries +0.0 there."""
+    s = synth.PcfSet([0, 2, 4], np.array([-0.0, 1.0, 0.0, 2.0]), np.array([1.0, 2.0, 3.0, 4.0]))
+    for red, m in (("sum", 1), ("mean", 1), ("sum", 2), ("std", 2), ("max", 2)):
+        off, t, v = oracle.reduce(s, m, red)
+        assert np.all(np.signbit(t) == False), (red, m, t)    # noqa: E712
