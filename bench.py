@@ -679,6 +679,62 @@ def run_workload(name, args):
                                    "seconds": dt,
                                    "sample": "every 10th PCF, both functionals, one thread"})
 
+    if name == "reduce":
+        from paper_2404_07183_gb300 import api
+        s = synth.stable_rank(n_pcfs=args.n or 20480)
+        N = s.n
+        x = P.PcfTensors.from_numpy(s, dev)
+        hbm = float(measured_peaks().get("hbm_gbs", 6800.0)) * 1e9
+        forms = {}
+        for red, m in (("mean", 128), ("std", 16)):
+            std_rows = x.nnz + m * P.pcf_reduce(x, m, "mean").nnz if red == "std" else 0
+            ws = torch.empty(api.pcf_reduce_workspace_size(x, m, red, std_rows),
+                             dtype=torch.uint8, device=dev)
+            out = api._csr_out(N // m, x.nnz, dev)
+
+            def step():
+                P.pcf_reduce(x, m, red, workspace=ws, check=False, trim=False, out=out)
+            ms = float(np.mean(_timed(step, args.steps, args.warmup, flush, stream)))
+            P.pcf_check(ws)
+            pos, rows = api.pcf_reduce_counters(ws)
+            alg = 16 * s.nnz + 16 * (pos + rows)
+            forms[red] = {"group_size": m, "ms_per_step": ms,
+                          "breakpoints_per_s": s.nnz / (ms * 1e-3),
+                          "merge_positions": pos, "rows_written": rows,
+                          "merge_positions_per_s": pos / (ms * 1e-3),
+                          "hbm_frac": alg / (ms * 1e-3) / hbm,
+                          "result_rows": int(out[1][-1].item())}
+        import oracle
+        t0 = time.perf_counter()
+        sub = synth.subset(s, np.arange(16 * 128))
+        oracle.reduce(sub, 128, "mean")
+        sub_std = synth.subset(s, np.arange(64 * 16))
+        oracle.reduce(sub_std, 16, "std")
+        dt = time.perf_counter() - t0
+        cores = len(os.sched_getaffinity(0))
+        f = forms["mean"]
+        return _line(name, f["breakpoints_per_s"], "input-breakpoints/s", f["ms_per_step"],
+                     args.steps, args.warmup, "f64",
+                     {"workload": f"mean of {N // 128} groups of 128 stable-rank PCFs "
+                                  f"(N={N}, {s.nnz} breakpoints) by binary ReducePair trees; "
+                                  "std of groups of 16 alongside",
+                      "N": N, "nnz": s.nnz, "l2": "flushed between steps"},
+                     roofline={"bound": "hbm",
+                               "achieved": (16 * s.nnz + 16 * (f["merge_positions"]
+                                                               + f["rows_written"]))
+                               / (f["ms_per_step"] * 1e-3) / 1e9,
+                               "peak": hbm / 1e9, "unit": "GB/s", "frac": f["hbm_frac"],
+                               "traffic": None,
+                               "note": "16 B per input row read once, plus 16 B per merge "
+                                       "position and per row written over all ReducePair passes "
+                                       "(library work counters); the call also validates"},
+                     forms=forms,
+                     cpu_baseline={"value": (sub.nnz + sub_std.nnz) / dt,
+                                   "unit": "input-breakpoints/s", "cores": cores,
+                                   "kind": "oracle", "seconds": dt,
+                                   "sample": "mean of 16 groups of 128 and std of 64 groups "
+                                             "of 16, all host threads"})
+
     if name == "gradient":
         s, G = synth.gradient(n_pcfs=args.n or 4096)
         N = s.n
@@ -783,7 +839,7 @@ def main():
                     help="force a walk schedule instead of autotuning it")
     ap.add_argument("--workload", default="stable_rank",
                     choices=["stable_rank", "uniform_small", "lognormal", "gradient", "euler",
-                             "appendix_a", "segments", "all"])
+                             "appendix_a", "segments", "reduce", "all"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -792,7 +848,8 @@ def main():
     elif args.workload == "stable_rank":
         run_ours(args)
     else:
-        names = (["uniform_small", "gradient", "lognormal", "euler", "appendix_a", "segments"]
+        names = (["uniform_small", "gradient", "lognormal", "euler", "appendix_a", "segments",
+                  "reduce"]
                  if args.workload == "all"
                  else [args.workload])
         for nm in names:

@@ -388,6 +388,16 @@ int pcf_combine_workspace_size(const pcf_csr* a, const pcf_csr* b, size_t* bytes
 int pcf_combine(const pcf_csr* a, const pcf_csr* b, int op, pcf_csr_out* out,
                 void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
+/*
+ * Work done by the last pcf_reduce / pcf_combine on `workspace` (synchronizes
+ * `stream`): *positions = merge positions visited over all its ReducePair
+ * passes (one per input breakpoint of every pass), *rows = rows those passes
+ * wrote.  With 16-byte (t, v) rows, 16 * (positions + rows) bytes is the
+ * least DRAM traffic of the passes.  Either pointer may be NULL.
+ */
+int pcf_reduce_counters(const void* workspace, cudaStream_t stream, int64_t* positions,
+                        int64_t* rows);
+
 /* Bytes of the fixed device scratch array behind pcf_pairwise_noalloc. */
 #define PCF_NOALLOC_SCRATCH_BYTES (16u << 20)
 

@@ -36,7 +36,7 @@ SYMBOLS = ("pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross", "pc
            "pcf_check", "pcf_status_string", "pcf_version", "pcf_pairwise_noalloc",
            "pcf_pairwise_ex", "pcf_cross_ex", "pcf_sort_order", "pcf_segment_integrals",
            "pcf_reduce_workspace_size", "pcf_reduce", "pcf_combine_workspace_size",
-           "pcf_combine")
+           "pcf_combine", "pcf_reduce_counters")
 PCF_RED_SUM, PCF_RED_MEAN, PCF_RED_MAX, PCF_RED_MIN, PCF_RED_STD = range(5)
 PCF_OP_ADD, PCF_OP_SUB, PCF_OP_MUL, PCF_OP_MAX, PCF_OP_MIN, PCF_OP_SQDIFF = range(6)
 PCF_FN_INTEGRAL, PCF_FN_LP = 0, 1
@@ -134,6 +134,8 @@ def load(build_if_missing: bool = False):
         lib.pcf_combine_workspace_size.argtypes = [CSR, CSR, ctypes.POINTER(SZ)]
         lib.pcf_combine.restype = I
         lib.pcf_combine.argtypes = [CSR, CSR, I, OUT, P, SZ, P]
+        lib.pcf_reduce_counters.restype = I
+        lib.pcf_reduce_counters.argtypes = [P, P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
         lib.pcf_version.restype = ctypes.c_char_p
         lib.pcf_version.argtypes = []
         _lib = lib

@@ -26,7 +26,7 @@ __all__ = ["PcfError", "PcfTensors", "pcf_workspace_size", "pcf_prepare", "pcf_s
            "pcf_pairwise", "pcf_cross",
            "pcf_cross_to_host",
            "pcf_pairwise_backward", "pcf_check", "PairwiseFn", "PairwiseGraph", "pdist",
-           "l2_kernel", "pcf_reduce", "pcf_combine", "mean", "std",
+           "l2_kernel", "pcf_reduce", "pcf_combine", "pcf_reduce_counters", "mean", "std",
            "parse_metric", "PRECISIONS", "REDUCTIONS", "OPS"]
 
 PRECISIONS = {"f64": abi.PCF_PREC_F64, "f32c": abi.PCF_PREC_F32_COMP, "f32": abi.PCF_PREC_F32,
@@ -488,8 +488,19 @@ def pcf_reduce_workspace_size(x: PcfTensors, group_size, reduction="mean", std_r
     return int(out.value)
 
 
+def pcf_reduce_counters(workspace: torch.Tensor, stream=None):
+    """(merge positions, rows written) of the last reduction on ``workspace``."""
+    lib = abi.load()
+    pos, rows = ctypes.c_int64(0), ctypes.c_int64(0)
+    rc = lib.pcf_reduce_counters(ctypes.c_void_p(workspace.data_ptr()), _stream_handle(stream),
+                                 ctypes.byref(pos), ctypes.byref(rows))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_reduce_counters")
+    return int(pos.value), int(rows.value)
+
+
 def pcf_reduce(x: PcfTensors, group_size=None, reduction="mean", workspace=None, stream=None,
-               check=True, trim=True):
+               check=True, trim=True, out=None):
     """Reduce each run of ``group_size`` consecutive PCFs (default: all of x)
     to one PCF by a binary tree of ReducePair nodes (Sec. 4, Alg. 4, Fig. 2):
     ``"sum"``, ``"mean"``, ``"max"``, ``"min"`` or the sample ``"std"``
@@ -508,7 +519,9 @@ def pcf_reduce(x: PcfTensors, group_size=None, reduction="mean", workspace=None,
         ws = _workspace(pcf_reduce_workspace_size(x, m, reduction, std_rows), dev, None)
     else:
         ws = workspace      # its capacity is checked by the library
-    out, off, t, v = _csr_out(x.n // m, x.nnz, dev)
+    if out is None:
+        out = _csr_out(x.n // m, x.nnz, dev)
+    out, off, t, v = out
     cx = x.csr()
     rc = lib.pcf_reduce(ctypes.byref(cx), m, REDUCTIONS[reduction], ctypes.byref(out),
                         ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream))

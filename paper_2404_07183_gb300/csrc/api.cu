@@ -530,7 +530,10 @@ int pcf_check(const void* workspace, cudaStream_t stream, int* detail, int64_t* 
     }
     if (detail) *detail = (int)(key & 15ull);
     if (index) *index = (int64_t)((key >> 4) & ((1ull << 58) - 1));
-    return (int)(key & 15ull) == kErrCapacity ? PCF_ENOWS : PCF_EINVAL;
+    const int reason = (int)(key & 15ull);
+    if (reason == kErrCapacity) return PCF_ENOWS;
+    if (reason == kErrWait) return PCF_ETIMEOUT;
+    return PCF_EINVAL;
 }
 
 const char* pcf_status_string(int status)

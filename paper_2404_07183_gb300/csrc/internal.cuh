@@ -35,7 +35,7 @@ constexpr size_t kAlign = 256;
 //   is reported first, then the smallest offending element.
 enum ErrDetail : int {
     kErrOffsets = 1, kErrT0 = 2, kErrOrder = 3, kErrTimeNaN = 4,
-    kErrValueNaN = 5, kErrRange32 = 6, kErrDense32 = 7, kErrCapacity = 8
+    kErrValueNaN = 5, kErrRange32 = 6, kErrDense32 = 7, kErrCapacity = 8, kErrWait = 9
 };
 constexpr unsigned long long kNoError = ~0ull;
 

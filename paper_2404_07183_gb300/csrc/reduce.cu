@@ -65,9 +65,13 @@ struct RpArgs {
     double2* out_el;          // AoS output, or
     double* out_t; double* out_v;   // SoA output (out_t != nullptr)
     int64_t out_cap;          // rows available in the output
-    int64_t* chunk;           // [nchunk_cap]: counts, then exclusive bases
+    unsigned long long* state;  // [nchunk_cap + 1]: ticket, then chunk states (zeroed)
+    int64_t* part;              // [nchunk_cap]: first output PCF of each chunk
     int64_t nchunk_cap;
+    unsigned long long div_M;   // p / (c_out or m) = (p * div_M) >> div_s, p < 2^31
+    int div_s;
     Header* hdr;
+    unsigned long long* stats;  // [0] merge positions, [1] rows written (per call)
 };
 
 __device__ __forceinline__ double rp_h(int op, double a, double b)
@@ -89,16 +93,24 @@ __device__ __forceinline__ double rp_map(int op, double v, double s)
     return v;
 }
 
+// p / d for 0 <= p < 2^31 by multiply and shift: with s = 31 + ceil(log2 d)
+// and M = ceil(2^s / d), p*M/2^s exceeds p/d by less than 2^31/2^s <= 1/d,
+// which never reaches the next integer.
+__device__ __forceinline__ int64_t rp_div(const RpArgs& a, int64_t p)
+{
+    return (int64_t)(((unsigned long long)p * a.div_M) >> a.div_s);
+}
+
 // First merge position of output p (p = P gives the total).
 __device__ __forceinline__ int64_t rp_item_off(const RpArgs& a, int64_t p)
 {
     switch (a.mode) {
     case kModeTree: {
-        const int64_t g = p / a.c_out, k = p - g * a.c_out;
+        const int64_t g = rp_div(a, p), k = p - g * a.c_out;
         return a.a_off[g * a.c_in + 2 * k];
     }
     case kModeBcast: {
-        const int64_t g = p / a.m, r = p - g * a.m;
+        const int64_t g = rp_div(a, p), r = p - g * a.m;
         int64_t o = a.a_off[p] + a.m * a.b_off[g];
         if (r) o += r * (a.b_off[g + 1] - a.b_off[g]);
         return o;
@@ -116,7 +128,7 @@ __device__ __forceinline__ void rp_operands(const RpArgs& a, int64_t p, const do
     const double2* bel = a.b_el;
     switch (a.mode) {
     case kModeTree: {
-        const int64_t g = p / a.c_out, k = p - g * a.c_out;
+        const int64_t g = rp_div(a, p), k = p - g * a.c_out;
         const int64_t ia = g * a.c_in + 2 * k;
         a0 = a.a_off[ia]; a1 = a.a_off[ia + 1];
         if (2 * k + 1 < a.c_in) { b0 = a1; b1 = a.a_off[ia + 2]; }
@@ -124,7 +136,7 @@ __device__ __forceinline__ void rp_operands(const RpArgs& a, int64_t p, const do
         break;
     }
     case kModeBcast: {
-        const int64_t g = p / a.m;
+        const int64_t g = rp_div(a, p);
         a0 = a.a_off[p]; a1 = a.a_off[p + 1]; b0 = a.b_off[g]; b1 = a.b_off[g + 1];
         break;
     }
@@ -149,8 +161,8 @@ __device__ __forceinline__ int64_t rp_find(const RpArgs& a, int64_t q, int64_t l
     return lo;
 }
 
-// Inclusive block scan of one int per thread (256 threads); returns the
-// thread's exclusive prefix and the block total.
+// Exclusive block scan of one int per thread (256 threads); also returns the
+// block total.
 __device__ __forceinline__ int rp_block_scan(int x, int& total, int* warp_sums)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -174,175 +186,215 @@ __device__ __forceinline__ int rp_block_scan(int x, int& total, int* warp_sums)
     __syncthreads();
     total = warp_sums[kRpThreads / 32 - 1];
     const int before = warp ? warp_sums[warp - 1] : 0;
-    __syncthreads();
     return before + v - x;
 }
 
-// Count pass (WRITE = false) and write pass (WRITE = true) over the chunks.
-template <bool WRITE>
+// Times are non-negative (t_0 = -0.0 is stored as +0.0), so their float64
+// bit patterns order like the values and compare on the integer pipe.
+__device__ __forceinline__ long long tkey(double t) { return __double_as_longlong(t); }
+
+// a == b as float64 values (+0 == -0, NaN != NaN), on the integer pipe.
+__device__ __forceinline__ bool vsame(double a, double b)
+{
+    const unsigned long long x = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long y = (unsigned long long)__double_as_longlong(b);
+    const bool not_nan = (x & 0x7fffffffffffffffull) <= 0x7ff0000000000000ull;
+    return (x == y && not_nan) || ((x | y) << 1) == 0;
+}
+
+// Chunk states of the single-pass scan: flag in bits 62-63, value below.
+constexpr unsigned long long kStAgg = 1ull << 62;    // the chunk's own row count
+constexpr unsigned long long kStIncl = 2ull << 62;   // rows of chunks 0..c
+constexpr unsigned long long kStErr = 3ull << 62;    // gave up: successors stop too
+constexpr unsigned long long kStVal = (1ull << 62) - 1;
+constexpr long long kSpinPolls = 1ll << 20;          // per predecessor, ~0.1 s
+
+// Output position of chunk c's first row (decoupled look-back, one thread):
+// publish this chunk's count, add predecessors' counts until one publishes
+// its inclusive prefix, publish ours.  Chunks are taken in ticket order, so
+// every predecessor is running or done; each wait is bounded and an error
+// anywhere makes the waiters give up.  Returns -1 on giving up.
+__device__ long long rp_look_back(const RpArgs& a, long long c, int count)
+{
+    unsigned long long* st = a.state + 1;
+    if (c == 0) {
+        atomicExch(&st[0], kStIncl | (unsigned long long)count);
+        return 0;
+    }
+    atomicExch(&st[c], kStAgg | (unsigned long long)count);
+    long long excl = 0;
+    for (long long pred = c - 1;; --pred) {
+        unsigned long long v = 0;
+        long long polls = 0;
+        for (;;) {
+            v = __ldcg(&st[pred]);                      // L2, coherent across SMs
+            if (v >> 62) break;
+            if (++polls > kSpinPolls ||
+                ((polls & 1023) == 0 && __ldcg(&a.hdr->err) != kNoError)) {
+                v = kStErr;
+                break;
+            }
+            __nanosleep(64);
+        }
+        if ((v >> 62) == 3) {
+            atomicExch(&st[c], kStErr);
+            record_error(a.hdr, kErrWait, c);
+            return -1;
+        }
+        excl += (long long)(v & kStVal);
+        if ((v >> 62) == 2) break;
+    }
+    atomicExch(&st[c], kStIncl | (unsigned long long)(excl + count));
+    return excl;
+}
+
+// One merge-and-compact pass.  Persistent CTAs take 2048-position chunks by
+// ticket; each thread walks 8 positions, the CTA counts the kept rows, finds
+// their output position by look-back and writes them.
 __global__ void __launch_bounds__(kRpThreads) rp_kernel(const RpArgs a)
 {
-    __shared__ int64_t sP[2];
+    __shared__ long long sChunk, sBase;
     __shared__ int warp_sums[kRpThreads / 32];
+    __shared__ double2 sRow[kRpChunk];             // rows of slot tid * 8 + k
+    __shared__ int sExcl[kRpThreads];
+    __shared__ unsigned sKeep[kRpThreads];
     if (block_sees_error(a.hdr)) return;
     const int64_t total = rp_item_off(a, a.P);
     const int64_t nch = (total + kRpChunk - 1) / kRpChunk;
-    if (!WRITE && blockIdx.x == 0 && threadIdx.x == 0 && nch > a.nchunk_cap)
-        record_error(a.hdr, kErrCapacity, total);
-    const int64_t nrun = nch < a.nchunk_cap ? nch : a.nchunk_cap;
+    if (nch > a.nchunk_cap) {              // the same decision in every block
+        if (blockIdx.x == 0 && threadIdx.x == 0) record_error(a.hdr, kErrCapacity, total);
+        return;
+    }
+    const double2 inf2 = make_double2(INFINITY, 0.0);
 
-    for (int64_t c = blockIdx.x; c < nrun; c += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) sChunk = (long long)atomicAdd(a.state, 1ull);
+        __syncthreads();
+        const long long c = sChunk;
+        if (c >= nch) break;
         const int64_t cq0 = c * kRpChunk;
         const int64_t cq1 = (cq0 + kRpChunk < total ? cq0 + kRpChunk : total) - 1;
-        if (threadIdx.x == 0) {
-            const int64_t p0 = rp_find(a, cq0, 0, a.P - 1);
-            sP[0] = p0;
-            sP[1] = rp_find(a, cq1, p0, a.P - 1);
-        }
-        __syncthreads();
+        const int64_t p_lo = a.part[c], p_hi = c + 1 < nch ? a.part[c + 1] : a.P - 1;
         const int64_t q0 = cq0 + (int64_t)threadIdx.x * kRpItems;
 
         unsigned keep = 0, starts = 0;
         int64_t pstart = 0;
-        double kt[kRpItems], kv[kRpItems];
         if (q0 <= cq1) {
-            int64_t p = rp_find(a, q0, sP[0], sP[1]);
-            int64_t base = rp_item_off(a, p);
+            int64_t p = rp_find(a, q0, p_lo, p_hi);
             const double2* A; const double2* B;
             int64_t na, nb;
             rp_operands(a, p, A, na, B, nb);
             // merge-path split: i of A's and j of B's breakpoints precede q0
-            const int64_t d = q0 - base;
+            const int64_t d = q0 - rp_item_off(a, p);
             int64_t lo = d - nb > 0 ? d - nb : 0, hi = d < na ? d : na;
             while (lo < hi) {
                 const int64_t mid = (lo + hi) >> 1;
-                if (A[mid].x <= B[d - 1 - mid].x) lo = mid + 1; else hi = mid;
+                if (tkey(A[mid].x) <= tkey(B[d - 1 - mid].x)) lo = mid + 1; else hi = mid;
             }
             int64_t i = lo, j = d - lo;
-            const double2 inf2 = make_double2(INFINITY, 0.0);
             double2 eA = i < na ? A[i] : inf2, eB = j < nb ? B[j] : inf2;
-            double2 pA1 = i >= 1 ? A[i - 1] : inf2, pA2 = i >= 2 ? A[i - 2] : inf2;
-            double2 pB1 = j >= 1 ? B[j - 1] : inf2, pB2 = j >= 2 ? B[j - 2] : inf2;
+            // values of the breakpoints consumed last on each side
+            double fA = i >= 1 ? A[i - 1].y : 0.0, fB = j >= 1 ? B[j - 1].y : 0.0;
+            bool have_last = false;      // value of the previous distinct time known
+            double vlast = 0.0;
 #pragma unroll
             for (int k = 0; k < kRpItems; ++k) {
-                const int64_t q = q0 + k;
-                if (q <= cq1) {
+                if (q0 + k <= cq1) {
                     if (i + j == na + nb) {             // next output PCF
                         ++p;
-                        base = rp_item_off(a, p);
                         rp_operands(a, p, A, na, B, nb);
                         i = 0; j = 0;
                         eA = A[0]; eB = nb ? B[0] : inf2;
-                        pA1 = pA2 = pB1 = pB2 = inf2;
+                        have_last = false;
                     }
                     if (i + j == 0) {                    // first position of output p
                         if (!starts) pstart = p;
                         starts |= 1u << k;
                     }
-                    const bool takeA = (j >= nb) || (i < na && eA.x <= eB.x);
-                    double t;
-                    if (takeA) {
-                        t = eA.x;
-                        pA2 = pA1; pA1 = eA; ++i;
+                    const long long ta = tkey(eA.x), tb = tkey(eB.x);
+                    const bool fromA = ta <= tb;         // ties: A's breakpoint first
+                    const long long t = fromA ? ta : tb;
+                    if (fromA) {
+                        fA = eA.y; ++i;
                         eA = i < na ? A[i] : inf2;
                     } else {
-                        t = eB.x;
-                        pB2 = pB1; pB1 = eB; ++j;
+                        fB = eB.y; ++j;
                         eB = j < nb ? B[j] : inf2;
                     }
-                    const double tn = eA.x < eB.x ? eA.x : eB.x;
+                    const long long na_t = tkey(eA.x), nb_t = tkey(eB.x);
+                    const long long tn = na_t < nb_t ? na_t : nb_t;
                     bool kp = false;
                     double v = 0.0;
                     if (tn != t) {                       // last position with this time
                         if (a.mode == kModeMap) {
-                            v = rp_map(a.op, pA1.y, a.s);
-                            kp = (t == 0.0) || a.op == kOpCopy || v != rp_map(a.op, pA2.y, a.s);
+                            v = rp_map(a.op, fA, a.s);
+                            if (t == 0 || a.op == kOpCopy) kp = true;
+                            else kp = !vsame(v, have_last ? vlast : rp_map(a.op, A[i - 2].y, a.s));
                         } else if (nb == 0) {            // odd item moving up the tree
-                            v = pA1.y;
+                            v = fA;
                             kp = true;
                         } else {
-                            v = rp_h(a.op, pA1.y, pB1.y);
-                            if (t == 0.0) {
+                            v = rp_h(a.op, fA, fB);
+                            if (t == 0) {
                                 kp = true;
                             } else {
-                                const double fa = pA1.x == t ? pA2.y : pA1.y;
-                                const double gb = pB1.x == t ? pB2.y : pB1.y;
-                                kp = v != rp_h(a.op, fa, gb);
+                                double vp = vlast;
+                                if (!have_last) {        // values just before t, from memory
+                                    const double fa = tkey(A[i - 1].x) == t ? A[i - 2].y : fA;
+                                    const double gb = tkey(B[j - 1].x) == t ? B[j - 2].y : fB;
+                                    vp = rp_h(a.op, fa, gb);
+                                }
+                                kp = !vsame(v, vp);
                             }
                         }
+                        vlast = v;
+                        have_last = true;
                     }
-                    if (kp) keep |= 1u << k;
-                    kt[k] = t;
-                    kv[k] = v;
+                    if (kp) {
+                        keep |= 1u << k;
+                        sRow[threadIdx.x * kRpItems + k] = make_double2(__longlong_as_double(t), v);
+                    }
                 }
             }
         }
         int block_total;
-        const int mine = __popc(keep);
-        const int excl = rp_block_scan(mine, block_total, warp_sums);
-        if (!WRITE) {
-            if (threadIdx.x == 0) a.chunk[c] = block_total;
-        } else {
-            int64_t pos = a.chunk[c] + excl;
-            int64_t pc = pstart;
+        const int excl = rp_block_scan(__popc(keep), block_total, warp_sums);
+        sExcl[threadIdx.x] = excl;
+        sKeep[threadIdx.x] = keep;
+        if (threadIdx.x == 0) sBase = rp_look_back(a, c, block_total);
+        __syncthreads();
+        const long long base = sBase;
+        if (base < 0) break;
+        // offsets of the output PCFs that start in this thread's positions
+        int64_t pc = pstart;
 #pragma unroll
-            for (int k = 0; k < kRpItems; ++k) {
-                if (starts & (1u << k)) a.out_off[pc++] = pos;
-                if (keep & (1u << k)) {
-                    if (pos < a.out_cap) {
-                        if (a.out_t) { a.out_t[pos] = kt[k]; a.out_v[pos] = kv[k]; }
-                        else a.out_el[pos] = make_double2(kt[k], kv[k]);
-                    }
-                    ++pos;
-                }
+        for (int k = 0; k < kRpItems; ++k)
+            if (starts & (1u << k)) a.out_off[pc++] = base + excl + __popc(keep & ((1u << k) - 1));
+        // the chunk's rows are contiguous in the output: write them in order
+        for (int o = threadIdx.x; o < block_total; o += kRpThreads) {
+            int lo_t = 0, hi_t = kRpThreads - 1;       // last thread with sExcl <= o
+            while (lo_t < hi_t) {
+                const int mid = (lo_t + hi_t + 1) >> 1;
+                if (sExcl[mid] <= o) lo_t = mid; else hi_t = mid - 1;
+            }
+            unsigned m = sKeep[lo_t];
+            for (int r = o - sExcl[lo_t]; r > 0; --r) m &= m - 1;   // drop r lowest set bits
+            if (!m) continue;                                       // (cannot happen)
+            const double2 row = sRow[lo_t * kRpItems + (__ffs(m) - 1)];
+            const long long pos = base + o;
+            if (pos < a.out_cap) {
+                if (a.out_t) { a.out_t[pos] = row.x; a.out_v[pos] = row.y; }
+                else a.out_el[pos] = row;
             }
         }
-        __syncthreads();
-    }
-}
-
-// Exclusive scan of the chunk counts (one CTA); out_off[P] = total rows.
-__global__ void __launch_bounds__(1024) rp_scan_kernel(const RpArgs a)
-{
-    __shared__ int64_t warp_sums[32];
-    __shared__ int64_t carry;
-    if (block_sees_error(a.hdr)) return;
-    const int64_t total = rp_item_off(a, a.P);
-    int64_t nch = (total + kRpChunk - 1) / kRpChunk;
-    if (nch > a.nchunk_cap) nch = a.nchunk_cap;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int64_t base = 0; base < nch; base += 1024) {
-        const int64_t idx = base + threadIdx.x;
-        const int64_t x = idx < nch ? a.chunk[idx] : 0;
-        int64_t v = x;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int64_t y = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += y;
-        }
-        if (lane == 31) warp_sums[warp] = v;
-        __syncthreads();
-        if (warp == 0) {
-            int64_t w = warp_sums[lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int64_t y = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += y;
-            }
-            warp_sums[lane] = w;
+        if (c == nch - 1 && threadIdx.x == 0) {
+            const long long rows = base + block_total;
+            a.out_off[a.P] = rows;
+            if (rows > a.out_cap) record_error(a.hdr, kErrCapacity, rows);
+            a.stats[0] += (unsigned long long)total;
+            a.stats[1] += (unsigned long long)rows;
         }
         __syncthreads();
-        const int64_t excl = carry + (warp ? warp_sums[warp - 1] : 0) + v - x;
-        if (idx < nch) a.chunk[idx] = excl;
-        __syncthreads();
-        if (threadIdx.x == 0) carry += warp_sums[31];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        a.out_off[a.P] = carry;
-        if (carry > a.out_cap) record_error(a.hdr, kErrCapacity, carry);
     }
 }
 
@@ -354,15 +406,30 @@ __global__ void rp_pack_kernel(const T* __restrict__ t, const T* __restrict__ v,
     if (hdr->err != kNoError) return;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nnz;
          k += (int64_t)gridDim.x * blockDim.x)
-        el[k] = make_double2((double)t[k], (double)v[k]);
+        el[k] = make_double2(__longlong_as_double(__double_as_longlong((double)t[k]) &
+                                                  0x7fffffffffffffffll),    // -0.0 -> +0.0
+                             (double)v[k]);
 }
 
-__global__ void rp_init_kernel(Header* h, int64_t* off0)
+__global__ void rp_init_kernel(Header* h, unsigned long long* stats, int64_t* off0)
 {
     h->err = kNoError;
     h->maxlen[0] = h->maxlen[1] = 0;
     h->tiles = 0;
+    stats[0] = stats[1] = 0;
     if (off0) *off0 = 0;
+}
+
+// First output PCF of every chunk of merge positions (one thread per chunk).
+__global__ void rp_part_kernel(const RpArgs a)
+{
+    if (a.hdr->err != kNoError) return;
+    const int64_t total = rp_item_off(a, a.P);
+    int64_t nch = (total + kRpChunk - 1) / kRpChunk;
+    if (nch > a.nchunk_cap) nch = a.nchunk_cap;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < nch;
+         c += (int64_t)gridDim.x * blockDim.x)
+        a.part[c] = rp_find(a, c * kRpChunk, 0, a.P - 1);
 }
 
 int rp_grid()
@@ -370,33 +437,41 @@ int rp_grid()
     static std::once_flag once;
     static int per_sm = 1;
     std::call_once(once, [] {
-        int b0 = 0, b1 = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b0, rp_kernel<false>, kRpThreads, 0);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, rp_kernel<true>, kRpThreads, 0);
-        per_sm = b0 < b1 ? b0 : b1;
-        if (per_sm < 1) per_sm = 1;
+        int b = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, rp_kernel, kRpThreads, 0);
+        per_sm = b < 1 ? 1 : b;
     });
     return per_sm * device_sm_count();
 }
 
-// One merge-and-compact pass: count, scan, write.
+// One merge-and-compact pass (a zeroed ticket/state array, then the kernel).
 cudaError_t run_rp(RpArgs a, int64_t item_bound, cudaStream_t s)
 {
     if (a.P == 0) return cudaSuccess;
     a.nchunk_cap = (item_bound + kRpChunk - 1) / kRpChunk;
     if (a.nchunk_cap < 1) a.nchunk_cap = 1;
+    // divisor of the output index: items per group (tree) or rows per B row
+    const int64_t d = a.mode == kModeTree ? a.c_out : (a.mode == kModeBcast ? a.m : 1);
+    int lg = 0;
+    while ((1ll << lg) < d) ++lg;
+    a.div_s = 31 + lg;
+    a.div_M = (unsigned long long)((((unsigned __int128)1 << a.div_s) + (unsigned __int128)(d - 1)) /
+                                   (unsigned __int128)d);
+    cudaError_t e = cudaMemsetAsync(a.state, 0, sizeof(unsigned long long) * (size_t)(a.nchunk_cap + 1), s);
+    if (e != cudaSuccess) return e;
+    int64_t pgrid = (a.nchunk_cap + 255) / 256;
+    if (pgrid > (int64_t)device_sm_count() * 8) pgrid = (int64_t)device_sm_count() * 8;
+    rp_part_kernel<<<(int)pgrid, 256, 0, s>>>(a);
     int64_t grid = rp_grid();
     if (grid > a.nchunk_cap) grid = a.nchunk_cap;
-    rp_kernel<false><<<(int)grid, kRpThreads, 0, s>>>(a);
-    rp_scan_kernel<<<1, 1024, 0, s>>>(a);
-    rp_kernel<true><<<(int)grid, kRpThreads, 0, s>>>(a);
+    rp_kernel<<<(int)grid, kRpThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 // Workspace carve-up shared by the size query and the calls.
 struct RpLayout {
-    size_t hdr, lens_a, skey_a, lens_b, skey_b, el0, el0b, offA, offB, elA, elB, mean_off, mean_el,
-        chunk, total;
+    size_t hdr, stats, lens_a, skey_a, lens_b, skey_b, el0, el0b, offA, offB, elA, elB, mean_off, mean_el,
+        chunk, part, total;
 };
 
 RpLayout rp_layout(int64_t n, int64_t nnz, int64_t nb, int64_t nnzb, int64_t groups,
@@ -406,6 +481,7 @@ RpLayout rp_layout(int64_t n, int64_t nnz, int64_t nb, int64_t nnzb, int64_t gro
     size_t o = 0;
     auto take = [&](size_t bytes) { const size_t at = o; o += align_up(bytes); return at; };
     L.hdr = take(sizeof(Header));
+    L.stats = take(2 * sizeof(unsigned long long));
     L.lens_a = take(sizeof(int32_t) * (size_t)n);
     L.skey_a = take(sizeof(uint32_t) * (size_t)n);
     L.lens_b = take(sizeof(int32_t) * (size_t)nb);
@@ -418,20 +494,24 @@ RpLayout rp_layout(int64_t n, int64_t nnz, int64_t nb, int64_t nnzb, int64_t gro
     L.elB = take(tree ? sizeof(double2) * (size_t)cap_items : 0);
     L.mean_off = take(with_mean ? sizeof(int64_t) * (size_t)(groups + 1) : 0);
     L.mean_el = take(with_mean ? sizeof(double2) * (size_t)nnz : 0);
-    L.chunk = take(sizeof(int64_t) * (size_t)((cap_items + kRpChunk - 1) / kRpChunk + 1));
+    L.chunk = take(sizeof(unsigned long long) * (size_t)((cap_items + kRpChunk - 1) / kRpChunk + 2));
+    L.part = take(sizeof(int64_t) * (size_t)((cap_items + kRpChunk - 1) / kRpChunk + 2));
     L.total = o;
     return L;
 }
 
 struct RpSet { const int64_t* off; const double2* el; };
 
+// Per-pass scratch: ticket + chunk states, chunk partition.
+struct RpScratch { unsigned long long* state; int64_t* part; };
+
 // Binary tree over `groups` groups of c items of `src`; the root of each
 // group goes to `final` (AoS or SoA per its fields).  ping/pong: level
 // buffers.  Returns the set holding the result when `final` is null.
 cudaError_t run_tree(int op, RpSet src, int64_t groups, int64_t c, int64_t cap_items,
                      int64_t* offA, double2* elA, int64_t* offB, double2* elB,
-                     const RpArgs* final, int64_t* chunk, Header* hdr, RpSet* result,
-                     cudaStream_t s)
+                     const RpArgs* final, RpScratch chunk, Header* hdr,
+                     unsigned long long* stats, RpSet* result, cudaStream_t s)
 {
     bool ping = true;
     while (c > 1) {
@@ -440,7 +520,7 @@ cudaError_t run_tree(int op, RpSet src, int64_t groups, int64_t c, int64_t cap_i
         a.a_off = src.off; a.a_el = src.el;
         a.mode = kModeTree; a.op = op;
         a.P = groups * c_out; a.c_in = c; a.c_out = c_out;
-        a.chunk = chunk; a.hdr = hdr;
+        a.state = chunk.state; a.part = chunk.part; a.hdr = hdr; a.stats = stats;
         if (c_out == 1 && final) {
             a.out_off = final->out_off; a.out_el = final->out_el;
             a.out_t = final->out_t; a.out_v = final->out_v; a.out_cap = final->out_cap;
@@ -549,9 +629,10 @@ extern "C" int pcf_reduce(const pcf_csr* x, int64_t group_size, int reduction, p
     int64_t* offA = (int64_t*)(w + L.offA); int64_t* offB = (int64_t*)(w + L.offB);
     double2* elA = (double2*)(w + L.elA); double2* elB = (double2*)(w + L.elB);
     double2* el0 = (double2*)(w + L.el0);
-    int64_t* chunk = (int64_t*)(w + L.chunk);
+    const RpScratch chunk{(unsigned long long*)(w + L.chunk), (int64_t*)(w + L.part)};
+    unsigned long long* stats = (unsigned long long*)(w + L.stats);
 
-    rp_init_kernel<<<1, 1, 0, stream>>>(hdr, out->offsets);
+    rp_init_kernel<<<1, 1, 0, stream>>>(hdr, stats, out->offsets);
     if (x->n == 0) return cudaGetLastError() == cudaSuccess ? PCF_OK : PCF_ECUDA;
     if (rp_validate_pack(x, hdr, (int32_t*)(w + L.lens_a), (uint32_t*)(w + L.skey_a), 0, el0,
                          stream) != cudaSuccess)
@@ -568,20 +649,20 @@ extern "C" int pcf_reduce(const pcf_csr* x, int64_t group_size, int reduction, p
         RpArgs a{};
         a.a_off = src.off; a.a_el = src.el; a.mode = kModeMap; a.op = op; a.s = sdiv; a.P = P;
         a.out_off = dst.out_off; a.out_el = dst.out_el; a.out_t = dst.out_t; a.out_v = dst.out_v;
-        a.out_cap = dst.out_cap; a.chunk = chunk; a.hdr = hdr;
+        a.out_cap = dst.out_cap; a.state = chunk.state; a.part = chunk.part; a.hdr = hdr; a.stats = stats;
         return run_rp(a, bound, stream);
     };
 
     if (reduction == PCF_RED_SUM || reduction == PCF_RED_MAX || reduction == PCF_RED_MIN) {
         const int op = reduction == PCF_RED_MAX ? kOpMax : reduction == PCF_RED_MIN ? kOpMin : kOpAdd;
         if (m == 1) e = map_to(in, groups, kOpCopy, 1.0, fin, x->nnz);
-        else e = run_tree(op, in, groups, m, cap, offA, elA, offB, elB, &fin, chunk, hdr, nullptr,
-                          stream);
+        else e = run_tree(op, in, groups, m, cap, offA, elA, offB, elB, &fin, chunk, hdr, stats,
+                          nullptr, stream);
     } else {
         // the sum tree, then the values divided by m
         RpSet sum;
-        e = run_tree(kOpAdd, in, groups, m, cap, offA, elA, offB, elB, nullptr, chunk, hdr, &sum,
-                     stream);
+        e = run_tree(kOpAdd, in, groups, m, cap, offA, elA, offB, elB, nullptr, chunk, hdr, stats,
+                     &sum, stream);
         if (e == cudaSuccess && reduction == PCF_RED_MEAN) {
             e = map_to(sum, groups, kOpDiv, (double)m, fin, x->nnz);
         } else if (e == cudaSuccess) {
@@ -595,13 +676,14 @@ extern "C" int pcf_reduce(const pcf_csr* x, int64_t group_size, int reduction, p
                 a.a_off = x->offsets; a.a_el = el0;
                 a.b_off = mean.out_off; a.b_el = mean.out_el;
                 a.mode = kModeBcast; a.op = kOpSqdiff; a.m = m; a.P = x->n;
-                a.out_off = offA; a.out_el = elA; a.out_cap = cap; a.chunk = chunk; a.hdr = hdr;
+                a.out_off = offA; a.out_el = elA; a.out_cap = cap; a.state = chunk.state; a.part = chunk.part; a.hdr = hdr;
+                a.stats = stats;
                 e = run_rp(a, cap, stream);
             }
             RpSet ss;
             if (e == cudaSuccess)
                 e = run_tree(kOpAdd, RpSet{offA, elA}, groups, m, cap, offB, elB, offA, elA,
-                             nullptr, chunk, hdr, &ss, stream);
+                             nullptr, chunk, hdr, stats, &ss, stream);
             if (e == cudaSuccess) e = map_to(ss, groups, kOpSqrtDiv, (double)(m - 1), fin, cap);
         }
     }
@@ -632,7 +714,8 @@ extern "C" int pcf_combine(const pcf_csr* a, const pcf_csr* b, int op, pcf_csr_o
     Header* hdr = (Header*)(w + L.hdr);
     double2* elA = (double2*)(w + L.el0);
     double2* elB = (double2*)(w + L.el0b);
-    rp_init_kernel<<<1, 1, 0, stream>>>(hdr, out->offsets);
+    unsigned long long* stats = (unsigned long long*)(w + L.stats);
+    rp_init_kernel<<<1, 1, 0, stream>>>(hdr, stats, out->offsets);
     if (a->n == 0) return cudaGetLastError() == cudaSuccess ? PCF_OK : PCF_ECUDA;
     if (rp_validate_pack(a, hdr, (int32_t*)(w + L.lens_a), (uint32_t*)(w + L.skey_a), 0, elA,
                          stream) != cudaSuccess)
@@ -644,6 +727,21 @@ extern "C" int pcf_combine(const pcf_csr* a, const pcf_csr* b, int op, pcf_csr_o
     r.a_off = a->offsets; r.a_el = elA; r.b_off = b->offsets; r.b_el = elB;
     r.mode = pair ? kModePair : kModeBcast; r.op = op; r.m = a->n; r.P = a->n;
     r.out_off = out->offsets; r.out_t = out->times; r.out_v = out->values;
-    r.out_cap = out->capacity; r.chunk = (int64_t*)(w + L.chunk); r.hdr = hdr;
+    r.out_cap = out->capacity; r.state = (unsigned long long*)(w + L.chunk); r.part = (int64_t*)(w + L.part); r.hdr = hdr; r.stats = stats;
     return run_rp(r, items, stream) == cudaSuccess ? PCF_OK : PCF_ECUDA;
+}
+
+extern "C" int pcf_reduce_counters(const void* workspace, cudaStream_t stream,
+                                   int64_t* positions, int64_t* rows)
+{
+    if (!workspace || ((uintptr_t)workspace % kAlign)) return PCF_ENOWS;
+    unsigned long long st[2] = {0, 0};
+    const char* w = (const char*)workspace;
+    if (cudaMemcpyAsync(st, w + align_up(sizeof(Header)), sizeof st, cudaMemcpyDeviceToHost,
+                        stream) != cudaSuccess)
+        return PCF_ECUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return PCF_ECUDA;
+    if (positions) *positions = (int64_t)st[0];
+    if (rows) *rows = (int64_t)st[1];
+    return PCF_OK;
 }

@@ -166,3 +166,32 @@ def test_reduce_errors(pcf):
     # the same workspace works again afterwards
     got = _host(pcf.pcf_reduce(x, 12, "sum", workspace=ws))
     _assert_same(got, oracle.reduce(s, 12, "sum"))
+
+
+def test_reduce_counters(pcf):
+    import torch
+    from paper_2404_07183_gb300 import api
+    s = synth.random_set(16, seed=220, min_len=1, max_len=40)
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    ws = torch.empty(api.pcf_reduce_workspace_size(x, 2, "sum"), dtype=torch.uint8, device="cuda")
+    res = pcf.pcf_reduce(x, 2, "sum", workspace=ws)
+    assert api.pcf_reduce_counters(ws) == (s.nnz, res.nnz)       # one level: every row once
+    res = pcf.pcf_reduce(x, 16, "sum", workspace=ws)
+    pos, rows = api.pcf_reduce_counters(ws)
+    assert pos >= s.nnz and rows >= res.nnz and pos - s.nnz == rows - res.nnz
+    a, b = synth.subset(s, range(8)), synth.subset(s, range(8, 16))
+    xa, xb = pcf.PcfTensors.from_numpy(a, "cuda"), pcf.PcfTensors.from_numpy(b, "cuda")
+    nbytes = 1 << 20
+    wsc = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    res = pcf.pcf_combine(xa, xb, "max", workspace=wsc)
+    assert api.pcf_reduce_counters(wsc) == (a.nnz + b.nnz, res.nnz)
+
+
+def test_negative_zero_t0(pcf):
+    s = synth.PcfSet([0, 2, 4, 5], np.array([-0.0, 1.0, 0.0, 2.0, -0.0]),
+                     np.array([1.0, 2.0, 3.0, 4.0, 5.0]))
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    for red, m in (("sum", 1), ("mean", 1), ("sum", 3), ("std", 3), ("min", 3)):
+        got = _host(pcf.pcf_reduce(x, m, red))
+        _assert_same(got, oracle.reduce(s, m, red))
+        assert not np.any(np.signbit(got[1]))
