@@ -490,11 +490,9 @@ int pcf_segment_integrals(const pcf_csr* x, int functional, double p, int apply_
     if (rc != PCF_OK) return rc;
     init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
     if (x->n == 0) return cudaGetLastError() == cudaSuccess ? PCF_OK : PCF_ECUDA;
-    if (launch_validate(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz,
-                        precision == PCF_PREC_F64, hdr, sv, stream) != cudaSuccess)
-        return PCF_ECUDA;
+    // the input check runs inside the segment kernels (same reasons and indices)
     if (launch_segments(x, functional, p, apply_root, a, b, precision, out, out_dtype == PCF_F64,
-                        hdr, stream) != cudaSuccess)
+                        hdr, sv.lens, stream) != cudaSuccess)
         return PCF_ECUDA;
     return PCF_OK;
 }

@@ -2,13 +2,17 @@
 //
 // out[i] = r( int_a^b h(f_i(t)) dt ) with h(v) = v (the integral of f) or
 // h(v) = |v|^p (r = x^(1/p) when requested: the L_p norm).  A PCF's segments
-// [t_k, t_{k+1}) (the last one reaching inf) are clipped to [a, b]; one warp
-// takes one PCF, lane l the segments l, l + 32, ...; the lane partial sums are
-// combined in float64 in a fixed lane order.  Arithmetic per segment: float64
+// [t_k, t_{k+1}) (the last one reaching inf) are clipped to [a, b].  A warp
+// takes a PCF of at most 1024 breakpoints (lane l: segments l, l + 32, ...),
+// a CTA takes a longer one (thread t: segments t, t + 256, ...), so the
+// longest PCFs no longer set the kernel time; partial sums are combined in
+// float64 in a fixed order.  The input is checked in the same pass, with the
+// reasons and indices of pcf_pairwise's check.  Arithmetic per segment: float64
 // (PCF_PREC_F64), or float32 on float32 data with Kahan's compensated
 // summation per segment (PCF_PREC_F32_COMP; float64 data are rounded to
 // float32 first).  A last segment reaching b = inf adds 0 when h = 0 and
 // h * inf otherwise.
+#include <cfloat>
 #include <cmath>
 
 #include "internal.cuh"
@@ -44,68 +48,222 @@ template <> struct SegAcc<float> {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
+constexpr int64_t kSegLong = 1024;   // longer PCFs get a whole CTA
+constexpr int kSegUnroll = 4;        // elements in flight per thread
+
+// One segment [t_k, t_{k+1}) of PCF i: validate element k as the input check
+// of pcf_pairwise does (same reasons, same indices), then add its term.
 template <typename Tin, typename T>
-__global__ void segment_kernel(const int64_t* __restrict__ offsets, const Tin* __restrict__ times,
-                               const Tin* __restrict__ values, int64_t n, int functional, double p_,
-                               int apply_root, double lo_, double hi_, void* out, int out_f64,
-                               const Header* hdr)
+struct SegCtx {
+    const Tin* times; const Tin* values;
+    int functional; T p, lo, hi;
+    Header* hdr;
+    bool range32;                  // float64 data walked in float32
+    bool clip;                     // [a, b] is not [0, inf)
+};
+
+// Breakpoint data of one segment, loaded before any check runs so that the
+// loads of a whole batch are in flight together.
+template <typename Tin>
+struct SegLoad { Tin tk, vk, tp, tn; };
+
+template <typename Tin, typename T>
+__device__ __forceinline__ SegLoad<Tin> seg_load(const SegCtx<Tin, T>& c, int64_t k, int64_t o0,
+                                                 int64_t o1)
 {
-    const T p = (T)p_, lo = (T)lo_, hi = (T)hi_;
-    if (hdr->err != kNoError) return;
+    SegLoad<Tin> d;
+    d.tk = __ldg(c.times + k);
+    d.vk = __ldg(c.values + k);
+    d.tp = k > o0 ? __ldg(c.times + k - 1) : Tin(0);
+    d.tn = k + 1 < o1 ? __ldg(c.times + k + 1) : Tin(INFINITY);
+    return d;
+}
+
+template <typename Tin, typename T>
+__device__ __forceinline__ void seg_element(const SegCtx<Tin, T>& c, const SegLoad<Tin>& d,
+                                            int64_t k, int64_t o0, SegAcc<T>& sa,
+                                            bool& diverges, double& tail_sign)
+{
+    if (!isfinite(d.tk)) { record_error(c.hdr, kErrTimeNaN, k); return; }
+    if (!isfinite(d.vk)) { record_error(c.hdr, kErrValueNaN, k); return; }
+    if (k == o0) {
+        if (d.tk != Tin(0)) record_error(c.hdr, kErrT0, k);
+    } else if (!(d.tk > d.tp)) {
+        record_error(c.hdr, kErrOrder, k);
+    }
+    if (c.range32 &&
+        (fabs((double)d.tk) > (double)FLT_MAX || fabs((double)d.vk) > (double)FLT_MAX))
+        record_error(c.hdr, kErrRange32, k);
+    const T v = (T)d.vk;
+    const T h = c.functional == PCF_FN_INTEGRAL ? v : seg_pow<T>(v, c.p);
+    T l = (T)d.tk, r = (T)d.tn;
+    if (c.clip) {
+        l = l > c.lo ? l : c.lo;
+        r = r < c.hi ? r : c.hi;
+        if (!(r > l)) return;
+    }
+    if (isinf(r)) {
+        if (h != T(0)) { diverges = true; tail_sign = h > T(0) ? 1.0 : -1.0; }
+        return;
+    }
+    sa.add(h, r - l);
+}
+
+// Segments k0, k0 + step, ... (kSegUnroll of them) of one PCF: loads first.
+template <typename Tin, typename T>
+__device__ __forceinline__ void seg_batch(const SegCtx<Tin, T>& c, int64_t k0, int64_t step,
+                                          int64_t o0, int64_t o1, SegAcc<T>& sa, bool& diverges,
+                                          double& tail_sign)
+{
+    SegLoad<Tin> d[kSegUnroll];
+#pragma unroll
+    for (int u = 0; u < kSegUnroll; ++u) {
+        const int64_t k = k0 + step * u;
+        if (k < o1) d[u] = seg_load(c, k, o0, o1);
+    }
+#pragma unroll
+    for (int u = 0; u < kSegUnroll; ++u) {
+        const int64_t k = k0 + step * u;
+        if (k < o1) seg_element(c, d[u], k, o0, sa, diverges, tail_sign);
+    }
+}
+
+// Offsets of PCF i as pcf_pairwise's input check reads them; false if bad.
+__device__ __forceinline__ bool seg_offsets(const int64_t* offsets, int64_t i, int64_t n,
+                                            int64_t nnz, Header* hdr, int64_t& o0, int64_t& o1)
+{
+    o0 = offsets[i]; o1 = offsets[i + 1];
+    bool bad = !(o0 >= 0 && o1 > o0 && o1 <= nnz && (o1 - o0) < (1ll << 31));
+    if (i == 0 && o0 != 0) bad = true;
+    if (i == n - 1 && o1 != nnz) bad = true;
+    if (bad) record_error(hdr, kErrOffsets, i);
+    return !bad;
+}
+
+__device__ __forceinline__ double seg_finish(double acc, bool div, double sign, int functional,
+                                             int apply_root, double p)
+{
+    double I = div ? sign * (double)INFINITY : acc;
+    if (apply_root && functional == PCF_FN_LP && p != 1.0)
+        I = (p == 2.0) ? sqrt(I) : pow(I, 1.0 / p);
+    return I;
+}
+
+__device__ __forceinline__ void seg_store(void* out, int out_f64, int64_t i, double I)
+{
+    if (out_f64) reinterpret_cast<double*>(out)[i] = I;
+    else reinterpret_cast<float*>(out)[i] = (float)I;
+}
+
+// One warp per PCF of at most kSegLong breakpoints, lane l taking the
+// segments l, l + 32, ... (kSegUnroll loads in flight); longer PCFs go on a
+// list for segment_long_kernel.  The input check runs on the same loads.
+template <typename Tin, typename T>
+__global__ void segment_kernel(const int64_t* __restrict__ offsets, SegCtx<Tin, T> c, int64_t n,
+                               int64_t nnz, int apply_root, double p_, void* out, int out_f64,
+                               int32_t* long_list)
+{
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t i = warp0; i < n; i += nwarps) {
-        const int64_t o0 = offsets[i], o1 = offsets[i + 1];
+        int64_t o0, o1;
+        if (!seg_offsets(offsets, i, n, nnz, c.hdr, o0, o1)) continue;
+        if (o1 - o0 > kSegLong) {
+            if (lane == 0) long_list[atomicAdd(&c.hdr->tiles, 1ull)] = (int32_t)i;
+            continue;
+        }
         SegAcc<T> sa;
         bool diverges = false;
         double tail_sign = 0.0;
-        for (int64_t k = o0 + lane; k < o1; k += 32) {
-            const T v = (T)values[k];
-            const T h = functional == PCF_FN_INTEGRAL ? v : seg_pow<T>(v, p);
-            const T t0 = (T)times[k];
-            const T t1 = (k + 1 < o1) ? (T)times[k + 1] : T(INFINITY);
-            const T l = t0 > lo ? t0 : lo;
-            const T r = t1 < hi ? t1 : hi;
-            if (!(r > l)) continue;
-            if (isinf(r)) {
-                if (h != T(0)) { diverges = true; tail_sign = h > T(0) ? 1.0 : -1.0; }
-                continue;
-            }
-            sa.add(h, r - l);
-        }
+        for (int64_t k0 = o0 + lane; k0 < o1; k0 += 32 * kSegUnroll)
+            seg_batch(c, k0, 32, o0, o1, sa, diverges, tail_sign);
         double acc = sa.value();
 #pragma unroll
         for (int s = 16; s > 0; s >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, s);
         const unsigned div = __ballot_sync(0xffffffffu, diverges);
         double sign = 0.0;
         if (div) sign = __shfl_sync(0xffffffffu, tail_sign, __ffs(div) - 1);
+        if (lane == 0) seg_store(out, out_f64, i, seg_finish(acc, div != 0, sign, c.functional,
+                                                             apply_root, p_));
+    }
+}
+
+// One CTA per listed long PCF; thread partial sums combined in a fixed
+// order (warp shuffles, then the 8 warp sums in order).
+template <typename Tin, typename T>
+__global__ void __launch_bounds__(256) segment_long_kernel(const int64_t* __restrict__ offsets,
+                                                           SegCtx<Tin, T> c, int apply_root,
+                                                           double p_, void* out, int out_f64,
+                                                           const int32_t* long_list)
+{
+    __shared__ double sAcc[8];
+    __shared__ int sDiv[8];
+    __shared__ double sSign[8];
+    // no early exit on a recorded error: these PCFs' elements still have to
+    // be checked so that the smallest offending index is the one reported
+    const long long count = (long long)c.hdr->tiles;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (long long w = blockIdx.x; w < count; w += gridDim.x) {
+        const int64_t i = long_list[w];
+        const int64_t o0 = offsets[i], o1 = offsets[i + 1];
+        SegAcc<T> sa;
+        bool diverges = false;
+        double tail_sign = 0.0;
+        for (int64_t k0 = o0 + threadIdx.x; k0 < o1; k0 += 256 * kSegUnroll)
+            seg_batch(c, k0, 256, o0, o1, sa, diverges, tail_sign);
+        double acc = sa.value();
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, s);
+        const unsigned div = __ballot_sync(0xffffffffu, diverges);
         if (lane == 0) {
-            double I = div ? sign * (double)INFINITY : acc;
-            if (apply_root && functional == PCF_FN_LP && p_ != 1.0)
-                I = (p_ == 2.0) ? sqrt(I) : pow(I, 1.0 / p_);
-            if (out_f64) reinterpret_cast<double*>(out)[i] = I;
-            else reinterpret_cast<float*>(out)[i] = (float)I;
+            sAcc[warp] = acc;
+            sDiv[warp] = div != 0;
+            sSign[warp] = 0.0;
         }
+        if (div) {                                  // (div is the same in every lane)
+            const double sg = __shfl_sync(0xffffffffu, tail_sign, __ffs(div) - 1);
+            if (lane == 0) sSign[warp] = sg;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0, sign = 0.0;
+            bool any = false;
+            for (int q = 0; q < 8; ++q) {
+                tot += sAcc[q];
+                if (sDiv[q] && !any) { any = true; sign = sSign[q]; }
+            }
+            seg_store(out, out_f64, i, seg_finish(tot, any, sign, c.functional, apply_root, p_));
+        }
+        __syncthreads();
     }
 }
 
 cudaError_t launch_segments(const pcf_csr* x, int functional, double p, int apply_root,
                             double lo, double hi, int precision, void* out, int out_f64,
-                            const Header* hdr, cudaStream_t s)
+                            Header* hdr, int32_t* long_list, cudaStream_t s)
 {
     if (x->n == 0) return cudaSuccess;
     int64_t blocks = (x->n * 32 + 255) / 256;
     const int64_t cap = (int64_t)device_sm_count() * 16;
     if (blocks > cap) blocks = cap;
+    const int long_blocks = device_sm_count() * 4;
     const bool f32 = precision != PCF_PREC_F64;
-#define PCF_SEG_LAUNCH(TIN, TW)                                                               \
-    segment_kernel<TIN, TW><<<(int)blocks, 256, 0, s>>>(x->offsets, (const TIN*)x->times,      \
-        (const TIN*)x->values, x->n, functional, p, apply_root, lo, hi, out, out_f64, hdr)
+#define PCF_SEG_LAUNCH(TIN, TW)                                                                   \
+    {                                                                                             \
+        SegCtx<TIN, TW> c{(const TIN*)x->times, (const TIN*)x->values, functional, (TW)p, (TW)lo, \
+                          (TW)hi, hdr, sizeof(TIN) == 8 && sizeof(TW) == 4,                       \
+                          lo > 0.0 || !std::isinf(hi)};                                           \
+        segment_kernel<TIN, TW><<<(int)blocks, 256, 0, s>>>(x->offsets, c, x->n, x->nnz,         \
+                                                              apply_root, p, out, out_f64,        \
+                                                              long_list);                         \
+        segment_long_kernel<TIN, TW><<<long_blocks, 256, 0, s>>>(x->offsets, c, apply_root, p,    \
+                                                                  out, out_f64, long_list);       \
+    }
     if (x->dtype == PCF_F64) {
-        if (f32) PCF_SEG_LAUNCH(double, float); else PCF_SEG_LAUNCH(double, double);
+        if (f32) PCF_SEG_LAUNCH(double, float) else PCF_SEG_LAUNCH(double, double)
     } else {
-        if (f32) PCF_SEG_LAUNCH(float, float); else PCF_SEG_LAUNCH(float, double);
+        if (f32) PCF_SEG_LAUNCH(float, float) else PCF_SEG_LAUNCH(float, double)
     }
 #undef PCF_SEG_LAUNCH
     return cudaGetLastError();

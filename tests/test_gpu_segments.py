@@ -89,3 +89,54 @@ def test_segments_reject_bad_arguments(pcf):
     bad = pcf.PcfTensors.from_numpy(synth.PcfSet(s.offsets, t, s.values), "cuda")
     with pytest.raises(pcf.PcfError):
         pcf.pcf_segment_integrals(bad, "integral")
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32c"])
+def test_segments_long_pcfs(pcf, prec):
+    """PCFs above 1024 breakpoints take the CTA-per-PCF path."""
+    a = synth.random_set(12, seed=105, min_len=1000, max_len=5000)
+    b = synth.random_set(60, seed=106, min_len=1, max_len=200)
+    s = synth.PcfSet(np.concatenate([b.offsets, b.offsets[-1] + a.offsets[1:]]),
+                     np.concatenate([b.times, a.times]), np.concatenate([b.values, a.values]))
+    s = synth.subset(s, np.random.default_rng(7).permutation(s.n))
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    for kind, p, root, ab in (("lp", 2.0, True, (0.0, np.inf)), ("integral", 1.0, False, (1.5, 40.0)),
+                              ("lp", 3.5, False, (0.0, 25.0))):
+        got = pcf.pcf_segment_integrals(x, kind, p, root, ab[0], ab[1], precision=prec).cpu().numpy()
+        for i in range(s.n):
+            t, v = s.pcf(i)
+            want = oracle.segment_integral(t, v, kind, p, ab[0], ab[1])
+            scale = oracle.segment_integral(t, v, "lp", 1.0 if kind == "integral" else p, ab[0], ab[1])
+            if root and kind == "lp":
+                want, scale = want ** (1.0 / p), scale ** (1.0 / p)
+            tol = 1e-12 if prec == "f64" else 1e-5
+            assert abs(got[i] - want) <= tol * scale + 1e-30, (i, s.lengths()[i], got[i], want)
+
+
+def test_segments_error_report_matches_pairwise_check(pcf):
+    """The check inside the segment kernels reports what pcf_pairwise's does:
+    here the smallest offending element lies in a long PCF."""
+    a = synth.random_set(3, seed=107, min_len=2000, max_len=3000)
+    b = synth.random_set(20, seed=108, min_len=5, max_len=50)
+    s = synth.PcfSet(np.concatenate([a.offsets, a.offsets[-1] + b.offsets[1:]]),
+                     np.concatenate([a.times, b.times]), np.concatenate([a.values, b.values]))
+    t, v = s.times.copy(), s.values.copy()
+    k_long = int(s.offsets[1]) + 1500            # inside PCF 1 (long)
+    k_short = int(s.offsets[10]) + 3             # inside a short PCF, larger index
+    v[k_long] = np.nan
+    t[k_short] = t[k_short - 1]
+    bad = pcf.PcfTensors.from_numpy(synth.PcfSet(s.offsets, t, v), "cuda")
+    with pytest.raises(pcf.PcfError) as e1:
+        pcf.pcf_segment_integrals(bad, "lp", 2.0)
+    with pytest.raises(pcf.PcfError) as e2:
+        pcf.pcf_pairwise(bad, ["l1"])
+    assert (e1.value.detail, e1.value.index) == (e2.value.detail, e2.value.index) == (5, k_long)
+    # a time that is not finite in a long PCF, offsets error elsewhere: offsets first
+    off = s.offsets.copy()
+    off[15] = off[14]
+    bad2 = pcf.PcfTensors.from_numpy(synth.PcfSet(off, t, s.values), "cuda")
+    with pytest.raises(pcf.PcfError) as e1:
+        pcf.pcf_segment_integrals(bad2, "integral", precision="f32c")
+    with pytest.raises(pcf.PcfError) as e2:
+        pcf.pcf_pairwise(bad2, ["l1"], precision="f32c")
+    assert (e1.value.detail, e1.value.index) == (e2.value.detail, e2.value.index) == (1, 14)
