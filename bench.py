@@ -333,14 +333,21 @@ def run_ours(args):
     h2d = sum(h.numel() * h.element_size() for h in host_in)
     d2h = sum(h.numel() * h.element_size() for h in host_out)
 
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    phases = []
+
     def e2e_step():
+        ev[0].record()
         for d, h in zip(dev_in, host_in):
             d.copy_(h, non_blocking=True)
+        ev[1].record()
         xd = P.PcfTensors(*dev_in)
         P.pcf_pairwise(xd, METRICS, precision=prec, out=outs, workspace=ws, check=False,
                        schedule=results[prec]["schedule"])
+        ev[2].record()
         for h, o in zip(host_out, outs):
             h.copy_(o, non_blocking=True)
+        ev[3].record()
 
     for _ in range(2):
         e2e_step()
@@ -349,7 +356,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         e2e_step()
-    torch.cuda.synchronize()
+        torch.cuda.synchronize()
+        phases.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     P.pcf_check(ws)
 
@@ -394,7 +402,9 @@ def run_ours(args):
         "gpu_launches": head["steps"] * (4 + 2),
         "e2e": {"value": world * pairs / e2e_s, "unit": "pair-integrals/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": e2e_s * 1e3},
+                "ms_per_step": e2e_s * 1e3,
+                "phases_ms": dict(zip(("h2d", "prepare_and_walk", "d2h"),
+                                      np.mean(np.array(phases), axis=0).round(3).tolist()))},
         "pipe_peaks": pp,
         "clocks": head["clocks"],
     }
