@@ -398,6 +398,19 @@ int pcf_combine(const pcf_csr* a, const pcf_csr* b, int op, pcf_csr_out* out,
 int pcf_reduce_counters(const void* workspace, cudaStream_t stream, int64_t* positions,
                         int64_t* rows);
 
+/*
+ * Self-test of the bounded device waits (no counterpart in the paper).  The
+ * reductions turn per-chunk row counts into output positions by decoupled
+ * look-back, in which a chunk waits for its predecessors' published counts;
+ * every such wait gives up after a bounded number of polls, records reason 9
+ * and lets its successors stop.  This call runs that wait for chunk 1 while
+ * chunk 0 never publishes, with at most `polls` polls (1 .. 2^20), so the wait
+ * runs out: pcf_check(workspace) then returns PCF_ETIMEOUT with reason 9.
+ * Workspace: at least 512 bytes, 256-byte aligned.
+ */
+int pcf_selftest_wait_timeout(int64_t polls, void* workspace, size_t workspace_bytes,
+                              cudaStream_t stream);
+
 /* Bytes of the fixed device scratch array behind pcf_pairwise_noalloc. */
 #define PCF_NOALLOC_SCRATCH_BYTES (16u << 20)
 

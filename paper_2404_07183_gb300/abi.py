@@ -30,13 +30,14 @@ ERR_DETAIL = {
     6: "time or value outside float32 range for a float32 walk",
     7: "more coincident float32 breakpoints than one window holds",
     8: "result or intermediate larger than the output capacity or the workspace",
+    9: "a bounded device wait gave up",
 }
 
 SYMBOLS = ("pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross", "pcf_pairwise_backward",
            "pcf_check", "pcf_status_string", "pcf_version", "pcf_pairwise_noalloc",
            "pcf_pairwise_ex", "pcf_cross_ex", "pcf_sort_order", "pcf_segment_integrals",
            "pcf_reduce_workspace_size", "pcf_reduce", "pcf_combine_workspace_size",
-           "pcf_combine", "pcf_reduce_counters")
+           "pcf_combine", "pcf_reduce_counters", "pcf_selftest_wait_timeout")
 PCF_RED_SUM, PCF_RED_MEAN, PCF_RED_MAX, PCF_RED_MIN, PCF_RED_STD = range(5)
 PCF_OP_ADD, PCF_OP_SUB, PCF_OP_MUL, PCF_OP_MAX, PCF_OP_MIN, PCF_OP_SQDIFF = range(6)
 PCF_FN_INTEGRAL, PCF_FN_LP = 0, 1
@@ -136,6 +137,8 @@ def load(build_if_missing: bool = False):
         lib.pcf_combine.argtypes = [CSR, CSR, I, OUT, P, SZ, P]
         lib.pcf_reduce_counters.restype = I
         lib.pcf_reduce_counters.argtypes = [P, P, ctypes.POINTER(I64), ctypes.POINTER(I64)]
+        lib.pcf_selftest_wait_timeout.restype = I
+        lib.pcf_selftest_wait_timeout.argtypes = [I64, P, SZ, P]
         lib.pcf_version.restype = ctypes.c_char_p
         lib.pcf_version.argtypes = []
         _lib = lib

@@ -214,7 +214,8 @@ constexpr long long kSpinPolls = 1ll << 20;          // per predecessor, ~0.1 s
 // its inclusive prefix, publish ours.  Chunks are taken in ticket order, so
 // every predecessor is running or done; each wait is bounded and an error
 // anywhere makes the waiters give up.  Returns -1 on giving up.
-__device__ long long rp_look_back(const RpArgs& a, long long c, int count)
+__device__ long long rp_look_back(const RpArgs& a, long long c, int count,
+                                  long long max_polls = kSpinPolls)
 {
     unsigned long long* st = a.state + 1;
     if (c == 0) {
@@ -229,7 +230,7 @@ __device__ long long rp_look_back(const RpArgs& a, long long c, int count)
         for (;;) {
             v = __ldcg(&st[pred]);                      // L2, coherent across SMs
             if (v >> 62) break;
-            if (++polls > kSpinPolls ||
+            if (++polls > max_polls ||
                 ((polls & 1023) == 0 && __ldcg(&a.hdr->err) != kNoError)) {
                 v = kStErr;
                 break;
@@ -409,6 +410,13 @@ __global__ void rp_pack_kernel(const T* __restrict__ t, const T* __restrict__ v,
         el[k] = make_double2(__longlong_as_double(__double_as_longlong((double)t[k]) &
                                                   0x7fffffffffffffffll),    // -0.0 -> +0.0
                              (double)v[k]);
+}
+
+// Self-test setup: no error recorded, ticket and chunk states zero.
+__global__ void init_selftest_kernel(Header* h, unsigned long long* state)
+{
+    h->err = kNoError;
+    state[0] = state[1] = state[2] = 0;
 }
 
 __global__ void rp_init_kernel(Header* h, unsigned long long* stats, int64_t* off0)
@@ -744,4 +752,35 @@ extern "C" int pcf_reduce_counters(const void* workspace, cudaStream_t stream,
     if (positions) *positions = (int64_t)st[0];
     if (rows) *rows = (int64_t)st[1];
     return PCF_OK;
+}
+
+namespace pcfgb {
+namespace {
+
+// Self-test of the bounded wait: chunk 1 looks back at chunk 0, which never
+// publishes (its state stays 0), so the wait must give up after `polls`
+// polls, record the wait error and publish the poison state.
+__global__ void rp_wait_selftest_kernel(RpArgs a, long long polls)
+{
+    if (threadIdx.x == 0) rp_look_back(a, 1, 1, polls);
+}
+
+}  // namespace
+}  // namespace pcfgb
+
+extern "C" int pcf_selftest_wait_timeout(int64_t polls, void* workspace, size_t workspace_bytes,
+                                         cudaStream_t stream)
+{
+    if (polls < 1 || polls > (1ll << 20)) return PCF_EINVAL;
+    const size_t need = align_up(sizeof(Header)) + align_up(3 * sizeof(unsigned long long));
+    if (!workspace || ((uintptr_t)workspace % kAlign) || workspace_bytes < need) return PCF_ENOWS;
+    char* w = (char*)workspace;
+    Header* hdr = (Header*)w;
+    unsigned long long* state = (unsigned long long*)(w + align_up(sizeof(Header)));
+    RpArgs a{};
+    a.hdr = hdr;
+    a.state = state;
+    init_selftest_kernel<<<1, 1, 0, stream>>>(hdr, state);
+    rp_wait_selftest_kernel<<<1, 32, 0, stream>>>(a, (long long)polls);
+    return cudaGetLastError() == cudaSuccess ? PCF_OK : PCF_ECUDA;
 }

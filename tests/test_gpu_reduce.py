@@ -195,3 +195,27 @@ def test_negative_zero_t0(pcf):
         got = _host(pcf.pcf_reduce(x, m, red))
         _assert_same(got, oracle.reduce(s, m, red))
         assert not np.any(np.signbit(got[1]))
+
+
+def test_bounded_wait_gives_up(pcf):
+    """The look-back wait of the reductions is bounded: with a predecessor
+    that never publishes, it records reason 9 and pcf_check reports
+    PCF_ETIMEOUT; the context stays usable."""
+    import time
+
+    import torch
+    from paper_2404_07183_gb300 import abi, api
+    lib = abi.load()
+    ws = torch.zeros(4096, dtype=torch.uint8, device="cuda")
+    t0 = time.perf_counter()
+    rc = lib.pcf_selftest_wait_timeout(1000, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                       api._stream_handle(None))
+    assert rc == abi.PCF_OK
+    with pytest.raises(pcf.PcfError) as e:
+        api.pcf_check(ws)
+    assert e.value.code == abi.PCF_ETIMEOUT and e.value.detail == 9
+    assert time.perf_counter() - t0 < 10.0
+    # the device is still fine afterwards
+    s = synth.random_set(8, seed=221, max_len=20)
+    got = _host(pcf.pcf_reduce(pcf.PcfTensors.from_numpy(s, "cuda"), 4, "mean"))
+    _assert_same(got, oracle.reduce(s, 4, "mean"))
