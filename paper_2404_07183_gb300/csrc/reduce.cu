@@ -209,43 +209,59 @@ constexpr unsigned long long kStErr = 3ull << 62;    // gave up: successors stop
 constexpr unsigned long long kStVal = (1ull << 62) - 1;
 constexpr long long kSpinPolls = 1ll << 20;          // per predecessor, ~0.1 s
 
-// Output position of chunk c's first row (decoupled look-back, one thread):
-// publish this chunk's count, add predecessors' counts until one publishes
-// its inclusive prefix, publish ours.  Chunks are taken in ticket order, so
-// every predecessor is running or done; each wait is bounded and an error
-// anywhere makes the waiters give up.  Returns -1 on giving up.
+// Output position of chunk c's first row (decoupled look-back by one warp,
+// every lane calls this): publish this chunk's count, then read the states
+// of 32 predecessors at a time, add the counts of those up to the nearest one
+// that has published its inclusive prefix, and publish ours.  Chunks are
+// taken in ticket order, so every predecessor is running or done; each wait
+// is bounded and an error anywhere makes the waiters give up (poison state).
+// The sums are of integers, so their order does not matter.  Returns -1 on
+// giving up.
 __device__ long long rp_look_back(const RpArgs& a, long long c, int count,
                                   long long max_polls = kSpinPolls)
 {
+    const int lane = threadIdx.x & 31;
     unsigned long long* st = a.state + 1;
     if (c == 0) {
-        atomicExch(&st[0], kStIncl | (unsigned long long)count);
+        if (lane == 0) atomicExch(&st[0], kStIncl | (unsigned long long)count);
         return 0;
     }
-    atomicExch(&st[c], kStAgg | (unsigned long long)count);
+    if (lane == 0) atomicExch(&st[c], kStAgg | (unsigned long long)count);
     long long excl = 0;
-    for (long long pred = c - 1;; --pred) {
-        unsigned long long v = 0;
+    bool failed = false;
+    for (long long base = c - 1;; base -= 32) {
+        const long long pred = base - lane;
+        // before chunk 0: an inclusive prefix of 0
+        unsigned long long v = pred >= 0 ? __ldcg(&st[pred]) : kStIncl;
         long long polls = 0;
-        for (;;) {
-            v = __ldcg(&st[pred]);                      // L2, coherent across SMs
-            if (v >> 62) break;
-            if (++polls > max_polls ||
-                ((polls & 1023) == 0 && __ldcg(&a.hdr->err) != kNoError)) {
-                v = kStErr;
+        while (__any_sync(0xffffffffu, (v >> 62) == 0)) {
+            ++polls;
+            const bool give_up = polls > max_polls ||
+                                 ((polls & 1023) == 0 && __ldcg(&a.hdr->err) != kNoError);
+            if (__any_sync(0xffffffffu, give_up)) {         // the same decision in every lane
+                failed = true;
                 break;
             }
             __nanosleep(64);
+            if ((v >> 62) == 0) v = __ldcg(&st[pred]);      // (pred >= 0 here)
         }
-        if ((v >> 62) == 3) {
+        if (failed || __any_sync(0xffffffffu, (v >> 62) == 3)) { failed = true; break; }
+        const unsigned incl = __ballot_sync(0xffffffffu, (v >> 62) == 2);
+        const int stop = incl ? __ffs(incl) - 1 : 31;          // nearest inclusive prefix
+        long long val = lane <= stop ? (long long)(v & kStVal) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+        excl += val;
+        if (incl) break;
+    }
+    if (failed) {
+        if (lane == 0) {
             atomicExch(&st[c], kStErr);
             record_error(a.hdr, kErrWait, c);
-            return -1;
         }
-        excl += (long long)(v & kStVal);
-        if ((v >> 62) == 2) break;
+        return -1;
     }
-    atomicExch(&st[c], kStIncl | (unsigned long long)(excl + count));
+    if (lane == 0) atomicExch(&st[c], kStIncl | (unsigned long long)(excl + count));
     return excl;
 }
 
@@ -362,7 +378,10 @@ __global__ void __launch_bounds__(kRpThreads) rp_kernel(const RpArgs a)
         const int excl = rp_block_scan(__popc(keep), block_total, warp_sums);
         sExcl[threadIdx.x] = excl;
         sKeep[threadIdx.x] = keep;
-        if (threadIdx.x == 0) sBase = rp_look_back(a, c, block_total);
+        if (threadIdx.x < 32) {
+            const long long b = rp_look_back(a, c, block_total);
+            if (threadIdx.x == 0) sBase = b;
+        }
         __syncthreads();
         const long long base = sBase;
         if (base < 0) break;
@@ -762,7 +781,7 @@ namespace {
 // polls, record the wait error and publish the poison state.
 __global__ void rp_wait_selftest_kernel(RpArgs a, long long polls)
 {
-    if (threadIdx.x == 0) rp_look_back(a, 1, 1, polls);
+    rp_look_back(a, 1, 1, polls);                     // one warp
 }
 
 }  // namespace
