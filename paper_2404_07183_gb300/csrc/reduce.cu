@@ -18,15 +18,16 @@
 // q keeps a breakpoint when it is the last position with its time (so every
 // time of the union appears once) and either t = 0 or the value
 // h(f(t), g(t)) differs from h(f(t-), g(t-)) -- exactly the rows Alg. 4
-// inserts, decided locally from the two lists.  Each CTA takes chunks of
-// 2048 consecutive positions (8 per thread); a thread finds its output PCF by
-// binary search and its place in the merge by a merge-path search along the
-// diagonal, then walks its 8 positions.  A count pass, a one-CTA exclusive
-// scan over the chunk counts and a write pass (which redoes the walk and
-// writes the kept rows at their global positions) give the compacted output
-// and its offsets with no host synchronization between levels: grids are
-// sized for the host-known upper bound on positions and read the actual
-// number from device memory.
+// inserts, decided locally from the two lists.  Persistent CTAs take chunks
+// of 2048 consecutive positions by ticket (8 per thread); a thread finds its
+// output PCF by binary search between the chunk's partition bounds and its
+// place in the merge by a merge-path search along the diagonal, then walks
+// its 8 positions.  The CTA's kept rows go to shared memory, their output
+// position comes from a decoupled look-back over the chunks before it, and
+// they are written in order.  No host synchronization between levels: grids
+// are sized for the host-known bound on positions and read the actual number
+// from device memory.  (Chunk shapes of 128 x 16 and 512 x 4 positions were
+// slower: longer serial walks, or one CTA per SM.)
 #include <cmath>
 #include <mutex>
 
@@ -161,7 +162,7 @@ __device__ __forceinline__ int64_t rp_find(const RpArgs& a, int64_t q, int64_t l
     return lo;
 }
 
-// Exclusive block scan of one int per thread (256 threads); also returns the
+// Exclusive block scan of one int per thread (kRpThreads threads); also returns the
 // block total.
 __device__ __forceinline__ int rp_block_scan(int x, int& total, int* warp_sums)
 {
