@@ -219,3 +219,18 @@ def test_bounded_wait_gives_up(pcf):
     s = synth.random_set(8, seed=221, max_len=20)
     got = _host(pcf.pcf_reduce(pcf.PcfTensors.from_numpy(s, "cuda"), 4, "mean"))
     _assert_same(got, oracle.reduce(s, 4, "mean"))
+
+
+def test_reduce_benchmark_size_sampled(pcf):
+    """The benchmarked reduction input (stable-rank N = 20,480): every group is
+    reduced on the GPU, a sample of groups by the oracle; identical bits."""
+    s = synth.stable_rank(n_pcfs=20480)
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    for red, m, groups in (("mean", 128, (0, 77, 159)), ("std", 16, (0, 555, 1279))):
+        r = pcf.pcf_reduce(x, m, red)
+        off, t, v = (r.offsets.cpu().numpy(), r.times.cpu().numpy(), r.values.cpu().numpy())
+        for g in groups:
+            sub = synth.subset(s, np.arange(g * m, (g + 1) * m))
+            wo, wt, wv = oracle.reduce(sub, m, red)
+            np.testing.assert_array_equal(t[off[g]:off[g + 1]], wt)
+            np.testing.assert_array_equal(v[off[g]:off[g + 1]], wv)

@@ -140,3 +140,21 @@ def test_segments_error_report_matches_pairwise_check(pcf):
     with pytest.raises(pcf.PcfError) as e2:
         pcf.pcf_pairwise(bad2, ["l1"], precision="f32c")
     assert (e1.value.detail, e1.value.index) == (e2.value.detail, e2.value.index) == (1, 14)
+
+
+@pytest.mark.parametrize("prec", ["f32c", "f64"])
+def test_segments_full_size_sampled(pcf, prec):
+    """The benchmarked workload (log-normal N = 100,000, lengths up to ~10^4),
+    checked on every 97th PCF against the oracle."""
+    s = synth.lognormal()
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    norm = pcf.pcf_segment_integrals(x, "lp", 2.0, True, precision=prec).cpu().numpy()
+    integ = pcf.pcf_segment_integrals(x, "integral", precision=prec).cpu().numpy()
+    tol = 1e-12 if prec == "f64" else 1e-5
+    for i in range(0, s.n, 97):
+        t, v = s.pcf(i)
+        want = oracle.segment_integral(t, v, "lp", 2.0) ** 0.5
+        assert abs(norm[i] - want) <= tol * want + 1e-30, (i, norm[i], want)
+        w = oracle.segment_integral(t, v, "integral")
+        scale = oracle.segment_integral(t, v, "lp", 1.0)
+        assert abs(integ[i] - w) <= tol * scale + 1e-30, (i, integ[i], w)
