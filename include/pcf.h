@@ -273,6 +273,20 @@ int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root
                           void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
 /*
+ * pcf_pairwise_backward for one GPU's share of a multi-GPU split (NULL
+ * schedule = the whole matrix).  Only schedule->shard_index/shard_count are
+ * used (kernel must be PCF_SCHED_AUTO or PCF_SCHED_TILE_1024): the call walks
+ * the 32 x 32 upper-triangle tiles t (in the order of the forward tile walk)
+ * with t % shard_count == shard_index and writes the gradient of the pairs
+ * of those tiles (zeros elsewhere).  The shards' outputs sum to the whole
+ * gradient (one sum all-reduce, best in float64).
+ */
+int pcf_pairwise_backward_ex(const pcf_csr* x, int metric, double p, int apply_root,
+                             const void* fwd_out, const void* grad_out, int grad_dtype,
+                             void* grad_values, void* grad_times, const pcf_schedule* schedule,
+                             void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/*
  * Single-PCF integrals by segment iteration (Sec. 3.2, Alg. 3):
  *   out[i] = r( int_a^b h(f_i(t)) dt ),  0 <= a < b <= inf,
  * h per pcf_functional; r(x) = x^(1/p) for PCF_FN_LP with apply_root, else x.

@@ -37,7 +37,8 @@ SYMBOLS = ("pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross", "pc
            "pcf_check", "pcf_status_string", "pcf_version", "pcf_pairwise_noalloc",
            "pcf_pairwise_ex", "pcf_cross_ex", "pcf_sort_order", "pcf_segment_integrals",
            "pcf_reduce_workspace_size", "pcf_reduce", "pcf_combine_workspace_size",
-           "pcf_combine", "pcf_reduce_counters", "pcf_selftest_wait_timeout")
+           "pcf_combine", "pcf_reduce_counters", "pcf_selftest_wait_timeout",
+           "pcf_pairwise_backward_ex")
 PCF_RED_SUM, PCF_RED_MEAN, PCF_RED_MAX, PCF_RED_MIN, PCF_RED_STD = range(5)
 PCF_OP_ADD, PCF_OP_SUB, PCF_OP_MUL, PCF_OP_MAX, PCF_OP_MIN, PCF_OP_SQDIFF = range(6)
 PCF_FN_INTEGRAL, PCF_FN_LP = 0, 1
@@ -120,6 +121,8 @@ def load(build_if_missing: bool = False):
         lib.pcf_cross.argtypes = [CSR, CSR, I64, I64, INT, I, I, I64, I, I, P, SZ, P]
         lib.pcf_pairwise_backward.restype = I
         lib.pcf_pairwise_backward.argtypes = [CSR, I, D, I, P, P, I, P, P, P, SZ, P]
+        lib.pcf_pairwise_backward_ex.restype = I
+        lib.pcf_pairwise_backward_ex.argtypes = [CSR, I, D, I, P, P, I, P, P, SCH, P, SZ, P]
         lib.pcf_check.restype = I
         lib.pcf_check.argtypes = [P, P, ctypes.POINTER(I), ctypes.POINTER(I64)]
         lib.pcf_status_string.restype = ctypes.c_char_p

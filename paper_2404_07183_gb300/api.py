@@ -313,8 +313,10 @@ def pcf_cross(a: PcfTensors, b: PcfTensors, row_begin=0, row_end=None, metrics=(
 
 
 def pcf_pairwise_backward(x: PcfTensors, metric, grad_out: torch.Tensor, fwd_out=None,
-                          workspace=None, stream=None, check=True):
-    """(grad_values, grad_times) of sum(grad_out * F) for the FULL matrix F."""
+                          workspace=None, stream=None, check=True, shard=None):
+    """(grad_values, grad_times) of sum(grad_out * F) for the FULL matrix F.
+    ``shard=(rank, world)``: this GPU's share (tiles t with t % world == rank);
+    the shares sum to the whole gradient."""
     lib = abi.load()
     code, p, root = parse_metric(metric)
     dev = x.times.device
@@ -330,12 +332,13 @@ def pcf_pairwise_backward(x: PcfTensors, metric, grad_out: torch.Tensor, fwd_out
         if f.dtype != g.dtype:
             raise ValueError("fwd_out and grad_out must share a dtype")
     cx = x.csr()
-    rc = lib.pcf_pairwise_backward(
+    rc = lib.pcf_pairwise_backward_ex(
         ctypes.byref(cx), code, p, int(root),
         ctypes.c_void_p(f.data_ptr()) if f is not None else None,
         ctypes.c_void_p(g.data_ptr()), abi.PCF_F64 if g.dtype == torch.float64 else abi.PCF_F32,
         ctypes.c_void_p(gv.data_ptr()), ctypes.c_void_p(gt.data_ptr()),
-        ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream))
+        _schedule(None, shard), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+        _stream_handle(stream))
     if rc != abi.PCF_OK:
         raise PcfError(rc, "pcf_pairwise_backward")
     if check:

@@ -425,7 +425,32 @@ int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root
                           void* grad_values, void* grad_times, void* workspace,
                           size_t workspace_bytes, cudaStream_t stream)
 {
+    return pcf_pairwise_backward_ex(x, metric, p, apply_root, fwd_out, grad_out, grad_dtype,
+                                    grad_values, grad_times, nullptr, workspace, workspace_bytes,
+                                    stream);
+}
+
+int pcf_pairwise_backward_ex(const pcf_csr* x, int metric, double p, int apply_root,
+                             const void* fwd_out, const void* grad_out, int grad_dtype,
+                             void* grad_values, void* grad_times, const pcf_schedule* schedule,
+                             void* workspace, size_t workspace_bytes, cudaStream_t stream)
+{
     if (!csr_ok(x)) return PCF_EINVAL;
+    int64_t shard_index = 0, shard_count = 1;
+    if (schedule) {
+        for (int k = 0; k < 4; ++k)
+            if (schedule->reserved[k]) return PCF_EINVAL;
+        if (schedule->kernel != PCF_SCHED_AUTO && schedule->kernel != PCF_SCHED_TILE_1024)
+            return PCF_EINVAL;
+        if (schedule->shard_count > 1) {
+            if (schedule->shard_index < 0 || schedule->shard_index >= schedule->shard_count)
+                return PCF_EINVAL;
+            shard_index = schedule->shard_index;
+            shard_count = schedule->shard_count;
+        } else if (schedule->shard_count < 0 || schedule->shard_index != 0) {
+            return PCF_EINVAL;
+        }
+    }
     if (metric < PCF_L1 || metric > PCF_GRAM) return PCF_EINVAL;
     if (metric == PCF_LP && !(p >= 1.0 && std::isfinite(p))) return PCF_EINVAL;
     if (grad_dtype != PCF_F32 && grad_dtype != PCF_F64) return PCF_EINVAL;
@@ -466,6 +491,7 @@ int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root
     ba.G = grad_out; ba.F = fwd_out; ba.g_f64 = grad_dtype == PCF_F64;
     ba.metric = metric; ba.p = p; ba.apply_root = apply_root ? 1 : 0;
     ba.gv = gv; ba.gt = gt; ba.hdr = hdr;
+    ba.shard_index = shard_index; ba.shard_count = shard_count;
     if (launch_backward(ba, stream) != cudaSuccess) return PCF_ECUDA;
     if (launch_scatter_grad(sv, x->offsets, gv, gt, grad_values, grad_times,
                             x->dtype == PCF_F64, hdr, stream) != cudaSuccess)

@@ -9,7 +9,9 @@
 // with g(t_k-) the value of g just before t_k (left derivative where both PCFs
 // share the breakpoint).  The walk is recomputed per pair in float64 with the
 // simultaneous advance of Alg. 1, which hands both sides the pre-advance
-// values at a shared breakpoint.  Each unordered pair i < j is walked once
+// values at a shared breakpoint.  A multi-GPU split walks only the tiles t
+// with t % shard_count == shard_index; the partial gradients of all shards
+// sum to the whole (one all-reduce).  Each unordered pair i < j is walked once
 // with weight (G_ij + G_ji) r'(I_ij); the Gram diagonal F_ii = int f_i^2 is
 // differentiated by segment iteration (Sec. 3.2, Alg. 3).  Contributions are
 // summed with float64 atomics into packed-order accumulators, then scattered
@@ -68,7 +70,9 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BackArgs a)
     if (a.hdr->err != kNoError) return;
     const int r = threadIdx.x >> 5, c = threadIdx.x & 31;
     const int64_t NB = a.nb;
-    for (int64_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    for (int64_t u = blockIdx.x;; u += gridDim.x) {
+        const int64_t t = a.shard_index + u * a.shard_count;   // this shard's tiles
+        if (t >= a.ntiles) break;
         // upper-triangle tile order (row block bi <= column block bj)
         const double q = 2.0 * (double)NB + 1.0;
         const double disc = q * q - 8.0 * (double)t;
@@ -182,8 +186,8 @@ __global__ void scatter_grad_kernel(const int64_t* __restrict__ offsets, const i
 
 cudaError_t launch_backward(const BackArgs& a, cudaStream_t s)
 {
-    if (a.ntiles == 0) return cudaSuccess;
-    int64_t grid = a.ntiles;
+    if (a.ntiles <= a.shard_index) return cudaSuccess;
+    int64_t grid = (a.ntiles - a.shard_index + a.shard_count - 1) / a.shard_count;
     const int64_t cap = (int64_t)device_sm_count() * 8;
     if (grid > cap) grid = cap;
     switch (a.metric) {

@@ -150,6 +150,7 @@ struct BackArgs {
     int metric; double p; int apply_root;
     double* gv; double* gt;      // packed-order accumulators
     Header* hdr;
+    int64_t shard_index, shard_count;   // this call walks tiles t with t % count == index
 };
 cudaError_t launch_backward(const BackArgs& a, cudaStream_t s);
 cudaError_t launch_scatter_grad(const SetView& sv, const int64_t* offsets, const double* gv,

@@ -114,3 +114,26 @@ def test_gradient_workload_full_size_sampled(pcf):
         a, b = int(s.offsets[i]), int(s.offsets[i + 1])
         assert _rel(gv[a:b], acc_v) <= 1e-10
         assert _rel(gt[a:b], acc_t) <= 1e-10
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_backward_shards_sum_to_the_gradient(pcf, world):
+    """One matrix's gradient split over `world` GPUs (run here one after the
+    other): the shards' partial gradients sum to the unsharded one."""
+    import torch
+    s = synth.random_set(150, seed=131, min_len=2, max_len=60)
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    G = torch.randn(s.n, s.n, device="cuda", dtype=torch.float64)
+    for spec in (("l2", False), "gram", ("lp", 2.5, True)):
+        fwd = None
+        if spec == ("lp", 2.5, True):
+            fwd = pcf.pcf_pairwise(x, [spec], precision="f64", out_dtype=torch.float64)[0]
+        gv, gt = pcf.pcf_pairwise_backward(x, spec, G, fwd_out=fwd)
+        sv = torch.zeros_like(gv)
+        st = torch.zeros_like(gt)
+        for r in range(world):
+            pv, pt = pcf.pcf_pairwise_backward(x, spec, G, fwd_out=fwd, shard=(r, world))
+            sv += pv
+            st += pt
+        assert _rel(sv.cpu().numpy(), gv.cpu().numpy()) < 1e-12, spec
+        assert _rel(st.cpu().numpy(), gt.cpu().numpy()) < 1e-12, spec

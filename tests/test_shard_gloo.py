@@ -44,6 +44,27 @@ def _worker(rank, world, port, mode, q):
         s = synth.random_set(70, seed=91, min_len=1, max_len=40)
         n = s.n
         owned = shard.shard_pairs(s.lengths(), rank, world)
+        if mode == "backward":
+            # this rank's share of d(sum G * F)/d(values, times): G restricted to
+            # the pairs its tiles own, then one sum all-reduce of the gradients
+            G = np.random.default_rng(5).standard_normal((n, n))
+            Gr = np.zeros_like(G)
+            for i, j in owned:
+                Gr[i, j] = G[i, j]
+                Gr[j, i] = G[j, i]
+            gv, gt = oracle.backward(s, Gr, metric="l2", p=2.0)
+            tv, tt = torch.from_numpy(gv), torch.from_numpy(gt)
+            dist.all_reduce(tv)
+            dist.all_reduce(tt)
+            if rank == 0:
+                wv, wt = oracle.backward(s, G, metric="l2", p=2.0)
+                ev = float(np.max(np.abs(tv.numpy() - wv)) / np.max(np.abs(wv)))
+                et = float(np.max(np.abs(tt.numpy() - wt)) / np.max(np.abs(wt)))
+                q.put((rank, f"grad-ok={ev < 1e-12 and et < 1e-12}"))
+            else:
+                q.put((rank, "done"))
+            dist.destroy_process_group()
+            return
         part = np.zeros((n, n))
         for i, j in owned:
             v = oracle.integral(*s.pcf(i), *s.pcf(j), "l1")
@@ -104,6 +125,11 @@ def test_two_ranks_cover_every_pair_once():
 def test_three_ranks():
     out = _run(3, "ok")
     assert out[0] == "ok=True once=True", out
+
+
+def test_backward_shards_all_reduce_to_the_gradient():
+    out = _run(3, "backward")
+    assert out[0] == "grad-ok=True", out
 
 
 def test_dead_rank_is_detected_by_the_survivor():
