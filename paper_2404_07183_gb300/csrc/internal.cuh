@@ -159,7 +159,7 @@ cudaError_t launch_scatter_grad(const SetView& sv, const int64_t* offsets, const
 
 cudaError_t launch_segments(const pcf_csr* x, int functional, double p, int apply_root,
                             double lo, double hi, int precision, void* out, int out_f64,
-                            Header* hdr, int32_t* long_list, cudaStream_t s);
+                            Header* hdr, void* scratch, cudaStream_t s);
 cudaError_t launch_validate(const int64_t* offsets, const void* times, const void* values,
                             int in_dtype, int64_t n, int64_t nnz_total, int walk_f64,
                             Header* hdr, SetView& sv, cudaStream_t s);

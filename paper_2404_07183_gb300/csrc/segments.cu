@@ -2,16 +2,31 @@
 //
 // out[i] = r( int_a^b h(f_i(t)) dt ) with h(v) = v (the integral of f) or
 // h(v) = |v|^p (r = x^(1/p) when requested: the L_p norm).  A PCF's segments
-// [t_k, t_{k+1}) (the last one reaching inf) are clipped to [a, b].  A warp
-// takes a PCF of at most 1024 breakpoints (lane l: segments l, l + 32, ...),
-// a CTA takes a longer one (thread t: segments t, t + 256, ...), so the
-// longest PCFs no longer set the kernel time; partial sums are combined in
-// float64 in a fixed order.  The input is checked in the same pass, with the
-// reasons and indices of pcf_pairwise's check.  Arithmetic per segment: float64
-// (PCF_PREC_F64), or float32 on float32 data with Kahan's compensated
-// summation per segment (PCF_PREC_F32_COMP; float64 data are rounded to
-// float32 first).  A last segment reaching b = inf adds 0 when h = 0 and
-// h * inf otherwise.
+// [t_k, t_{k+1}) (the last one reaching inf) are clipped to [a, b].  A last
+// segment reaching b = inf adds 0 when h = 0 and h * inf otherwise.
+// Arithmetic per segment: float64 (PCF_PREC_F64), or float32 with Kahan's
+// compensated summation per segment (PCF_PREC_F32_COMP; float64 data are
+// rounded to float32 first).
+//
+// GPU design: one flat, element-balanced pass over the breakpoint arrays.
+//  * seg_table_kernel (thread per PCF) checks the offsets with the reasons and
+//    indices of pcf_pairwise's check and writes table[c] = number of PCFs that
+//    start before element c * kSegChunk, for every chunk c.
+//  * segment_kernel: CTA c owns the PCFs that start in chunk c (table[c] ..
+//    table[c + 1] - 1) and integrates every segment of them, so the last one
+//    may run past the chunk's end; no two CTAs share a PCF and no CTA waits
+//    for another.  The owned elements are streamed in rounds of 2048 (256
+//    threads x 8 consecutive elements, 16-byte vector loads when the arrays
+//    are aligned).  Each thread integrates its elements in order and splits
+//    them into runs at PCF boundaries; a CTA-wide segmented scan of the runs'
+//    partial sums (warp shuffles, then one warp over the eight warp totals)
+//    carries a PCF's partial sum across threads and rounds, in a fixed order;
+//    the thread holding a PCF's last element finishes it (tail rule, root)
+//    and stores it.
+//  * The input check of pcf_pairwise runs on the same loads (same reasons,
+//    same indices; an offsets error found by the table pass stops the
+//    integration, element errors leave every element checked so the smallest
+//    index wins).
 #include <cfloat>
 #include <cmath>
 
@@ -32,15 +47,51 @@ __device__ __forceinline__ T seg_h(T v, T p)
     else return pow(fabs(v), p);
 }
 
-// Per-lane accumulator: float64 fma, or float32 Kahan (sum - compensation).
-template <typename T> struct SegAcc;
-template <> struct SegAcc<double> {
-    double s = 0.0;
+constexpr int kSegThreads = 256;
+// consecutive elements per thread: 16 float (4 x 16-byte loads per array) or 8 double
+template <typename Tin> __host__ __device__ constexpr int seg_items() { return sizeof(Tin) == 4 ? 16 : 8; }
+constexpr int64_t kSegChunk = 8192;    // elements whose PCFs a CTA owns (2 or 4 rounds)
+constexpr int kSegBatch = 512;         // PCF offsets staged at a time
+
+// Partial sum of a run of segments with the head flag of the segmented scan:
+// flag = a PCF starts inside the run, so nothing before it is added.
+// float64: plain sum.  float32: Kahan pair, value = s - c.
+template <typename T> struct SegSum;
+template <> struct SegSum<double> {
+    double s;
+    int flag;
+    __device__ __forceinline__ void zero() { s = 0.0; }
     __device__ __forceinline__ void add(double h, double len) { s = fma(h, len, s); }
     __device__ __forceinline__ double value() const { return s; }
+    // sum of an earlier run a and a later run b
+    __device__ __forceinline__ static SegSum join(const SegSum& a, const SegSum& b)
+    {
+        SegSum r;
+        r.flag = a.flag | b.flag;
+        r.s = b.flag ? b.s : a.s + b.s;
+        return r;
+    }
+    __device__ __forceinline__ SegSum shfl_up(int o) const
+    {
+        SegSum r;
+        r.s = __shfl_up_sync(0xffffffffu, s, o);
+        r.flag = __shfl_up_sync(0xffffffffu, flag, o);
+        return r;
+    }
+    __device__ __forceinline__ SegSum shfl_idx(int l) const
+    {
+        SegSum r;
+        r.s = __shfl_sync(0xffffffffu, s, l);
+        r.flag = __shfl_sync(0xffffffffu, flag, l);
+        return r;
+    }
 };
-template <> struct SegAcc<float> {
-    float s = 0.f, c = 0.f;
+template <> struct SegSum<float> {
+    float s, c;
+    int flag;
+    __device__ __forceinline__ void zero() { s = 0.f; c = 0.f; }
+    // Kahan: the term h * len is formed inside the FMA that removes the
+    // running compensation, then t = s + y, c = (t - s) - y, s = t.
     __device__ __forceinline__ void add(float h, float len)
     {
         const float y = __fmaf_rn(h, len, -c);
@@ -49,136 +100,82 @@ template <> struct SegAcc<float> {
         s = t;
     }
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+    // (s_a - c_a) + (s_b - c_b): Knuth's TwoSum of the sums (exact: t + e),
+    // the rounding error e joining the compensations.
+    __device__ __forceinline__ static SegSum join(const SegSum& a, const SegSum& b)
+    {
+        SegSum r;
+        r.flag = a.flag | b.flag;
+        if (b.flag) { r.s = b.s; r.c = b.c; return r; }
+        const float t = __fadd_rn(a.s, b.s);
+        const float bp = __fsub_rn(t, a.s);
+        const float e = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(b.s, bp));
+        r.s = t;
+        r.c = __fsub_rn(__fadd_rn(a.c, b.c), e);
+        return r;
+    }
+    __device__ __forceinline__ SegSum shfl_up(int o) const
+    {
+        SegSum r;
+        r.s = __shfl_up_sync(0xffffffffu, s, o);
+        r.c = __shfl_up_sync(0xffffffffu, c, o);
+        r.flag = __shfl_up_sync(0xffffffffu, flag, o);
+        return r;
+    }
+    __device__ __forceinline__ SegSum shfl_idx(int l) const
+    {
+        SegSum r;
+        r.s = __shfl_sync(0xffffffffu, s, l);
+        r.c = __shfl_sync(0xffffffffu, c, l);
+        r.flag = __shfl_sync(0xffffffffu, flag, l);
+        return r;
+    }
 };
 
-// Sum of the 32 lanes' accumulators into lane 0's (fixed tree order).
-// float64: plain float64 additions.  float32: the lanes' (sum, compensation)
-// pairs are merged with Knuth's error-free TwoSum of the sums, the rounding
-// error joining the compensation, so every step stays on the FP32 pipe (the
-// FP64 pipe of GB300 is narrow) and the compensated error bound holds.
-__device__ __forceinline__ void seg_warp_reduce(SegAcc<double>& a)
+template <typename T>
+__device__ __forceinline__ SegSum<T> seg_identity()
 {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a.s += __shfl_down_sync(0xffffffffu, a.s, o);
-}
-__device__ __forceinline__ void seg_warp_reduce(SegAcc<float>& a)
-{
-    float s = a.s, c = a.c;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const float s2 = __shfl_down_sync(0xffffffffu, s, o);
-        const float c2 = __shfl_down_sync(0xffffffffu, c, o);
-        const float t = __fadd_rn(s, s2);                      // TwoSum(s, s2): t + e exactly
-        const float bp = __fsub_rn(t, s);
-        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(s2, bp));
-        s = t;
-        c = __fsub_rn(__fadd_rn(c, c2), e);                    // value = s - c
-    }
-    a.s = s; a.c = c;
-}
-// Lane 0's accumulator in every lane.
-__device__ __forceinline__ SegAcc<double> seg_lane0(const SegAcc<double>& a)
-{
-    SegAcc<double> r; r.s = __shfl_sync(0xffffffffu, a.s, 0); return r;
-}
-__device__ __forceinline__ SegAcc<float> seg_lane0(const SegAcc<float>& a)
-{
-    SegAcc<float> r;
-    r.s = __shfl_sync(0xffffffffu, a.s, 0);
-    r.c = __shfl_sync(0xffffffffu, a.c, 0);
+    SegSum<T> r;
+    r.zero();
+    r.flag = 0;
     return r;
 }
 
-constexpr int64_t kSegLong = 1024;   // longer PCFs get a whole CTA
-constexpr int kSegUnroll = 4;        // elements in flight per thread
-
-// One segment [t_k, t_{k+1}) of PCF i: validate element k as the input check
-// of pcf_pairwise does (same reasons, same indices), then add its term.
 template <typename Tin, typename T>
-struct SegCtx {
-    const Tin* times; const Tin* values;
-    int functional; T p, lo, hi;
+struct SegArgs {
+    const int64_t* offsets;
+    const Tin* times;
+    const Tin* values;
+    int64_t n, nnz;
+    const int64_t* table;          // [nchunks + 1]
+    int functional;
+    int apply_root;
+    double p;                      // exponent of the functional (float64)
+    T pw, lo, hi;                  // exponent and bounds in the arithmetic type
+    void* out;
+    int out_f64;
     Header* hdr;
-    bool range32;                  // float64 data walked in float32
-    bool clip;                     // [a, b] is not [0, inf)
 };
 
-// Breakpoint data of one segment, loaded before any check runs so that the
-// loads of a whole batch are in flight together.
-template <typename Tin>
-struct SegLoad { Tin tk, vk, tp, tn; };
-
-template <typename Tin, typename T>
-__device__ __forceinline__ SegLoad<Tin> seg_load(const SegCtx<Tin, T>& c, int64_t k, int64_t o0,
-                                                 int64_t o1)
+// Offsets check per PCF (the reasons and indices of pcf_pairwise's check)
+// and the chunk table: table[c] = #PCFs starting before element c * chunk.
+__global__ void seg_table_kernel(const int64_t* __restrict__ offsets, int64_t n, int64_t nnz,
+                                 int64_t nchunks, int64_t* __restrict__ table, Header* hdr)
 {
-    SegLoad<Tin> d;
-    d.tk = __ldg(c.times + k);
-    d.vk = __ldg(c.values + k);
-    d.tp = k > o0 ? __ldg(c.times + k - 1) : Tin(0);
-    d.tn = k + 1 < o1 ? __ldg(c.times + k + 1) : Tin(INFINITY);
-    return d;
-}
-
-template <int FN, typename Tin, typename T>
-__device__ __forceinline__ void seg_element(const SegCtx<Tin, T>& c, const SegLoad<Tin>& d,
-                                            int64_t k, int64_t o0, SegAcc<T>& sa,
-                                            bool& diverges, double& tail_sign)
-{
-    if (!isfinite(d.tk)) { record_error(c.hdr, kErrTimeNaN, k); return; }
-    if (!isfinite(d.vk)) { record_error(c.hdr, kErrValueNaN, k); return; }
-    if (k == o0) {
-        if (d.tk != Tin(0)) record_error(c.hdr, kErrT0, k);
-    } else if (!(d.tk > d.tp)) {
-        record_error(c.hdr, kErrOrder, k);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i0 == 0) { table[0] = 0; table[nchunks] = n; }
+    for (int64_t i = i0; i < n; i += stride) {
+        const int64_t o0 = offsets[i], o1 = offsets[i + 1];
+        bool bad = !(o0 >= 0 && o1 > o0 && o1 <= nnz && (o1 - o0) < (1ll << 31));
+        if (i == 0 && o0 != 0) bad = true;
+        if (i == n - 1 && o1 != nnz) bad = true;
+        if (bad) { record_error(hdr, kErrOffsets, i); continue; }
+        // chunks c with o0 < c * chunk <= o1 see PCFs 0..i starting before them
+        int64_t c1 = o1 / kSegChunk;
+        if (c1 > nchunks) c1 = nchunks;
+        for (int64_t c = o0 / kSegChunk + 1; c <= c1; ++c) table[c] = i + 1;
     }
-    if (c.range32 &&
-        (fabs((double)d.tk) > (double)FLT_MAX || fabs((double)d.vk) > (double)FLT_MAX))
-        record_error(c.hdr, kErrRange32, k);
-    const T v = (T)d.vk;
-    const T h = seg_h<FN, T>(v, c.p);
-    T l = (T)d.tk, r = (T)d.tn;
-    if (c.clip) {
-        l = l > c.lo ? l : c.lo;
-        r = r < c.hi ? r : c.hi;
-        if (!(r > l)) return;
-    }
-    if (isinf(r)) {
-        if (h != T(0)) { diverges = true; tail_sign = h > T(0) ? 1.0 : -1.0; }
-        return;
-    }
-    sa.add(h, r - l);
-}
-
-// Segments k0, k0 + step, ... (kSegUnroll of them) of one PCF: loads first.
-template <int FN, typename Tin, typename T>
-__device__ __forceinline__ void seg_batch(const SegCtx<Tin, T>& c, int64_t k0, int64_t step,
-                                          int64_t o0, int64_t o1, SegAcc<T>& sa, bool& diverges,
-                                          double& tail_sign)
-{
-    SegLoad<Tin> d[kSegUnroll];
-#pragma unroll
-    for (int u = 0; u < kSegUnroll; ++u) {
-        const int64_t k = k0 + step * u;
-        if (k < o1) d[u] = seg_load(c, k, o0, o1);
-    }
-#pragma unroll
-    for (int u = 0; u < kSegUnroll; ++u) {
-        const int64_t k = k0 + step * u;
-        if (k < o1) seg_element<FN>(c, d[u], k, o0, sa, diverges, tail_sign);
-    }
-}
-
-// Offsets of PCF i as pcf_pairwise's input check reads them; false if bad.
-__device__ __forceinline__ bool seg_offsets(const int64_t* offsets, int64_t i, int64_t n,
-                                            int64_t nnz, Header* hdr, int64_t& o0, int64_t& o1)
-{
-    o0 = offsets[i]; o1 = offsets[i + 1];
-    bool bad = !(o0 >= 0 && o1 > o0 && o1 <= nnz && (o1 - o0) < (1ll << 31));
-    if (i == 0 && o0 != 0) bad = true;
-    if (i == n - 1 && o1 != nnz) bad = true;
-    if (bad) record_error(hdr, kErrOffsets, i);
-    return !bad;
 }
 
 __device__ __forceinline__ double seg_finish(double acc, bool div, double sign, int functional,
@@ -196,149 +193,278 @@ __device__ __forceinline__ void seg_store(void* out, int out_f64, int64_t i, dou
     else reinterpret_cast<float*>(out)[i] = (float)I;
 }
 
-// One warp per PCF of at most kSegLong breakpoints, lane l taking the
-// segments l, l + 32, ... (kSegUnroll loads in flight); longer PCFs go on a
-// list for segment_long_kernel.  The input check runs on the same loads.
-template <typename Tin, typename T, int FN>
-__global__ void segment_kernel(const int64_t* __restrict__ offsets, SegCtx<Tin, T> c, int64_t n,
-                               int64_t nnz, int apply_root, double p_, void* out, int out_f64,
-                               int32_t* long_list)
+// Elements [k0, k0 + N) of times and values.  VEC: 16-byte loads (the
+// arrays are 16-byte aligned and k0 is a multiple of N).
+template <typename Tin, bool VEC, int N>
+__device__ __forceinline__ void seg_load(const Tin* __restrict__ times, const Tin* __restrict__ values,
+                                         int64_t nnz, int64_t k0, Tin (&t)[N], Tin (&v)[N])
 {
-    const int lane = threadIdx.x & 31;
-    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    // float64 form: finished PCFs wait in the lanes (lane j holds the j-th)
-    // and are rooted and stored 32 at a time, one warp-wide pass of the
-    // float64 finish instead of one per PCF (measured: 0.72 -> 0.66 ms on the
-    // log-normal set; the float32 form is faster finishing each PCF in lane 0)
-    constexpr bool kBatch = sizeof(T) == 8;
-    SegAcc<T> held;
-    int64_t held_i = -1;
-    double held_sign = 0.0;
-    int slot = 0;
-    auto flush = [&]() {
-        if (held_i >= 0)
-            seg_store(out, out_f64, held_i, seg_finish(held.value(), held_sign != 0.0, held_sign,
-                                                       c.functional, apply_root, p_));
-        held_i = -1;
-        slot = 0;
-    };
-    for (int64_t i = warp0; i < n; i += nwarps) {
-        int64_t o0, o1;
-        if (!seg_offsets(offsets, i, n, nnz, c.hdr, o0, o1)) continue;
-        if (o1 - o0 > kSegLong) {
-            if (lane == 0) long_list[atomicAdd(&c.hdr->tiles, 1ull)] = (int32_t)i;
-            continue;
+    if (VEC && k0 + N <= nnz) {
+        if constexpr (sizeof(Tin) == 4) {
+            const float4* pt = reinterpret_cast<const float4*>(times + k0);
+            const float4* pv = reinterpret_cast<const float4*>(values + k0);
+#pragma unroll
+            for (int u = 0; u < N / 4; ++u) {
+                const float4 a = __ldg(pt + u), b = __ldg(pv + u);
+                t[4 * u] = a.x; t[4 * u + 1] = a.y; t[4 * u + 2] = a.z; t[4 * u + 3] = a.w;
+                v[4 * u] = b.x; v[4 * u + 1] = b.y; v[4 * u + 2] = b.z; v[4 * u + 3] = b.w;
+            }
+        } else {
+            const double2* pt = reinterpret_cast<const double2*>(times + k0);
+            const double2* pv = reinterpret_cast<const double2*>(values + k0);
+#pragma unroll
+            for (int u = 0; u < N / 2; ++u) {
+                const double2 a = __ldg(pt + u), b = __ldg(pv + u);
+                t[2 * u] = a.x; t[2 * u + 1] = a.y;
+                v[2 * u] = b.x; v[2 * u + 1] = b.y;
+            }
         }
-        SegAcc<T> sa;
-        bool diverges = false;
-        double tail_sign = 0.0;
-        for (int64_t k0 = o0 + lane; k0 < o1; k0 += 32 * kSegUnroll)
-            seg_batch<FN>(c, k0, 32, o0, o1, sa, diverges, tail_sign);
-        seg_warp_reduce(sa);
-        const SegAcc<T> tot = seg_lane0(sa);
-        const unsigned div = __ballot_sync(0xffffffffu, diverges);
-        double sign = 0.0;
-        if (div) sign = __shfl_sync(0xffffffffu, tail_sign, __ffs(div) - 1);
-        if constexpr (kBatch) {
-            if (lane == slot) { held = tot; held_i = i; held_sign = sign; }
-            if (++slot == 32) flush();
-        } else if (lane == 0) {
-            seg_store(out, out_f64, i, seg_finish(tot.value(), div != 0, sign, c.functional,
-                                                  apply_root, p_));
+    } else {
+#pragma unroll
+        for (int q = 0; q < N; ++q) {
+            const bool in = k0 + q < nnz;
+            t[q] = in ? __ldg(times + k0 + q) : Tin(0);
+            v[q] = in ? __ldg(values + k0 + q) : Tin(0);
         }
     }
-    if constexpr (kBatch) flush();
 }
 
-// One CTA per listed long PCF; thread partial sums combined in a fixed
-// order (warp shuffles, then the 8 warp sums in order).
-template <typename Tin, typename T, int FN>
-__global__ void __launch_bounds__(256) segment_long_kernel(const int64_t* __restrict__ offsets,
-                                                           SegCtx<Tin, T> c, int apply_root,
-                                                           double p_, void* out, int out_f64,
-                                                           const int32_t* long_list)
+// The input check of one element (reasons and indices of pcf_pairwise's
+// check); only run by a thread whose fast check found something wrong.
+template <typename Tin, bool R32>
+__device__ __noinline__ void seg_record(Header* hdr, int64_t k, Tin tk, Tin vk, Tin tp, bool is_first)
 {
-    __shared__ double sAcc[8];
-    __shared__ int sDiv[8];
-    __shared__ double sSign[8];
-    // no early exit on a recorded error: these PCFs' elements still have to
-    // be checked so that the smallest offending index is the one reported
-    const long long count = (long long)c.hdr->tiles;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (long long w = blockIdx.x; w < count; w += gridDim.x) {
-        const int64_t i = long_list[w];
-        const int64_t o0 = offsets[i], o1 = offsets[i + 1];
-        SegAcc<T> sa;
-        bool diverges = false;
-        double tail_sign = 0.0;
-        for (int64_t k0 = o0 + threadIdx.x; k0 < o1; k0 += 256 * kSegUnroll)
-            seg_batch<FN>(c, k0, 256, o0, o1, sa, diverges, tail_sign);
-        seg_warp_reduce(sa);
-        const double acc = sa.value();
-        const unsigned div = __ballot_sync(0xffffffffu, diverges);
-        if (lane == 0) {
-            sAcc[warp] = acc;
-            sDiv[warp] = div != 0;
-            sSign[warp] = 0.0;
-        }
-        if (div) {                                  // (div is the same in every lane)
-            const double sg = __shfl_sync(0xffffffffu, tail_sign, __ffs(div) - 1);
-            if (lane == 0) sSign[warp] = sg;
-        }
+    if (!isfinite(tk)) { record_error(hdr, kErrTimeNaN, k); return; }
+    if (!isfinite(vk)) { record_error(hdr, kErrValueNaN, k); return; }
+    if (is_first) {
+        if (tk != Tin(0)) record_error(hdr, kErrT0, k);
+    } else if (!(tk > tp)) {
+        record_error(hdr, kErrOrder, k);
+    }
+    if (R32 && (fabs((double)tk) > (double)FLT_MAX || fabs((double)vk) > (double)FLT_MAX))
+        record_error(hdr, kErrRange32, k);
+}
+
+template <typename Tin, typename T, int FN, bool VEC, bool CLIP>
+__global__ void __launch_bounds__(kSegThreads, sizeof(Tin) == 4 && sizeof(T) == 4 ? 3 : 2) segment_kernel(const SegArgs<Tin, T> g)
+{
+    using Sum = SegSum<T>;
+    constexpr int N = seg_items<Tin>();
+    constexpr int64_t kRound = (int64_t)kSegThreads * N;
+    constexpr bool R32 = sizeof(Tin) == 8 && sizeof(T) == 4;   // float64 data in float32
+    __shared__ int64_t soff[kSegBatch + 1];
+    __shared__ double sres[kSegBatch];          // raw integrals of the batch's PCFs
+    __shared__ signed char sdiv[kSegBatch];     // 0, or the sign of an infinite last segment
+    // scan exchange, double-buffered by round parity (one barrier per round)
+    __shared__ Sum warp_tot[2][kSegThreads / 32];
+    __shared__ Sum carry_sh[2];
+
+    // an offsets error (recorded by the table pass, before this kernel) makes
+    // the chunk table meaningless: nothing to integrate.  Element errors do
+    // not stop the pass, so that every element is checked.
+    if (__syncthreads_or(threadIdx.x == 0 && g.hdr->err < (1ull << 62))) return;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t c = blockIdx.x;
+    int64_t a = g.table[c], b = g.table[c + 1];
+    if (a < 0) a = 0;
+    if (b > g.n) b = g.n;
+
+    for (int64_t a0 = a; a0 < b; a0 += kSegBatch) {
+        const int np = (int)((b - a0) < kSegBatch ? (b - a0) : kSegBatch);
+        for (int j = tid; j <= np; j += kSegThreads) soff[j] = g.offsets[a0 + j];
+        if (tid == 0) carry_sh[0] = seg_identity<T>();
         __syncthreads();
-        if (threadIdx.x == 0) {
-            double tot = 0.0, sign = 0.0;
-            bool any = false;
-            for (int q = 0; q < 8; ++q) {
-                tot += sAcc[q];
-                if (sDiv[q] && !any) { any = true; sign = sSign[q]; }
+        const int64_t e_lo = soff[0], e_hi = soff[np];
+        const int64_t r_begin = e_lo - (e_lo % N);
+        const int64_t nrounds = (e_hi - r_begin + kRound - 1) / kRound;
+
+        for (int64_t r = 0; r < nrounds; ++r) {
+            const int64_t k0 = r_begin + r * kRound + (int64_t)tid * N;
+            const bool active = k0 < e_hi && k0 + N > e_lo;
+            Tin tt[N], vv[N];
+            if (active) {
+                seg_load<Tin, VEC, N>(g.times, g.values, g.nnz, k0, tt, vv);
+            } else {
+#pragma unroll
+                for (int q = 0; q < N; ++q) { tt[q] = Tin(0); vv[q] = Tin(0); }
             }
-            seg_store(out, out_f64, i, seg_finish(tot, any, sign, c.functional, apply_root, p_));
+            // neighbours: t_{k0-1} from the lane before, t_{k0+N} from the lane after
+            Tin t_prev = __shfl_up_sync(0xffffffffu, tt[N - 1], 1);
+            Tin t_next = __shfl_down_sync(0xffffffffu, tt[0], 1);
+            if (active && lane == 0 && k0 > 0) t_prev = __ldg(g.times + k0 - 1);
+            if (active && lane == 31 && k0 + N < g.nnz) t_next = __ldg(g.times + k0 + N);
+
+            // ---- this thread's elements, in order ----
+            // Positions are kept relative to k0 (clamped to [-1, N + 1]), so the
+            // per-element bookkeeping is 32-bit.
+            Sum run = seg_identity<T>();        // the open run (flag: it started here)
+            Sum first = seg_identity<T>();      // a continued run that ended here
+            int first_j = -1;
+            int first_div = 0, run_div = 0;     // 0, or the sign of an infinite last segment
+            if (active) {
+                auto rel = [&](int64_t e) -> int {
+                    const int64_t d = e - k0;
+                    return d < -1 ? -1 : d > N + 1 ? N + 1 : (int)d;
+                };
+                const int q_lo = rel(e_lo) < 0 ? 0 : rel(e_lo);
+                const int q_hi = rel(e_hi) > N ? N : rel(e_hi);
+                // PCF (batch-local) of the first owned element: soff[j] <= k < soff[j + 1]
+                const int64_t kf = k0 + q_lo;
+                int lo_j = 0, hi_j = np - 1;
+                while (lo_j < hi_j) {
+                    const int m = (lo_j + hi_j + 1) >> 1;
+                    if (soff[m] <= kf) lo_j = m; else hi_j = m - 1;
+                }
+                int j = lo_j;
+                const int j_first = j;
+                int sb = rel(soff[j]), nb = rel(soff[j + 1]);   // start, next start
+                bool bad = false;
+#pragma unroll
+                for (int q = 0; q < N; ++q) {
+                    const bool in = q >= q_lo && q < q_hi;
+                    if (in && q == nb) { ++j; sb = nb; nb = rel(soff[j + 1]); }
+                    const bool is_first = q == sb, is_last = q + 1 == nb;
+                    const Tin tk = tt[q], vk = vv[q];
+                    const Tin tp = q > 0 ? tt[q - 1] : t_prev;
+                    const Tin tn = q + 1 < N ? tt[q + 1] : t_next;
+                    // fast input check, exact report below
+                    bool ok = fabs(tk) < Tin(INFINITY) && fabs(vk) < Tin(INFINITY) &&
+                              (is_first ? tk == Tin(0) : tk > tp);
+                    if (R32) ok = ok && fabs((double)tk) <= (double)FLT_MAX &&
+                                  fabs((double)vk) <= (double)FLT_MAX;
+                    bad |= in && !ok;
+                    if (in && is_first) { run = seg_identity<T>(); run.flag = 1; run_div = 0; }
+                    const T h = seg_h<FN, T>((T)vk, g.pw);
+                    T l = (T)tk, rr = is_last ? T(INFINITY) : (T)tn;
+                    if (CLIP) {
+                        l = l > g.lo ? l : g.lo;
+                        rr = rr < g.hi ? rr : g.hi;
+                    }
+                    const bool use = in && (!CLIP || rr > l);
+                    const bool inf_seg = isinf(rr);
+                    if (use && !inf_seg) run.add(h, rr - l);
+                    if (use && inf_seg && h != T(0)) run_div = h > T(0) ? 1 : -1;
+                    if (in && is_last) {
+                        if (run.flag) {
+                            // the whole PCF lies in this thread's elements
+                            sres[j] = run.value();
+                            sdiv[j] = (signed char)run_div;
+                        } else {
+                            // continued from earlier threads: finished after the scan
+                            first = run;
+                            first_j = j;
+                            first_div = run_div;
+                        }
+                        run = seg_identity<T>();
+                        run_div = 0;
+                    }
+                }
+                if (bad) {
+                    // exact report: walk the elements again with the full check
+                    // (compile-time indices keep tt / vv in registers)
+                    int jj = j_first, sb2 = rel(soff[jj]), nb2 = rel(soff[jj + 1]);
+#pragma unroll
+                    for (int q = 0; q < N; ++q) {
+                        if (q < q_lo || q >= q_hi) continue;
+                        if (q == nb2) { ++jj; sb2 = nb2; nb2 = rel(soff[jj + 1]); }
+                        const Tin tp = q > 0 ? tt[q - 1] : t_prev;
+                        seg_record<Tin, R32>(g.hdr, k0 + q, tt[q], vv[q], tp, q == sb2);
+                    }
+                }
+                // a head anywhere in the thread: nothing before it is carried
+                run.flag = (sb >= q_lo && sb < q_hi) || j != j_first ? 1 : 0;
+            }
+
+            // ---- segmented scan of the open runs: carry into each thread ----
+            const int par = (int)(r & 1);
+            Sum inc = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const Sum up = inc.shfl_up(o);
+                if (lane >= o) inc = Sum::join(up, inc);
+            }
+            Sum exc = inc.shfl_up(1);
+            if (lane == 0) exc = seg_identity<T>();
+            if (lane == 31) warp_tot[par][warp] = inc;
+            __syncthreads();
+            // every warp scans the warp totals before its own (and the carry of
+            // the rounds before); the last warp publishes the next carry
+            {
+                const Sum cin = carry_sh[par];
+                Sum winc = lane < warp ? warp_tot[par][lane] : seg_identity<T>();
+#pragma unroll
+                for (int o = 1; o < kSegThreads / 32; o <<= 1) {
+                    const Sum up = winc.shfl_up(o);
+                    if (lane >= o) winc = Sum::join(up, winc);
+                }
+                // lane warp - 1 now holds warps 0 .. warp-1 combined
+                Sum before = winc.shfl_idx(warp > 0 ? warp - 1 : 0);
+                if (warp == 0) before = seg_identity<T>();
+                const Sum pre = Sum::join(cin, before);
+                if (warp == kSegThreads / 32 - 1 && lane == 31)
+                    carry_sh[par ^ 1] = Sum::join(pre, inc);
+                if (first_j >= 0) {
+                    const Sum tot = Sum::join(Sum::join(pre, exc), first);
+                    sres[first_j] = tot.value();
+                    sdiv[first_j] = (signed char)first_div;
+                }
+            }
         }
         __syncthreads();
+        // ---- finish the batch's PCFs (tail rule, root) with coalesced stores ----
+        for (int j = tid; j < np; j += kSegThreads)
+            seg_store(g.out, g.out_f64, a0 + j,
+                      seg_finish(sres[j], sdiv[j] != 0, (double)sdiv[j], g.functional,
+                                 g.apply_root, g.p));
+        __syncthreads();   // soff, sres and the carry are rewritten by the next batch
     }
 }
 
 cudaError_t launch_segments(const pcf_csr* x, int functional, double p, int apply_root,
                             double lo, double hi, int precision, void* out, int out_f64,
-                            Header* hdr, int32_t* long_list, cudaStream_t s)
+                            Header* hdr, void* scratch, cudaStream_t s)
 {
     if (x->n == 0) return cudaSuccess;
-    int64_t blocks = (x->n * 32 + 255) / 256;
-    const int64_t cap = (int64_t)device_sm_count() * 16;
-    if (blocks > cap) blocks = cap;
-    const int long_blocks = device_sm_count() * 4;
+    const int64_t nchunks = (x->nnz + kSegChunk - 1) / kSegChunk;
+    int64_t* table = reinterpret_cast<int64_t*>(scratch);
+    {
+        int64_t blocks = (x->n + 255) / 256;
+        const int64_t cap = (int64_t)device_sm_count() * 16;
+        if (blocks > cap) blocks = cap;
+        seg_table_kernel<<<(int)blocks, 256, 0, s>>>(x->offsets, x->n, x->nnz, nchunks, table, hdr);
+    }
+    if (nchunks == 0) return cudaGetLastError();
     const bool f32 = precision != PCF_PREC_F64;
     const int fn = functional == PCF_FN_INTEGRAL ? kFnIntegral
                    : p == 1.0 ? kFnAbs : p == 2.0 ? kFnSquare : p == 3.0 ? kFnCube : kFnPow;
-#define PCF_SEG_FN(TIN, TW, FN)                                                                   \
-    {                                                                                             \
-        segment_kernel<TIN, TW, FN><<<(int)blocks, 256, 0, s>>>(x->offsets, c, x->n, x->nnz,      \
-                                                                apply_root, p, out, out_f64,      \
-                                                                long_list);                       \
-        segment_long_kernel<TIN, TW, FN><<<long_blocks, 256, 0, s>>>(x->offsets, c, apply_root,   \
-                                                                     p, out, out_f64, long_list); \
+    const bool vec = ((uintptr_t)x->times % 16 == 0) && ((uintptr_t)x->values % 16 == 0);
+    const bool clip = lo > 0.0 || !std::isinf(hi);
+#define PCF_SEG_GO(TIN, TW, FN)                                                                    \
+    {                                                                                              \
+        SegArgs<TIN, TW> g{x->offsets, (const TIN*)x->times, (const TIN*)x->values, x->n, x->nnz,  \
+                           table, functional, apply_root ? 1 : 0, p, (TW)p, (TW)lo, (TW)hi, out,   \
+                           out_f64, hdr};                                                          \
+        const unsigned grid = (unsigned)nchunks;                                                   \
+        if (vec && clip) segment_kernel<TIN, TW, FN, true, true><<<grid, kSegThreads, 0, s>>>(g);  \
+        else if (vec) segment_kernel<TIN, TW, FN, true, false><<<grid, kSegThreads, 0, s>>>(g);    \
+        else if (clip) segment_kernel<TIN, TW, FN, false, true><<<grid, kSegThreads, 0, s>>>(g);   \
+        else segment_kernel<TIN, TW, FN, false, false><<<grid, kSegThreads, 0, s>>>(g);            \
     }
-#define PCF_SEG_LAUNCH(TIN, TW)                                                                   \
-    {                                                                                             \
-        SegCtx<TIN, TW> c{(const TIN*)x->times, (const TIN*)x->values, functional, (TW)p, (TW)lo, \
-                          (TW)hi, hdr, sizeof(TIN) == 8 && sizeof(TW) == 4,                       \
-                          lo > 0.0 || !std::isinf(hi)};                                           \
-        switch (fn) {                                                                             \
-        case kFnIntegral: PCF_SEG_FN(TIN, TW, kFnIntegral) break;                                 \
-        case kFnAbs: PCF_SEG_FN(TIN, TW, kFnAbs) break;                                           \
-        case kFnSquare: PCF_SEG_FN(TIN, TW, kFnSquare) break;                                     \
-        case kFnCube: PCF_SEG_FN(TIN, TW, kFnCube) break;                                         \
-        default: PCF_SEG_FN(TIN, TW, kFnPow) break;                                               \
-        }                                                                                         \
+#define PCF_SEG_LAUNCH(TIN, TW)                                                                    \
+    switch (fn) {                                                                                  \
+    case kFnIntegral: PCF_SEG_GO(TIN, TW, kFnIntegral) break;                                      \
+    case kFnAbs: PCF_SEG_GO(TIN, TW, kFnAbs) break;                                                \
+    case kFnSquare: PCF_SEG_GO(TIN, TW, kFnSquare) break;                                          \
+    case kFnCube: PCF_SEG_GO(TIN, TW, kFnCube) break;                                              \
+    default: PCF_SEG_GO(TIN, TW, kFnPow) break;                                                    \
     }
     if (x->dtype == PCF_F64) {
         if (f32) PCF_SEG_LAUNCH(double, float) else PCF_SEG_LAUNCH(double, double)
     } else {
         if (f32) PCF_SEG_LAUNCH(float, float) else PCF_SEG_LAUNCH(float, double)
     }
-#undef PCF_SEG_FN
+#undef PCF_SEG_GO
 #undef PCF_SEG_LAUNCH
     return cudaGetLastError();
 }

@@ -158,3 +158,63 @@ def test_segments_full_size_sampled(pcf, prec):
         w = oracle.segment_integral(t, v, "integral")
         scale = oracle.segment_integral(t, v, "lp", 1.0)
         assert abs(integ[i] - w) <= tol * scale + 1e-30, (i, integ[i], w)
+
+
+def _mixed_layout_set(seed):
+    """Lengths chosen to cross every boundary of the flat pass: thousands of
+    length-1 and length-2 PCFs (several staged batches of PCF offsets inside
+    one 8192-breakpoint chunk), PCFs of 20,000 and 41,000 breakpoints (many
+    rounds, several chunks, no PCF starting in some chunks), and random
+    lengths with an odd total."""
+    rng = np.random.default_rng(seed)
+    parts = [synth.random_set(1500, seed=seed + 1, min_len=1, max_len=2),
+             synth.random_set(1, seed=seed + 2, min_len=20000, max_len=20000),
+             synth.random_set(300, seed=seed + 3, min_len=1, max_len=300),
+             synth.random_set(1, seed=seed + 4, min_len=41000, max_len=41000),
+             synth.random_set(1200, seed=seed + 5, min_len=1, max_len=3),
+             synth.random_set(77, seed=seed + 6, min_len=2000, max_len=9000)]
+    offs, ts, vs, base = [np.zeros(1, np.int64)], [], [], 0
+    for p in parts:
+        offs.append(p.offsets[1:] + base)
+        base += int(p.offsets[-1])
+        ts.append(p.times)
+        vs.append(p.values)
+    s = synth.PcfSet(np.concatenate(offs), np.concatenate(ts), np.concatenate(vs))
+    return synth.subset(s, rng.permutation(s.n)) if seed % 2 else s
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32c"])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("aligned", [True, False])
+def test_segments_chunk_and_batch_layouts(pcf, prec, dtype, aligned):
+    """Every PCF of a set whose lengths cross the chunk, round and batch
+    boundaries of the flat pass, with 16-byte aligned arrays (vector loads)
+    and with arrays that start one element off (scalar loads)."""
+    import torch
+    s = _mixed_layout_set(11 if aligned else 12).astype(dtype)
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    if not aligned:
+        def shifted(a):
+            big = torch.empty(a.numel() + 1, dtype=a.dtype, device=a.device)
+            big[1:] = a
+            return big[1:]
+        x = pcf.PcfTensors(x.offsets, shifted(x.times), shifted(x.values))
+        assert x.times.data_ptr() % 16 != 0
+    # float64 data integrated in float32: the oracle sees the rounded input
+    ref = s.astype(np.float32) if (prec == "f32c" and dtype == np.float64) else s
+    tol = 1e-12 if prec == "f64" else 1e-5
+    for kind, p, root, ab in (("lp", 2.0, True, (0.0, np.inf)),
+                              ("integral", 1.0, False, (0.75, 60.0))):
+        got = pcf.pcf_segment_integrals(x, kind, p, root, ab[0], ab[1],
+                                        precision=prec).cpu().numpy()
+        for i in range(s.n):
+            t, v = ref.pcf(i)
+            want = oracle.segment_integral(t, v, kind, p, ab[0], ab[1])
+            scale = oracle.segment_integral(t, v, "lp", 1.0 if kind == "integral" else p,
+                                            ab[0], ab[1])
+            if root:
+                want, scale = want ** (1.0 / p), scale ** (1.0 / p)
+            if np.isinf(want):
+                assert got[i] == want, (i, got[i], want)
+            else:
+                assert abs(got[i] - want) <= tol * scale + 1e-30, (i, s.lengths()[i], got[i], want)
