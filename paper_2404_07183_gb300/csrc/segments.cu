@@ -245,6 +245,44 @@ __device__ __noinline__ void seg_record(Header* hdr, int64_t k, Tin tk, Tin vk, 
         record_error(hdr, kErrRange32, k);
 }
 
+// Fast input check of a thread's elements, on the pipes the arithmetic does
+// not saturate: it only has to notice that something may be wrong (the exact
+// report is made by seg_record).  Non-finite values poison a float
+// accumulator (x * 0 is NaN for inf and NaN) or, for float64 arithmetic, the
+// largest exponent field seen; the widths t_{k+1} - t_k between elements of
+// one PCF must stay > 0 (float compare, or the order of the bit patterns of
+// float64 times, which catches the first descent below a non-negative time).
+template <typename Tin, typename T>
+struct SegCheck {
+    float fin = 0.f, md = INFINITY;      // float data or float arithmetic
+    unsigned emax = 0u;                  // float64 data, float64 arithmetic
+    bool order_bad = false;
+    __device__ __forceinline__ void value(Tin t, Tin v)
+    {
+        if constexpr (sizeof(T) == 4) fin = fmaf((float)t, 0.f, fmaf((float)v, 0.f, fin));
+        else if constexpr (sizeof(Tin) == 4) fin = fmaf(t, 0.f, fmaf(v, 0.f, fin));
+        else {
+            const unsigned a = (unsigned)__double2hiint(t) & 0x7ff00000u;
+            const unsigned b = (unsigned)__double2hiint(v) & 0x7ff00000u;
+            emax = max(emax, max(a, b));
+        }
+    }
+    // t_next > t within one PCF
+    __device__ __forceinline__ void order(Tin t, Tin t_next)
+    {
+        if constexpr (sizeof(Tin) == 4 || sizeof(T) == 4) {
+            const float d = (float)t_next - (float)t;
+            md = fminf(md, d);
+        } else {
+            order_bad |= !(__double_as_longlong(t_next) > __double_as_longlong(t));
+        }
+    }
+    __device__ __forceinline__ bool bad() const
+    {
+        return fin != 0.f || !(md > 0.f) || emax == 0x7ff00000u || order_bad;
+    }
+};
+
 template <typename Tin, typename T, int FN, bool VEC, bool CLIP>
 __global__ void __launch_bounds__(kSegThreads, sizeof(Tin) == 4 && sizeof(T) == 4 ? 3 : 2) segment_kernel(const SegArgs<Tin, T> g)
 {
@@ -296,19 +334,14 @@ __global__ void __launch_bounds__(kSegThreads, sizeof(Tin) == 4 && sizeof(T) == 
             if (active && lane == 31 && k0 + N < g.nnz) t_next = __ldg(g.times + k0 + N);
 
             // ---- this thread's elements, in order ----
-            // Positions are kept relative to k0 (clamped to [-1, N + 1]), so the
-            // per-element bookkeeping is 32-bit.
-            Sum run = seg_identity<T>();        // the open run (flag: it started here)
+            Sum run = seg_identity<T>();        // the open run (flag: its PCF starts here)
             Sum first = seg_identity<T>();      // a continued run that ended here
             int first_j = -1;
             int first_div = 0, run_div = 0;     // 0, or the sign of an infinite last segment
             if (active) {
-                auto rel = [&](int64_t e) -> int {
-                    const int64_t d = e - k0;
-                    return d < -1 ? -1 : d > N + 1 ? N + 1 : (int)d;
-                };
-                const int q_lo = rel(e_lo) < 0 ? 0 : rel(e_lo);
-                const int q_hi = rel(e_hi) > N ? N : rel(e_hi);
+                const int64_t dlo = e_lo - k0, dhi = e_hi - k0;
+                const int q_lo = dlo > 0 ? (int)dlo : 0;
+                const int q_hi = dhi < N ? (int)dhi : N;
                 // PCF (batch-local) of the first owned element: soff[j] <= k < soff[j + 1]
                 const int64_t kf = k0 + q_lo;
                 int lo_j = 0, hi_j = np - 1;
@@ -316,36 +349,73 @@ __global__ void __launch_bounds__(kSegThreads, sizeof(Tin) == 4 && sizeof(T) == 
                     const int m = (lo_j + hi_j + 1) >> 1;
                     if (soff[m] <= kf) lo_j = m; else hi_j = m - 1;
                 }
-                int j = lo_j;
-                const int j_first = j;
-                int sb = rel(soff[j]), nb = rel(soff[j + 1]);   // start, next start
+                const int j0 = lo_j;
+                // bit q of bnd: a PCF of the batch starts at k0 + q (the batch end
+                // counts as a start), q = 0 .. N
+                uint32_t bnd = 0;
+                for (int jj = j0; jj <= np; ++jj) {
+                    const int64_t d = soff[jj] - k0;
+                    if (d > N) break;
+                    if (d >= 0) bnd |= 1u << (int)d;
+                }
+                const uint32_t inm = ((1u << q_hi) - 1u) & ~((1u << q_lo) - 1u);
+                const uint32_t headm = bnd & inm;           // first elements of PCFs
+                const uint32_t lastm = (bnd >> 1) & inm;    // last elements of PCFs
+                // batch-local PCF of element q: jbase + popc(headm & bits 0..q)
+                const int jbase = j0 - (int)((headm >> q_lo) & 1u);
+                if (inm != (1u << N) - 1u) {
+                    // edge of the owned range: the elements outside it belong to other
+                    // CTAs; stand-ins (increasing finite times, value 0) add nothing
+                    // and pass the check
+                    if (q_lo > 0) t_prev = Tin(-2 * N);
+                    if (q_hi < N) t_next = Tin(2 * N);
+#pragma unroll
+                    for (int q = 0; q < N; ++q) {
+                        if (q < q_lo) { tt[q] = Tin(q - N); vv[q] = Tin(0); }
+                        if (q >= q_hi) { tt[q] = Tin(q + 1); vv[q] = Tin(0); }
+                    }
+                }
+                SegCheck<Tin, T> chk;
                 bool bad = false;
+                if (!(headm & 1u)) chk.order(t_prev, tt[0]);
 #pragma unroll
                 for (int q = 0; q < N; ++q) {
-                    const bool in = q >= q_lo && q < q_hi;
-                    if (in && q == nb) { ++j; sb = nb; nb = rel(soff[j + 1]); }
-                    const bool is_first = q == sb, is_last = q + 1 == nb;
                     const Tin tk = tt[q], vk = vv[q];
-                    const Tin tp = q > 0 ? tt[q - 1] : t_prev;
                     const Tin tn = q + 1 < N ? tt[q + 1] : t_next;
-                    // fast input check, exact report below
-                    bool ok = fabs(tk) < Tin(INFINITY) && fabs(vk) < Tin(INFINITY) &&
-                              (is_first ? tk == Tin(0) : tk > tp);
-                    if (R32) ok = ok && fabs((double)tk) <= (double)FLT_MAX &&
-                                  fabs((double)vk) <= (double)FLT_MAX;
-                    bad |= in && !ok;
-                    if (in && is_first) { run = seg_identity<T>(); run.flag = 1; run_div = 0; }
-                    const T h = seg_h<FN, T>((T)vk, g.pw);
-                    T l = (T)tk, rr = is_last ? T(INFINITY) : (T)tn;
-                    if (CLIP) {
-                        l = l > g.lo ? l : g.lo;
-                        rr = rr < g.hi ? rr : g.hi;
+                    const T tkT = (T)tk, vkT = (T)vk, tnT = (T)tn;
+                    chk.value(tk, vk);
+                    if ((headm >> q) & 1u) {
+                        bad |= tk != Tin(0);
+                        run = seg_identity<T>();
+                        run.flag = 1;
+                        run_div = 0;
                     }
-                    const bool use = in && (!CLIP || rr > l);
-                    const bool inf_seg = isinf(rr);
-                    if (use && !inf_seg) run.add(h, rr - l);
-                    if (use && inf_seg && h != T(0)) run_div = h > T(0) ? 1 : -1;
-                    if (in && is_last) {
+                    const T h = seg_h<FN, T>(vkT, g.pw);
+                    if (!((lastm >> q) & 1u)) {
+                        const T len = tnT - tkT;
+                        chk.order(tk, tn);
+                        if (CLIP) {
+                            const T l = tkT > g.lo ? tkT : g.lo;
+                            const T rr = tnT < g.hi ? tnT : g.hi;
+                            if (rr > l) run.add(h, rr - l);
+                        } else {
+                            run.add(h, len);
+                        }
+                    } else {
+                        // last segment [t_k, inf) clipped to [a, b]
+                        if (CLIP) {
+                            const T l = tkT > g.lo ? tkT : g.lo;
+                            if (g.hi > l) {
+                                if (isinf(g.hi)) {
+                                    if (h != T(0)) run_div = h > T(0) ? 1 : -1;
+                                } else {
+                                    run.add(h, g.hi - l);
+                                }
+                            }
+                        } else if (h != T(0)) {
+                            run_div = h > T(0) ? 1 : -1;
+                        }
+                        const int j = jbase + __popc(headm & ((2u << q) - 1u));
                         if (run.flag) {
                             // the whole PCF lies in this thread's elements
                             sres[j] = run.value();
@@ -356,24 +426,22 @@ __global__ void __launch_bounds__(kSegThreads, sizeof(Tin) == 4 && sizeof(T) == 
                             first_j = j;
                             first_div = run_div;
                         }
-                        run = seg_identity<T>();
-                        run_div = 0;
                     }
                 }
+                bad |= chk.bad();
                 if (bad) {
                     // exact report: walk the elements again with the full check
                     // (compile-time indices keep tt / vv in registers)
-                    int jj = j_first, sb2 = rel(soff[jj]), nb2 = rel(soff[jj + 1]);
 #pragma unroll
                     for (int q = 0; q < N; ++q) {
                         if (q < q_lo || q >= q_hi) continue;
-                        if (q == nb2) { ++jj; sb2 = nb2; nb2 = rel(soff[jj + 1]); }
                         const Tin tp = q > 0 ? tt[q - 1] : t_prev;
-                        seg_record<Tin, R32>(g.hdr, k0 + q, tt[q], vv[q], tp, q == sb2);
+                        seg_record<Tin, R32>(g.hdr, k0 + q, tt[q], vv[q], tp,
+                                             ((headm >> q) & 1u) != 0);
                     }
                 }
-                // a head anywhere in the thread: nothing before it is carried
-                run.flag = (sb >= q_lo && sb < q_hi) || j != j_first ? 1 : 0;
+                // a PCF starts in this thread: nothing before it is carried on
+                run.flag = headm != 0u ? 1 : 0;
             }
 
             // ---- segmented scan of the open runs: carry into each thread ----
