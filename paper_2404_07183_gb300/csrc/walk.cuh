@@ -386,8 +386,14 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
             // ---- stage elements [S, S + min(W, len - S)) of the PCFs whose
             //      window start moved (the others are still in place) ----
             // THREADS is a multiple of 16, so a thread always serves the same
-            // slot (tid & 15) of each region and walks k in steps of THREADS/16.
+            // slot (tid & 15) of each region.  A thread copies whole 32-byte
+            // sectors of its PCF (G elements, two 16-byte loads; the packed
+            // arrays are 256-byte aligned, so a sector holding one element of
+            // the set lies inside its buffer) and stores the ones inside the
+            // window; the 16 lanes of a half-warp store 16 different slots, so
+            // the shared-memory stores are free of bank conflicts.
             {
+                constexpr int G = 32 / (int)sizeof(E);
                 const int slot = tid & 15;
 #pragma unroll 1
                 for (int region = 0; region < NPCF / kGroup; ++region) {
@@ -397,10 +403,23 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                     const int len = sLen[p];
                     int kend = len - S;
                     if (kend > W) kend = W;
-                    const E* src = (p < kTile ? packR : packC) + sOff[p] + S;
+                    const int64_t g0 = sOff[p] + S;               // first element of the window
+                    const int lead = (int)(g0 & (G - 1));         // its place in its sector
+                    const E* src = (p < kTile ? packR : packC) + (g0 - lead);
+                    const int nsec = (kend + lead + G - 1) / G;
                     unsigned char* dst = smem + (unsigned)region * regionBytes + (unsigned)slot * sizeof(E);
-                    for (int k = tid >> 4; k < kend; k += THREADS / 16)
-                        *reinterpret_cast<E*>(dst + (unsigned)k * kRow) = src[k];
+                    for (int sc = tid >> 4; sc < nsec; sc += THREADS / 16) {
+                        const float4* q = reinterpret_cast<const float4*>(src + sc * G);
+                        union { float4 f[2]; E e[G]; } u;
+                        u.f[0] = __ldg(q);
+                        u.f[1] = __ldg(q + 1);
+#pragma unroll
+                        for (int v = 0; v < G; ++v) {
+                            const int k = sc * G - lead + v;
+                            if (k >= 0 && k < kend)
+                                *reinterpret_cast<E*>(dst + (unsigned)k * kRow) = u.e[v];
+                        }
+                    }
                 }
             }
             __syncthreads();
