@@ -46,9 +46,9 @@ FP64_OPS_PER_STEP = 1 + 1 + 1 + 2 + 2   # dt, d, L1 fma, L2 mul+fma, Gram mul+fm
 # DRAM bytes (read + write) per launch of the benchmark's compensated walk,
 # from one ncu capture (profiles/walk_f32c_dram_traffic_stable_rank_n20000.md),
 # valid only while the walk's source is the one that was measured.
-TRAFFIC_RECORD = {"source_sha256_16": "6005a2e6a9ca1252+a61c2acb5526ec88",
-                  "by_schedule_layout": {("tile512x3", "full"): 33889372416 + 31335099648,
-                                         ("tile512x3", "sorted"): 287516928 + 5276136448}}
+TRAFFIC_RECORD = {"source_sha256_16": "b908d804cd4f19a0+dae2d9473682ceec",
+                  "by_schedule_layout": {("tile512x3", "full"): 34974103296 + 32682371840,
+                                         ("tile512x3", "sorted"): 376924416 + 5578889984}}
 
 
 def walk_source_id():
