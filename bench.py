@@ -785,11 +785,19 @@ def run_workload(name, args):
         if not args.no_cpu:
             oracle.backward(sub, G[:300, :300], metric="l2", p=2.0)
         dt = max(time.perf_counter() - t0, 1e-9)
+        # float64 operations per rectangle of the L2 adjoint: dt, d, d*dt, two
+        # value-gradient fma; time gradient of the advancing side: v_new - v_other,
+        # its square, fma(d, d, -b*b), times the weight
+        bw_ops = 9
         return _line(name, pairs / (ms * 1e-3), "pair-gradients/s", ms, args.steps, args.warmup,
                      "f64", {"workload": "gradient N=4096 n~U{20..200} Exp(1) N(0,1) float64, "
                              "d(sum G*D2^2)/d(values, times)", "N": N, "pairs": pairs,
                              "merge_steps": steps_walk, "l2": "flushed between steps"},
                      merge_steps_per_s=rate,
+                     roofline={"bound": "fp64 pipe", "achieved": rate, "peak": fp64(bw_ops),
+                               "unit": "merge-steps/s", "frac": rate / fp64(bw_ops),
+                               "note": f"whole backward call (recomputing walk + scatter); "
+                                       f"{bw_ops} float64 ops per merge step"},
                      cpu_baseline={"value": 300 * 299 / 2 / dt, "unit": "pair-gradients/s",
                                    "cores": 1, "kind": "oracle", "seconds": dt,
                                    "sample": "first 300 PCFs, single-threaded oracle adjoint"})
