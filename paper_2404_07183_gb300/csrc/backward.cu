@@ -119,12 +119,15 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BackArgs a)
 
         // Alg. 1 walk over [0, inf) with simultaneous advance on ties.  End
         // times are compared by their bit patterns on the integer pipe
-        // (non-negative doubles order like their bits; +inf marks the tail);
-        // for L1, L2 and the Gram the value gradients of both sides share one
-        // product and the time gradient h(v_old, g) - h(v_new, g) is taken in
-        // factored form, so that the narrow FP64 pipe only does the
-        // arithmetic of the adjoint: L2 9, Gram 8, L1 7 float64 operations
-        // per rectangle (L_p keeps the general form).
+        // (non-negative doubles order like their bits; +inf marks the tail).
+        // For L1, L2 and the Gram the value gradients of both sides share one
+        // product, and the time gradient h(v_old, g) - h(v_new, g) is taken
+        // in factored form; every integrand is symmetric, h(a, b) = h(b, a),
+        // so the side that advances (f on a tie) is handled by one
+        // branch-free update with selected operands and addresses -- lanes
+        // of a warp advancing different sides no longer run two half-empty
+        // branches -- and the second side of a shared breakpoint by a rare
+        // extra branch.  float64 operations per rectangle: L2 9, Gram 7, L1 7.
         int kf = 0, kg = 0;
         double2 ef = a.pack[of], eg = a.pack[og];
         double tc = 0.0, gvf = 0.0, gvg = 0.0;
@@ -132,57 +135,56 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BackArgs a)
         const double w2 = 2.0 * w;
         for (;;) {
             const long long bf = __double_as_longlong(ef.x), bg = __double_as_longlong(eg.x);
-            const long long bn = bf < bg ? bf : bg;
+            const bool sf = bf <= bg;               // f advances (also on a tie)
+            const long long bn = sf ? bf : bg;
             if (bn == kInfBits) break;
+            const bool tie = bf == bg;
             const double tn = __longlong_as_double(bn);
             const double dt = tn - tc;
             const double vf = ef.y, vg = eg.y;
-            const bool adv_f = bf <= bg, adv_g = bg <= bf;
-            double tgf = 0.0, tgg = 0.0;            // time gradients (w applied below)
-            double2 nf = ef, ng = eg;
-            if (adv_f) nf = a.pack[of + kf + 1];
-            if (adv_g) ng = a.pack[og + kg + 1];
+            const int64_t at = sf ? of + kf : og + kg;   // advancing side's current element
+            const double2 nx = a.pack[at + 1];
+            const double v_old = sf ? vf : vg, other = sf ? vg : vf;
+            double d = 0.0;
             if constexpr (METRIC == PCF_L2) {
-                // dh/dv_f = 2 d, dh/dv_g = -2 d;  d_old^2 - d_new^2 as fma(d, d, -b*b)
-                const double d = vf - vg, e = d * dt;
+                // dh/dv_f = 2 d = -dh/dv_g
+                d = vf - vg;
+                const double e = d * dt;
                 gvf = fma(w2, e, gvf);
                 gvg = fma(-w2, e, gvg);
-                if (adv_f) { const double bb = nf.y - vg; tgf = fma(d, d, -(bb * bb)); }
-                if (adv_g) { const double bb = ng.y - vf; tgg = fma(d, d, -(bb * bb)); }
             } else if constexpr (METRIC == PCF_GRAM) {
-                // dh/dv_f = v_g, dh/dv_g = v_f;  (v_old - v_new) * other
+                // dh/dv_f = v_g, dh/dv_g = v_f
                 const double wdt = w * dt;
                 gvf = fma(wdt, vg, gvf);
                 gvg = fma(wdt, vf, gvg);
-                if (adv_f) tgf = (vf - nf.y) * vg;
-                if (adv_g) tgg = (vg - ng.y) * vf;
             } else if constexpr (METRIC == PCF_L1) {
-                // dh/dv_f = sign(d) = -dh/dv_g (0 where d = 0);  |d_old| - |d_new|
-                const double d = vf - vg;
+                // dh/dv_f = sign(d) = -dh/dv_g, 0 where d = 0
+                d = vf - vg;
                 const long long db = __double_as_longlong(d);
                 const double wdt = w * dt;
                 const double sw = (db << 1) == 0 ? 0.0 : (db < 0 ? -wdt : wdt);
                 gvf += sw;
                 gvg -= sw;
-                if (adv_f) tgf = fabs(d) - fabs(nf.y - vg);
-                if (adv_g) tgg = fabs(d) - fabs(ng.y - vf);
             } else {
                 gvf += w * bw_dh<METRIC>(vf, vg, a.p) * dt;
                 gvg += w * bw_dh<METRIC>(vg, vf, a.p) * dt;
-                if (adv_f) tgf = bw_h<METRIC>(vf, vg, a.p) - bw_h<METRIC>(nf.y, vg, a.p);
-                if (adv_g) tgg = bw_h<METRIC>(vg, vf, a.p) - bw_h<METRIC>(ng.y, vf, a.p);
             }
-            if (adv_f) {
-                atomicAdd(&a.gv[of + kf], gvf);
-                gvf = 0.0;
-                atomicAdd(&a.gt[of + kf + 1], w * tgf);
-                ++kf;
-                ef = nf;
-            }
-            if (adv_g) {
+            // h(v_old, other) - h(v_new, other) for the advancing side
+            auto tgrad = [&](double vo, double vn, double ot) -> double {
+                if constexpr (METRIC == PCF_L2) { const double bb = vn - ot; return fma(d, d, -(bb * bb)); }
+                else if constexpr (METRIC == PCF_GRAM) return (vo - vn) * ot;
+                else if constexpr (METRIC == PCF_L1) return fabs(d) - fabs(vn - ot);
+                else return bw_h<METRIC>(vo, ot, a.p) - bw_h<METRIC>(vn, ot, a.p);
+            };
+            atomicAdd(&a.gv[at], sf ? gvf : gvg);
+            atomicAdd(&a.gt[at + 1], w * tgrad(v_old, nx.y, other));
+            if (sf) { gvf = 0.0; ++kf; ef = nx; } else { gvg = 0.0; ++kg; eg = nx; }
+            if (tie) {
+                // shared breakpoint: g advances too, against f's value before it
+                const double2 ng = a.pack[og + kg + 1];
                 atomicAdd(&a.gv[og + kg], gvg);
+                atomicAdd(&a.gt[og + kg + 1], w * tgrad(vg, ng.y, vf));
                 gvg = 0.0;
-                atomicAdd(&a.gt[og + kg + 1], w * tgg);
                 ++kg;
                 eg = ng;
             }
