@@ -284,7 +284,7 @@ struct SegCheck {
 };
 
 template <typename Tin, typename T, int FN, bool VEC, bool CLIP>
-__global__ void __launch_bounds__(kSegThreads, sizeof(Tin) == 4 && sizeof(T) == 4 ? 3 : 2) segment_kernel(const SegArgs<Tin, T> g)
+__global__ void __launch_bounds__(kSegThreads, sizeof(Tin) == 4 && sizeof(T) == 4 ? 4 : 2) segment_kernel(const SegArgs<Tin, T> g)
 {
     using Sum = SegSum<T>;
     constexpr int N = seg_items<Tin>();
