@@ -33,6 +33,10 @@ sys.path.insert(0, ROOT)
 from paper_2404_07183_gb300 import synth  # noqa: E402
 
 METRICS = ["l1", "l2", "gram"]
+# the headline metric and workload, shared by both arms of the benchmark
+HEADLINE_METRIC = ("pair-integrals/s and merge-steps/s at 1 GB300 (FP32-comp vs FP64), "
+                   "% issue roofline")
+HEADLINE_WORKLOAD = "stable_rank N=20000 n~U{50..500} Exp(0.1) gaps, L1+L2+Gram fused"
 # Algorithmic operations per merge step (frozen tally, see the design notes):
 # common part 5 (compare, select rectangle end, dt, fetch, advance) + d = a-b 1
 # L1 |d|*dt fma 1, L2 d*d + fma 2, Gram a*b + fma 2; compensated (Kahan): each
@@ -180,12 +184,14 @@ def run_reference(args):
     elapsed = sum(times)
     value = total_pairs / elapsed
     line = {
-        "impl": "reference", "metric": "pair-integrals/s (L1+L2+Gram) and merge-steps/s",
-        "value": value, "unit": "pair-integrals/s", "n_gpus": 0, "steps": args.steps,
+        "impl": "reference", "metric": HEADLINE_METRIC,
+        "value": value, "unit": "pair-integrals/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps,
-        "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "stable_rank N=20000 n~U{50..500} L1+L2+Gram",
-                   "sample": f"{rows_per_step} consecutive rows x 20000 columns per step"},
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": HEADLINE_WORKLOAD, "N": s.n, "nnz": s.nnz, "metrics": METRICS,
+                   "precision": "f64 (CPU oracle walk)",
+                   "sample": f"{rows_per_step} consecutive rows x {s.n} columns per step"},
         "cpu_baseline": {"value": value, "unit": "pair-integrals/s", "cores": cores,
                          "kind": "oracle",
                          "sample": f"{rows_per_step} rows x {s.n} cols x 3 metrics per step"},
@@ -375,12 +381,12 @@ def run_ours(args):
     walk_rate = walk_steps / (head["walk_ms"] * 1e-3)
     issue_peak = sms * 128 * fmax / TALLY[prec]
     line = {
-        "metric": "pair-integrals/s and merge-steps/s at 1 GB300 (FP32-comp vs FP64), % issue roofline",
+        "metric": HEADLINE_METRIC,
         "value": value, "unit": "pair-integrals/s", "n_gpus": world, "steps": head["steps"],
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (compensated)",
         "data": "synthetic",
-        "config": {"workload": "stable_rank N=20000 n~U{50..500} Exp(0.1) gaps, L1+L2+Gram fused",
+        "config": {"workload": HEADLINE_WORKLOAD,
                    "N": N, "nnz": s.nnz, "metrics": METRICS, "precision": prec,
                    "layout": "full N x N", "out_dtype": "f32",
                    "pair_integrals_per_step": pairs, "merge_steps_per_step": walk_steps + diag_steps,
