@@ -529,14 +529,19 @@ def run_workload(name, args):
         x = P.PcfTensors.from_numpy(s, dev)
         pairs = N * (N - 1) // 2
         out = {}
+        tuned = {}
+        from paper_2404_07183_gb300 import autotune
         for prec in ("f64", "f32c"):
             o = [torch.empty((N, N), dtype=torch.float64, device=dev)]
             ws = torch.empty(P.pcf_workspace_size(x, None, prec), dtype=torch.uint8, device=dev)
+            sched, timings = autotune.tune_pairwise(x, ["l1"], prec, out_dtype=torch.float64,
+                                                    repeats=3)
+            tuned[prec] = {"schedule": sched, "timings_ms": timings}
 
             def step():
                 P.pcf_prepare(x, prec, workspace=ws)
                 P.pcf_pairwise(x, ["l1"], precision=prec, out=o, workspace=ws, prepared=True,
-                               check=False)
+                               check=False, schedule=tuned[prec]["schedule"])
             step()
             P.pcf_check(ws)
             g = torch.cuda.CUDAGraph()
@@ -551,7 +556,7 @@ def run_workload(name, args):
                      "f64", {"workload": "uniform_small N=1000 n~U{10..100} Exp(1) N(0,1) "
                              "float64, L1 upper triangle", "N": N, "pairs": pairs,
                              "merge_steps": steps_walk, "cuda_graph": True,
-                             "l2": "flushed between steps"},
+                             "l2": "flushed between steps", "autotune": tuned},
                      merge_steps_per_s=rate,
                      roofline={"bound": "fp64 pipe", "achieved": rate, "peak": fp64(3),
                                "unit": "merge-steps/s", "frac": rate / fp64(3),
