@@ -218,3 +218,33 @@ def test_segments_chunk_and_batch_layouts(pcf, prec, dtype, aligned):
                 assert got[i] == want, (i, got[i], want)
             else:
                 assert abs(got[i] - want) <= tol * scale + 1e-30, (i, s.lengths()[i], got[i], want)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32c"])
+@pytest.mark.parametrize("lengths", [[16] * 1024, [4096] * 5 + [1] * 3, [8192] * 3 + [8191, 1],
+                                     [1] * 8192 + [16] * 512, [8193, 4095, 1, 16, 15, 17] * 3])
+def test_segments_boundaries_on_thread_round_chunk_edges(pcf, prec, lengths):
+    """PCF boundaries exactly on the 16-breakpoint thread ranges, the
+    4,096-breakpoint rounds and the 8,192-breakpoint chunks of the flat pass
+    (and one off), float32 data (vector loads)."""
+    rng = np.random.default_rng(sum(lengths) % 1000)
+    offs = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    t = np.empty(offs[-1]); v = np.empty(offs[-1])
+    for i, n in enumerate(lengths):
+        g = rng.exponential(1.0, n - 1)
+        t[offs[i]:offs[i + 1]] = np.concatenate([[0.0], np.cumsum(g)])
+        vv = rng.standard_normal(n)
+        vv[-1] = 0.0
+        v[offs[i]:offs[i + 1]] = vv
+    s = synth.PcfSet(offs, t, v).astype(np.float32)
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    tol = 1e-12 if prec == "f64" else 1e-5
+    for kind, p, root in (("lp", 2.0, True), ("integral", 1.0, False)):
+        got = pcf.pcf_segment_integrals(x, kind, p, root, precision=prec).cpu().numpy()
+        for i in range(s.n):
+            ti, vi = s.pcf(i)
+            want = oracle.segment_integral(ti, vi, kind, p)
+            scale = oracle.segment_integral(ti, vi, "lp", 1.0 if kind == "integral" else p)
+            if root:
+                want, scale = want ** (1.0 / p), scale ** (1.0 / p)
+            assert abs(got[i] - want) <= tol * scale + 1e-30, (i, lengths[i], got[i], want)
