@@ -15,14 +15,16 @@
 //  * segment_kernel: CTA c owns the PCFs that start in chunk c (table[c] ..
 //    table[c + 1] - 1) and integrates every segment of them, so the last one
 //    may run past the chunk's end; no two CTAs share a PCF and no CTA waits
-//    for another.  The owned elements are streamed in rounds of 2048 (256
-//    threads x 8 consecutive elements, 16-byte vector loads when the arrays
-//    are aligned).  Each thread integrates its elements in order and splits
-//    them into runs at PCF boundaries; a CTA-wide segmented scan of the runs'
-//    partial sums (warp shuffles, then one warp over the eight warp totals)
-//    carries a PCF's partial sum across threads and rounds, in a fixed order;
-//    the thread holding a PCF's last element finishes it (tail rule, root)
-//    and stores it.
+//    for another.  The owned elements are streamed in rounds of 256 threads
+//    x 16 consecutive float elements (8 double), with 16-byte vector loads
+//    when the arrays are aligned.  Each thread integrates its elements in
+//    order and splits them into runs at PCF starts (a bit mask built from
+//    the batch's offsets in shared memory); a CTA-wide segmented scan of the
+//    runs' partial sums (warp shuffles, then every warp over the eight warp
+//    totals, one barrier per round) carries a PCF's partial sum across
+//    threads and rounds in a fixed order.  A finished PCF's raw integral is
+//    parked in shared memory and the batch's PCFs are finished (tail rule,
+//    root) and stored together at the end of the batch.
 //  * The input check of pcf_pairwise runs on the same loads (same reasons,
 //    same indices; an offsets error found by the table pass stops the
 //    integration, element errors leave every element checked so the smallest
@@ -50,7 +52,10 @@ __device__ __forceinline__ T seg_h(T v, T p)
 constexpr int kSegThreads = 256;
 // consecutive elements per thread: 16 float (4 x 16-byte loads per array) or 8 double
 template <typename Tin> __host__ __device__ constexpr int seg_items() { return sizeof(Tin) == 4 ? 16 : 8; }
-constexpr int64_t kSegChunk = 8192;    // elements whose PCFs a CTA owns (2 or 4 rounds)
+// elements whose PCFs a CTA owns: 1.875 rounds of 4,096 (3.75 of 2,048), so the
+// chunk plus the overflow of its last PCF usually fits 2 (4) rounds instead
+// of spilling a few hundred elements into an extra round
+constexpr int64_t kSegChunk = 7680;
 constexpr int kSegBatch = 512;         // PCF offsets staged at a time
 
 // Partial sum of a run of segments with the head flag of the segmented scan:

@@ -163,7 +163,7 @@ def test_segments_full_size_sampled(pcf, prec):
 def _mixed_layout_set(seed):
     """Lengths chosen to cross every boundary of the flat pass: thousands of
     length-1 and length-2 PCFs (several staged batches of PCF offsets inside
-    one 8192-breakpoint chunk), PCFs of 20,000 and 41,000 breakpoints (many
+    one 7,680-breakpoint chunk), PCFs of 20,000 and 41,000 breakpoints (many
     rounds, several chunks, no PCF starting in some chunks), and random
     lengths with an odd total."""
     rng = np.random.default_rng(seed)
@@ -222,10 +222,11 @@ def test_segments_chunk_and_batch_layouts(pcf, prec, dtype, aligned):
 
 @pytest.mark.parametrize("prec", ["f64", "f32c"])
 @pytest.mark.parametrize("lengths", [[16] * 1024, [4096] * 5 + [1] * 3, [8192] * 3 + [8191, 1],
+                                     [7680] * 3 + [7679, 1], [3840] * 6 + [2048] * 3,
                                      [1] * 8192 + [16] * 512, [8193, 4095, 1, 16, 15, 17] * 3])
 def test_segments_boundaries_on_thread_round_chunk_edges(pcf, prec, lengths):
     """PCF boundaries exactly on the 16-breakpoint thread ranges, the
-    4,096-breakpoint rounds and the 8,192-breakpoint chunks of the flat pass
+    4,096-breakpoint rounds and the 7,680-breakpoint chunks of the flat pass
     (and one off), float32 data (vector loads)."""
     rng = np.random.default_rng(sum(lengths) % 1000)
     offs = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
