@@ -904,7 +904,16 @@ def main():
                  if args.workload == "all"
                  else [args.workload])
         for nm in names:
-            print(json.dumps(run_workload(nm, args)), flush=True)
+            # clocks sampled over the whole workload run (its timed steps are
+            # too short for the 200 ms sampling period alone)
+            clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_{nm}.csv")
+            os.makedirs(os.path.dirname(clk_path), exist_ok=True)
+            sampler, sfh = start_clock_sampler(clk_path)
+            d = run_workload(nm, args)
+            d["clocks"] = stop_clock_sampler(sampler, sfh, clk_path, 0) if sampler else None
+            if d["clocks"] is not None:
+                d["clocks"]["window"] = "whole workload run"
+            print(json.dumps(d), flush=True)
 
 
 if __name__ == "__main__":

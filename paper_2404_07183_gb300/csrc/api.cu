@@ -517,7 +517,9 @@ int pcf_segment_integrals(const pcf_csr* x, int functional, double p, int apply_
     init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
     if (x->n == 0) return cudaGetLastError() == cudaSuccess ? PCF_OK : PCF_ECUDA;
     // the input check runs inside the segment kernels (same reasons and indices)
-    // scratch: the chunk table (one int64 per 8192 breakpoints) in the packed area
+    // scratch in the packed area: the chunk table and the long-PCF pieces
+    // (60 bytes per chunk of 7,680 breakpoints, + 8; the area holds 16 per
+    // breakpoint and at least 256)
     if (launch_segments(x, functional, p, apply_root, a, b, precision, out, out_dtype == PCF_F64,
                         hdr, sv.packed, stream) != cudaSuccess)
         return PCF_ECUDA;

@@ -11,7 +11,8 @@
 // GPU design: one flat, element-balanced pass over the breakpoint arrays.
 //  * seg_table_kernel (thread per PCF) checks the offsets with the reasons and
 //    indices of pcf_pairwise's check and writes table[c] = number of PCFs that
-//    start before element c * kSegChunk, for every chunk c.
+//    start before element c * kSegChunk, for every chunk c, flagged when that
+//    PCF is long (more than kSegLong breakpoints).
 //  * segment_kernel: CTA c owns the PCFs that start in chunk c (table[c] ..
 //    table[c + 1] - 1) and integrates every segment of them, so the last one
 //    may run past the chunk's end; no two CTAs share a PCF and no CTA waits
@@ -25,6 +26,11 @@
 //    threads and rounds in a fixed order.  A finished PCF's raw integral is
 //    parked in shared memory and the batch's PCFs are finished (tail rule,
 //    root) and stored together at the end of the batch.
+//  * A long PCF (the last of its first chunk) is left out of that pass and
+//    split at the chunk edges into pieces; segment_piece_kernel, a second
+//    grid that starts while segment_kernel is still running, integrates each
+//    piece with one CTA, and the CTA that finishes a PCF's last piece sums
+//    the pieces' Kahan pairs in piece order (no CTA waits for another).
 //  * The input check of pcf_pairwise runs on the same loads (same reasons,
 //    same indices; an offsets error found by the table pass stops the
 //    integration, element errors leave every element checked so the smallest
@@ -57,6 +63,20 @@ template <typename Tin> __host__ __device__ constexpr int seg_items() { return s
 // of spilling a few hundred elements into an extra round
 constexpr int64_t kSegChunk = 7680;
 constexpr int kSegBatch = 512;         // PCF offsets staged at a time
+// PCFs longer than kSegLong breakpoints are not integrated by the CTA that
+// owns them but split into pieces of kSegChunk breakpoints, one CTA each,
+// whose Kahan partials a combine pass sums in piece order
+constexpr int64_t kSegLong = 4 * kSegChunk;
+// Chunk table entry: the PCF count in the low bits; kTabLong: the PCF before
+// the boundary (index count - 1) is longer than kSegLong; kTabCover: that
+// long PCF also covers the boundary's breakpoint (it ends after it).
+constexpr int64_t kTabLong = 1ll << 62;
+constexpr int64_t kTabCover = 1ll << 61;
+constexpr int64_t kTabCount = kTabCover - 1;
+
+// Partial integral of one piece of a long PCF: the Kahan pair (float64 form:
+// s only) and the sign of an infinite last segment (0 if none).
+struct SegPart { double s, c; int div; int pad; };
 
 // Partial sum of a run of segments with the head flag of the segmented scan:
 // flag = a PCF starts inside the run, so nothing before it is added.
@@ -88,6 +108,21 @@ template <> struct SegSum<double> {
         SegSum r;
         r.s = __shfl_sync(0xffffffffu, s, l);
         r.flag = __shfl_sync(0xffffffffu, flag, l);
+        return r;
+    }
+    __device__ __forceinline__ SegSum shfl_down(int o) const
+    {
+        SegSum r;
+        r.s = __shfl_down_sync(0xffffffffu, s, o);
+        r.flag = __shfl_down_sync(0xffffffffu, flag, o);
+        return r;
+    }
+    __device__ __forceinline__ void to_part(SegPart& p) const { p.s = s; p.c = 0.0; }
+    __device__ __forceinline__ static SegSum from_part(const SegPart* p)
+    {
+        SegSum r;
+        r.s = __ldcg(&p->s);
+        r.flag = 0;
         return r;
     }
 };
@@ -135,6 +170,24 @@ template <> struct SegSum<float> {
         r.flag = __shfl_sync(0xffffffffu, flag, l);
         return r;
     }
+    __device__ __forceinline__ SegSum shfl_down(int o) const
+    {
+        SegSum r;
+        r.s = __shfl_down_sync(0xffffffffu, s, o);
+        r.c = __shfl_down_sync(0xffffffffu, c, o);
+        r.flag = __shfl_down_sync(0xffffffffu, flag, o);
+        return r;
+    }
+    // a float pair is stored exactly in the float64 fields of a SegPart
+    __device__ __forceinline__ void to_part(SegPart& p) const { p.s = s; p.c = c; }
+    __device__ __forceinline__ static SegSum from_part(const SegPart* p)
+    {
+        SegSum r;
+        r.s = (float)__ldcg(&p->s);
+        r.c = (float)__ldcg(&p->c);
+        r.flag = 0;
+        return r;
+    }
 };
 
 template <typename T>
@@ -157,6 +210,9 @@ struct SegArgs {
     int apply_root;
     double p;                      // exponent of the functional (float64)
     T pw, lo, hi;                  // exponent and bounds in the arithmetic type
+    SegPart* part_start;           // [nchunks]: piece of the long PCF starting in chunk c
+    SegPart* part_cover;           // [nchunks]: piece of the long PCF covering chunk c's start
+    unsigned int* long_done;       // [nchunks]: pieces finished, by the long PCF's first chunk
     void* out;
     int out_f64;
     Header* hdr;
@@ -165,21 +221,28 @@ struct SegArgs {
 // Offsets check per PCF (the reasons and indices of pcf_pairwise's check)
 // and the chunk table: table[c] = #PCFs starting before element c * chunk.
 __global__ void seg_table_kernel(const int64_t* __restrict__ offsets, int64_t n, int64_t nnz,
-                                 int64_t nchunks, int64_t* __restrict__ table, Header* hdr)
+                                 int64_t nchunks, int64_t* __restrict__ table,
+                                 unsigned int* __restrict__ long_done, Header* hdr)
 {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i0 == 0) { table[0] = 0; table[nchunks] = n; }
+    if (i0 == 0) table[0] = 0;
+    for (int64_t c = i0; c < nchunks; c += stride) long_done[c] = 0u;   // pieces finished
     for (int64_t i = i0; i < n; i += stride) {
         const int64_t o0 = offsets[i], o1 = offsets[i + 1];
         bool bad = !(o0 >= 0 && o1 > o0 && o1 <= nnz && (o1 - o0) < (1ll << 31));
         if (i == 0 && o0 != 0) bad = true;
         if (i == n - 1 && o1 != nnz) bad = true;
         if (bad) { record_error(hdr, kErrOffsets, i); continue; }
-        // chunks c with o0 < c * chunk <= o1 see PCFs 0..i starting before them
+        const int64_t lng = o1 - o0 > kSegLong ? kTabLong : 0;
+        // chunks 0 < c < nchunks with o0 < c * chunk <= o1 see PCFs 0..i
+        // starting before them (exactly one i per c); the last PCF writes the
+        // end entry
         int64_t c1 = o1 / kSegChunk;
-        if (c1 > nchunks) c1 = nchunks;
-        for (int64_t c = o0 / kSegChunk + 1; c <= c1; ++c) table[c] = i + 1;
+        if (c1 > nchunks - 1) c1 = nchunks - 1;
+        for (int64_t c = o0 / kSegChunk + 1; c <= c1; ++c)
+            table[c] = (i + 1) | lng | (lng && c * kSegChunk < o1 ? kTabCover : 0);
+        if (i == n - 1) table[nchunks] = n | lng;
     }
 }
 
@@ -288,6 +351,173 @@ struct SegCheck {
     }
 };
 
+// Fixed-order sum of the 32 lanes' pairs into lane 0 (lane l before l + 1).
+template <typename T>
+__device__ __forceinline__ SegSum<T> seg_warp_sum(SegSum<T> acc)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const SegSum<T> other = acc.shfl_down(o);
+        if ((lane & (2 * o - 1)) == 0) acc = SegSum<T>::join(acc, other);
+    }
+    return acc;
+}
+
+// Breakpoints [ks, ke) of the long PCF with breakpoints o0 .. o1 - 1,
+// integrated by the whole CTA (N consecutive breakpoints per thread and
+// round, the threads' Kahan pairs summed in a fixed order), with the input
+// check of the main pass.  The result is valid in thread 0.
+template <typename Tin, typename T, int FN, bool VEC, bool CLIP>
+__device__ __forceinline__ SegPart seg_piece(const SegArgs<Tin, T>& g, int64_t o0, int64_t o1, int64_t ks,
+                             int64_t ke, SegSum<T>* red, int* red_div)
+{
+    using Sum = SegSum<T>;
+    constexpr int N = seg_items<Tin>();
+    constexpr int64_t kRound = (int64_t)kSegThreads * N;
+    constexpr bool R32 = sizeof(Tin) == 8 && sizeof(T) == 4;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    Sum acc = seg_identity<T>();
+    int div = 0;
+    SegCheck<Tin, T> chk;
+    bool bad = false;
+    const int64_t rb = ks - (ks % N);
+    for (int64_t k0 = rb + (int64_t)tid * N; k0 < ke; k0 += kRound) {
+        Tin tt[N], vv[N];
+        seg_load<Tin, VEC, N>(g.times, g.values, g.nnz, k0, tt, vv);
+        const Tin t_prev = k0 > 0 ? __ldg(g.times + k0 - 1) : Tin(0);
+        const Tin t_next = k0 + N < g.nnz ? __ldg(g.times + k0 + N) : Tin(INFINITY);
+#pragma unroll
+        for (int u = 0; u < N; ++u) {
+            const int64_t k = k0 + u;
+            if (k < ks || k >= ke) continue;
+            const Tin tk = tt[u], vk = vv[u];
+            const Tin tp = u > 0 ? tt[u - 1] : t_prev;
+            const Tin tn = u + 1 < N ? tt[u + 1] : t_next;
+            chk.value(tk, vk);
+            if (k == o0) bad |= tk != Tin(0);
+            else chk.order(tp, tk);
+            const T tkT = (T)tk, tnT = (T)tn;
+            const T h = seg_h<FN, T>((T)vk, g.pw);
+            if (k + 1 < o1) {
+                if (CLIP) {
+                    const T l = tkT > g.lo ? tkT : g.lo;
+                    const T rr = tnT < g.hi ? tnT : g.hi;
+                    if (rr > l) acc.add(h, rr - l);
+                } else {
+                    acc.add(h, tnT - tkT);
+                }
+            } else if (CLIP) {
+                // last segment [t_k, inf) clipped to [a, b]
+                const T l = tkT > g.lo ? tkT : g.lo;
+                if (g.hi > l) {
+                    if (isinf(g.hi)) {
+                        if (h != T(0)) div = h > T(0) ? 1 : -1;
+                    } else {
+                        acc.add(h, g.hi - l);
+                    }
+                }
+            } else if (h != T(0)) {
+                div = h > T(0) ? 1 : -1;
+            }
+        }
+    }
+    if (bad || chk.bad()) {
+        // exact report, as in the main pass
+        for (int64_t k0 = rb + (int64_t)tid * N; k0 < ke; k0 += kRound)
+            for (int u = 0; u < N; ++u) {
+                const int64_t k = k0 + u;
+                if (k < ks || k >= ke) continue;
+                const Tin tp = k > 0 ? __ldg(g.times + k - 1) : Tin(0);
+                seg_record<Tin, R32>(g.hdr, k, __ldg(g.times + k), __ldg(g.values + k), tp, k == o0);
+            }
+    }
+    acc = seg_warp_sum<T>(acc);
+    const int wdiv = __reduce_add_sync(0xffffffffu, div);   // one thread at most holds the end
+    if (lane == 0) { red[warp] = acc; red_div[warp] = wdiv; }
+    __syncthreads();
+    SegPart out{};
+    if (tid == 0) {
+        Sum tot = red[0];
+        int dv = red_div[0];
+        for (int w = 1; w < kSegThreads / 32; ++w) {
+            tot = Sum::join(tot, red[w]);
+            dv += red_div[w];
+        }
+        tot.to_part(out);
+        out.div = dv;
+    }
+    __syncthreads();
+    return out;
+}
+
+// Piece `slot` of the long PCF i has been integrated (result in thread 0):
+// store it; the CTA that finishes the PCF's last piece sums the pieces in
+// order (the piece in its first chunk, then the chunks it covers) with one
+// warp, applies the tail rule and the root, and stores the result.  No CTA
+// waits for another: the last one to count in does the combine.
+template <typename Tin, typename T>
+__device__ void seg_piece_done(const SegArgs<Tin, T>& g, int64_t i, SegPart* slot,
+                               const SegPart& part, int* s_last)
+{
+    using Sum = SegSum<T>;
+    const int64_t o0 = g.offsets[i], o1 = g.offsets[i + 1];
+    const int64_t c_s = o0 / kSegChunk, c_e = (o1 - 1) / kSegChunk;
+    const int npieces = (int)(c_e - c_s + 1);
+    if (threadIdx.x == 0) {
+        *slot = part;
+        __threadfence();
+        const unsigned done = atomicAdd(&g.long_done[c_s], 1u) + 1u;
+        *s_last = done == (unsigned)npieces;
+        __threadfence();
+    }
+    __syncthreads();
+    if (*s_last && threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        const int per = (npieces + 31) / 32;
+        Sum acc = seg_identity<T>();
+        int dv = 0;
+        for (int k = lane * per; k < npieces && k < (lane + 1) * per; ++k) {
+            const SegPart* pp = k == 0 ? &g.part_start[c_s] : &g.part_cover[c_s + k];
+            acc = Sum::join(acc, Sum::from_part(pp));
+            dv += __ldcg(&pp->div);
+        }
+        acc = seg_warp_sum<T>(acc);
+        dv = __reduce_add_sync(0xffffffffu, dv);
+        if (lane == 0)
+            seg_store(g.out, g.out_f64, i, seg_finish(acc.value(), dv != 0, (double)(dv > 0 ? 1 : -1),
+                                                      g.functional, g.apply_root, g.p));
+    }
+    __syncthreads();
+}
+
+// The pieces of long PCFs in chunk c (owned PCFs a .. b - 1): the part of
+// PCF a - 1 that covers the chunk's first breakpoint (cover) and the part of
+// PCF b - 1 that starts in the chunk (start), at most two.
+template <typename Tin, typename T, int FN, bool VEC, bool CLIP>
+__device__ __forceinline__ void seg_long_pieces(const SegArgs<Tin, T> g, int64_t c, int64_t a, int64_t b,
+                                             bool cover, bool start)
+{
+    __shared__ SegSum<T> red[kSegThreads / 32];
+    __shared__ int red_div[kSegThreads / 32];
+    __shared__ int s_last;
+    const int64_t cs0 = c * kSegChunk;
+    const int64_t cs1 = cs0 + kSegChunk < g.nnz ? cs0 + kSegChunk : g.nnz;
+    if (cover) {
+        const int64_t pc = a - 1;
+        const int64_t o0 = g.offsets[pc], o1 = g.offsets[pc + 1];
+        const SegPart part =
+            seg_piece<Tin, T, FN, VEC, CLIP>(g, o0, o1, cs0, o1 < cs1 ? o1 : cs1, red, red_div);
+        seg_piece_done<Tin, T>(g, pc, &g.part_cover[c], part, &s_last);
+    }
+    if (start) {
+        const int64_t ps = b - 1;
+        const int64_t o0 = g.offsets[ps], o1 = g.offsets[ps + 1];
+        const SegPart part = seg_piece<Tin, T, FN, VEC, CLIP>(g, o0, o1, o0, cs1, red, red_div);
+        seg_piece_done<Tin, T>(g, ps, &g.part_start[c], part, &s_last);
+    }
+}
+
 template <typename Tin, typename T, int FN, bool VEC, bool CLIP>
 __global__ void __launch_bounds__(kSegThreads, sizeof(Tin) == 4 && sizeof(T) == 4 ? 4 : 2) segment_kernel(const SegArgs<Tin, T> g)
 {
@@ -309,9 +539,14 @@ __global__ void __launch_bounds__(kSegThreads, sizeof(Tin) == 4 && sizeof(T) == 
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t c = blockIdx.x;
-    int64_t a = g.table[c], b = g.table[c + 1];
-    if (a < 0) a = 0;
+    const int64_t ta = g.table[c], tb = g.table[c + 1];
+    int64_t a = ta & kTabCount, b = tb & kTabCount;
     if (b > g.n) b = g.n;
+    if (a > b) a = b;
+    // the PCF starting in this chunk, if long (necessarily its last), is left
+    // to segment_piece_kernel, which may start now
+    if ((tb & kTabLong) != 0 && b > a) --b;
+    asm volatile("griddepcontrol.launch_dependents;");
 
     for (int64_t a0 = a; a0 < b; a0 += kSegBatch) {
         const int np = (int)((b - a0) < kSegBatch ? (b - a0) : kSegBatch);
@@ -494,18 +729,66 @@ __global__ void __launch_bounds__(kSegThreads, sizeof(Tin) == 4 && sizeof(T) == 
     }
 }
 
+// Long PCFs, piece by piece, in a second grid launched as a programmatic
+// dependent of segment_kernel: it needs only the chunk table, so it starts
+// once every segment_kernel CTA has started and runs in that kernel's tail.
+// CTA k looks at chunks k, k + grid, k + 2 grid, ... (the pieces of one long
+// PCF lie in consecutive chunks and so spread over the CTAs) and integrates
+// the pieces of the flagged ones.  Every CTA finally waits for segment_kernel
+// to complete, so this grid never completes before it.
+template <typename Tin, typename T, int FN, bool VEC, bool CLIP>
+__global__ void __launch_bounds__(kSegThreads, 2) segment_piece_kernel(const SegArgs<Tin, T> g,
+                                                                       int64_t nchunks)
+{
+    __shared__ int64_t list[kSegThreads];
+    __shared__ int list_n;
+    if (!__syncthreads_or(threadIdx.x == 0 && g.hdr->err < (1ull << 62))) {
+        const int64_t G = gridDim.x;
+        for (int64_t base = blockIdx.x; base < nchunks; base += G * kSegThreads) {
+            if (threadIdx.x == 0) list_n = 0;
+            __syncthreads();
+            const int64_t c = base + (int64_t)threadIdx.x * G;
+            if (c < nchunks) {
+                const int64_t ta = g.table[c], tb = g.table[c + 1];
+                if ((ta & kTabCover) || ((tb & kTabLong) && (tb & kTabCount) > (ta & kTabCount)))
+                    list[atomicAdd(&list_n, 1)] = c;
+            }
+            __syncthreads();
+            const int m = list_n;
+            for (int k = 0; k < m; ++k) {
+                const int64_t cc = list[k];
+                const int64_t ta = g.table[cc], tb = g.table[cc + 1];
+                const int64_t a = ta & kTabCount, b = tb & kTabCount;
+                seg_long_pieces<Tin, T, FN, VEC, CLIP>(g, cc, a, b, (ta & kTabCover) != 0,
+                                                       (tb & kTabLong) != 0 && b > a);
+            }
+            __syncthreads();   // the list is rewritten
+        }
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 cudaError_t launch_segments(const pcf_csr* x, int functional, double p, int apply_root,
                             double lo, double hi, int precision, void* out, int out_f64,
                             Header* hdr, void* scratch, cudaStream_t s)
 {
     if (x->n == 0) return cudaSuccess;
     const int64_t nchunks = (x->nnz + kSegChunk - 1) / kSegChunk;
-    int64_t* table = reinterpret_cast<int64_t*>(scratch);
+    // scratch: chunk table [nchunks + 1], the two piece arrays [nchunks] and
+    // the pieces-finished counters [nchunks]: 60 bytes per chunk of 7,680
+    // breakpoints (+ 8), within the 16 bytes per breakpoint (256 at least)
+    // the call's workspace provides
+    char* sp = reinterpret_cast<char*>(scratch);
+    int64_t* table = reinterpret_cast<int64_t*>(sp);
+    SegPart* part_start = reinterpret_cast<SegPart*>(sp + 8 * (nchunks + 1));
+    SegPart* part_cover = part_start + nchunks;
+    unsigned int* long_done = reinterpret_cast<unsigned int*>(part_cover + nchunks);
     {
-        int64_t blocks = (x->n + 255) / 256;
+        int64_t blocks = ((x->n > nchunks ? x->n : nchunks) + 255) / 256;
         const int64_t cap = (int64_t)device_sm_count() * 16;
         if (blocks > cap) blocks = cap;
-        seg_table_kernel<<<(int)blocks, 256, 0, s>>>(x->offsets, x->n, x->nnz, nchunks, table, hdr);
+        seg_table_kernel<<<(int)blocks, 256, 0, s>>>(x->offsets, x->n, x->nnz, nchunks, table,
+                                                      long_done, hdr);
     }
     if (nchunks == 0) return cudaGetLastError();
     const bool f32 = precision != PCF_PREC_F64;
@@ -513,16 +796,42 @@ cudaError_t launch_segments(const pcf_csr* x, int functional, double p, int appl
                    : p == 1.0 ? kFnAbs : p == 2.0 ? kFnSquare : p == 3.0 ? kFnCube : kFnPow;
     const bool vec = ((uintptr_t)x->times % 16 == 0) && ((uintptr_t)x->values % 16 == 0);
     const bool clip = lo > 0.0 || !std::isinf(hi);
+    // a PCF longer than kSegLong needs more than kSegLong breakpoints in all
+    const bool long_possible = x->nnz > kSegLong;
+    const unsigned pgrid =
+        (unsigned)(nchunks < 2 * (int64_t)device_sm_count() ? nchunks : 2 * device_sm_count());
+    cudaError_t e = cudaSuccess;
+    // programmatic dependent launch: the piece grid may start before
+    // segment_kernel completes (it reads nothing segment_kernel writes)
+    auto launch_pieces = [&](auto kernel, const auto& g) {
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(pgrid);
+        cfg.blockDim = dim3(kSegThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        return cudaLaunchKernelEx(&cfg, kernel, g, nchunks);
+    };
 #define PCF_SEG_GO(TIN, TW, FN)                                                                    \
     {                                                                                              \
         SegArgs<TIN, TW> g{x->offsets, (const TIN*)x->times, (const TIN*)x->values, x->n, x->nnz,  \
-                           table, functional, apply_root ? 1 : 0, p, (TW)p, (TW)lo, (TW)hi, out,   \
-                           out_f64, hdr};                                                          \
+                           table, functional, apply_root ? 1 : 0, p, (TW)p, (TW)lo, (TW)hi,        \
+                           part_start, part_cover, long_done, out, out_f64, hdr};                  \
         const unsigned grid = (unsigned)nchunks;                                                   \
         if (vec && clip) segment_kernel<TIN, TW, FN, true, true><<<grid, kSegThreads, 0, s>>>(g);  \
         else if (vec) segment_kernel<TIN, TW, FN, true, false><<<grid, kSegThreads, 0, s>>>(g);    \
         else if (clip) segment_kernel<TIN, TW, FN, false, true><<<grid, kSegThreads, 0, s>>>(g);   \
         else segment_kernel<TIN, TW, FN, false, false><<<grid, kSegThreads, 0, s>>>(g);            \
+        if (long_possible) {                                                                        \
+            if (vec && clip) e = launch_pieces(segment_piece_kernel<TIN, TW, FN, true, true>, g);   \
+            else if (vec) e = launch_pieces(segment_piece_kernel<TIN, TW, FN, true, false>, g);     \
+            else if (clip) e = launch_pieces(segment_piece_kernel<TIN, TW, FN, false, true>, g);    \
+            else e = launch_pieces(segment_piece_kernel<TIN, TW, FN, false, false>, g);             \
+        }                                                                                           \
     }
 #define PCF_SEG_LAUNCH(TIN, TW)                                                                    \
     switch (fn) {                                                                                  \
@@ -539,6 +848,7 @@ cudaError_t launch_segments(const pcf_csr* x, int functional, double p, int appl
     }
 #undef PCF_SEG_GO
 #undef PCF_SEG_LAUNCH
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

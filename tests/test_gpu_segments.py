@@ -93,7 +93,8 @@ def test_segments_reject_bad_arguments(pcf):
 
 @pytest.mark.parametrize("prec", ["f64", "f32c"])
 def test_segments_long_pcfs(pcf, prec):
-    """PCFs above 1024 breakpoints take the CTA-per-PCF path."""
+    """PCFs of 1,000 to 5,000 breakpoints among short ones: PCFs that run
+    past the end of the chunk that owns them."""
     a = synth.random_set(12, seed=105, min_len=1000, max_len=5000)
     b = synth.random_set(60, seed=106, min_len=1, max_len=200)
     s = synth.PcfSet(np.concatenate([b.offsets, b.offsets[-1] + a.offsets[1:]]),
@@ -249,3 +250,108 @@ def test_segments_boundaries_on_thread_round_chunk_edges(pcf, prec, lengths):
             if root:
                 want, scale = want ** (1.0 / p), scale ** (1.0 / p)
             assert abs(got[i] - want) <= tol * scale + 1e-30, (i, lengths[i], got[i], want)
+
+
+def _set_from_lengths(lengths, seed, dtype=np.float64):
+    """PCFs with the given lengths: times 0, g_1, g_1 + g_2, ... (gaps
+    uniform in [0.5, 1.5]), values N(0, 1) with the last one 0."""
+    rng = np.random.default_rng(seed)
+    offs = np.concatenate([[0], np.cumsum(lengths)]).astype(np.int64)
+    t = np.empty(offs[-1]); v = np.empty(offs[-1])
+    for i, n in enumerate(lengths):
+        t[offs[i]:offs[i + 1]] = np.concatenate([[0.0], np.cumsum(rng.uniform(0.5, 1.5, n - 1))])
+        vv = rng.standard_normal(n)
+        vv[-1] = 0.0
+        v[offs[i]:offs[i + 1]] = vv
+    return synth.PcfSet(offs, t, v).astype(dtype)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32c"])
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+@pytest.mark.parametrize("lengths", [
+    [5, 100_000, 7],                          # one long PCF, several chunks
+    [40_000, 35_000, 3, 61_441],              # long PCFs back to back (a chunk with two pieces)
+    [7680 - 17, 7680 * 5, 17, 7680 * 4 + 1],  # long PCFs starting / ending on chunk edges
+    [30_720, 30_721, 2],                      # at and just above the long threshold
+    [100, 7680 * 5 - 100],                    # long last PCF, breakpoint count a multiple of the chunk
+    [7680 * 5, 7680 * 5],                     # a long PCF ending exactly on a chunk edge
+    [31_000],                                 # a single long PCF
+])
+def test_segments_long_pcfs_split_into_pieces(pcf, prec, dtype, lengths):
+    """PCFs longer than four 7,680-breakpoint chunks are split at the chunk
+    edges, integrated one piece per CTA and combined in piece order."""
+    s = _set_from_lengths(lengths, seed=len(lengths) + sum(lengths) % 97, dtype=dtype)
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    tol = 1e-12 if prec == "f64" else 1e-5
+    for kind, p, root, ab in (("lp", 2.0, True, (0.0, np.inf)), ("integral", 1.0, False, (0.0, np.inf)),
+                              ("lp", 1.0, False, (2.5, 31_000.0))):
+        got = pcf.pcf_segment_integrals(x, kind, p, root, ab[0], ab[1], precision=prec).cpu().numpy()
+        for i in range(s.n):
+            ti, vi = s.pcf(i)
+            want = oracle.segment_integral(ti, vi, kind, p, ab[0], ab[1])
+            scale = oracle.segment_integral(ti, vi, "lp", 1.0 if kind == "integral" else p, ab[0], ab[1])
+            if root:
+                want, scale = want ** (1.0 / p), scale ** (1.0 / p)
+            assert abs(got[i] - want) <= tol * scale + 1e-30, (i, lengths[i], got[i], want)
+
+
+def test_segments_long_pcf_repeatable_and_error_report(pcf):
+    """The pieces of a long PCF are summed in a fixed order (same bits on a
+    second call); an invalid breakpoint in a later piece is reported as by
+    pcf_pairwise's check."""
+    s = _set_from_lengths([3, 90_000, 4], seed=5, dtype=np.float32)
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    a1 = pcf.pcf_segment_integrals(x, "lp", 2.0, True, precision="f32c").cpu().numpy()
+    a2 = pcf.pcf_segment_integrals(x, "lp", 2.0, True, precision="f32c").cpu().numpy()
+    np.testing.assert_array_equal(a1, a2)
+    t, v = s.times.copy(), s.values.copy()
+    k = int(s.offsets[1]) + 70_001            # in the tenth piece of the long PCF
+    v[k] = np.inf
+    t[k + 5] = t[k + 4]                       # and an order error after it
+    bad = pcf.PcfTensors.from_numpy(synth.PcfSet(s.offsets, t, v), "cuda")
+    with pytest.raises(pcf.PcfError) as e1:
+        pcf.pcf_segment_integrals(bad, "integral", precision="f32c")
+    with pytest.raises(pcf.PcfError) as e2:
+        pcf.pcf_pairwise(bad, ["l1"], precision="f32c")
+    assert (e1.value.detail, e1.value.index) == (e2.value.detail, e2.value.index) == (5, k)
+
+
+def test_segments_long_pcfs_in_cuda_graph(pcf):
+    """The piece grid is a programmatic dependent of the main pass; captured in
+    a CUDA graph and replayed with new contents, the results equal those of
+    direct calls bit for bit, for both functionals back to back."""
+    import torch
+    s = _set_from_lengths([5, 100_000, 7, 40_000, 300], seed=11, dtype=np.float32)
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    ws = torch.empty(pcf.pcf_workspace_size(x, None, "f64"), dtype=torch.uint8, device="cuda")
+    o1 = torch.empty(s.n, dtype=torch.float64, device="cuda")
+    o2 = torch.empty(s.n, dtype=torch.float64, device="cuda")
+
+    def step():
+        pcf.pcf_segment_integrals(x, "lp", 2.0, True, precision="f32c", out=o1, workspace=ws,
+                                  check=False)
+        pcf.pcf_segment_integrals(x, "integral", precision="f32c", out=o2, workspace=ws,
+                                  check=False)
+
+    step()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for vals in (s.values, -2.0 * s.values, s.values):
+        x.values.copy_(torch.from_numpy(np.ascontiguousarray(vals)))
+        g.replay()
+        torch.cuda.synchronize()
+        pcf.pcf_check(ws)
+        r1, r2 = o1.cpu().numpy(), o2.cpu().numpy()
+        step()
+        np.testing.assert_array_equal(r1, o1.cpu().numpy())
+        np.testing.assert_array_equal(r2, o2.cpu().numpy())
+        for i in range(s.n):
+            ti, vi = s.pcf(i)
+            vi = vals[s.offsets[i]:s.offsets[i + 1]].astype(np.float64)
+            want = oracle.segment_integral(ti, vi, "lp", 2.0) ** 0.5
+            assert abs(r1[i] - want) <= 1e-5 * want + 1e-30, (i, r1[i], want)
+            want = oracle.segment_integral(ti, vi, "integral", 1.0)
+            scale = oracle.segment_integral(ti, vi, "lp", 1.0)
+            assert abs(r2[i] - want) <= 1e-5 * scale + 1e-30, (i, r2[i], want)
