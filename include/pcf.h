@@ -229,6 +229,31 @@ int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precisi
                     cudaStream_t stream);
 
 /*
+ * FULL pairwise matrices (Sec. 3.1, as pcf_pairwise with PCF_OUT_FULL)
+ * streamed to host memory while they are computed.  The walk runs in bands
+ * of its tile order; when a band ends, the rows whose pairs are all written
+ * are copied by a copy kernel on copy_stream into host_out, while the next
+ * band is computed on stream.
+ *   F[k].out:    device N x N matrix of out_dtype (written as by pcf_pairwise).
+ *   host_out[k]: host N x N matrix of out_dtype, row-major, page-locked and
+ *                device-accessible (cudaHostAlloc, or cudaHostRegister'd);
+ *                caller-owned, written by the device until the call's work
+ *                on `stream` is complete.
+ *   nbands:      0 = 16; 1 = one walk, then one copy.  The first and last
+ *                bands are smaller than the others.
+ *   schedule:    as pcf_pairwise_ex (NULL = AUTO); no shards.
+ *   copy_stream: may equal stream (no overlap).  Work on `stream` enqueued
+ *                after this call starts after the last copy.
+ * Workspace as pcf_pairwise.  Returns PCF_OK, PCF_EINVAL (as pcf_pairwise,
+ * or a host_out pointer the device cannot address), PCF_ENOWS, PCF_ECUDA;
+ * data errors are reported by pcf_check.
+ */
+int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int precision,
+                         int out_dtype, const pcf_schedule* schedule, void* const* host_out,
+                         int nbands, void* workspace, size_t workspace_bytes,
+                         cudaStream_t stream, cudaStream_t copy_stream);
+
+/*
  * Cross matrices between rows [row_begin, row_end) of collection a and all of
  * collection b (the pairwise matrix of Sec. 3.1 taken between two sets).
  * Output k is a (row_end - row_begin) x b->n row-major block with leading

@@ -38,7 +38,7 @@ SYMBOLS = ("pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross", "pc
            "pcf_pairwise_ex", "pcf_cross_ex", "pcf_sort_order", "pcf_segment_integrals",
            "pcf_reduce_workspace_size", "pcf_reduce", "pcf_combine_workspace_size",
            "pcf_combine", "pcf_reduce_counters", "pcf_selftest_wait_timeout",
-           "pcf_pairwise_backward_ex")
+           "pcf_pairwise_backward_ex", "pcf_pairwise_to_host")
 PCF_RED_SUM, PCF_RED_MEAN, PCF_RED_MAX, PCF_RED_MIN, PCF_RED_STD = range(5)
 PCF_OP_ADD, PCF_OP_SUB, PCF_OP_MUL, PCF_OP_MAX, PCF_OP_MIN, PCF_OP_SQDIFF = range(6)
 PCF_FN_INTEGRAL, PCF_FN_LP = 0, 1
@@ -109,6 +109,8 @@ def load(build_if_missing: bool = False):
         lib.pcf_pairwise_ex.restype = I
         WIN = ctypes.POINTER(PcfWindow)
         lib.pcf_pairwise_ex.argtypes = [CSR, INT, I, I, I, I, I, SCH, WIN, P, SZ, P]
+        lib.pcf_pairwise_to_host.restype = I
+        lib.pcf_pairwise_to_host.argtypes = [CSR, INT, I, I, I, SCH, P, I, P, SZ, P, P]
         lib.pcf_cross_ex.restype = I
         lib.pcf_cross_ex.argtypes = [CSR, CSR, I64, I64, INT, I, I, I64, I, I, SCH, WIN, P, SZ, P]
         lib.pcf_segment_integrals.restype = I

@@ -346,6 +346,46 @@ def pcf_pairwise_backward(x: PcfTensors, metric, grad_out: torch.Tensor, fwd_out
     return gv, gt
 
 
+def pcf_pairwise_to_host(x: PcfTensors, metrics=("l1",), precision="f32c",
+                         out_dtype=torch.float32, host_out=None, out=None, bands=0,
+                         workspace=None, stream=None, copy_stream=None, check=True,
+                         schedule=None):
+    """FULL pairwise matrices (as ``pcf_pairwise``) streamed to page-locked
+    host memory while they are computed: the walk runs in bands, and the rows
+    a band completes are copied to ``host_out`` on ``copy_stream`` while the
+    next band runs.  ``out``: the device matrices (allocated if None);
+    ``bands``: 0 = the library's default.  Returns the host tensors."""
+    lib = abi.load()
+    if isinstance(metrics, (str, tuple)):
+        metrics = [metrics]
+    metrics = list(metrics)
+    n = x.n
+    dev = x.times.device
+    if out is None:
+        out = [torch.empty((n, n), dtype=out_dtype, device=dev) for _ in metrics]
+    if host_out is None:
+        host_out = [torch.empty((n, n), dtype=out[0].dtype).pin_memory() for _ in metrics]
+    for h, o in zip(host_out, out):
+        if not h.is_pinned() or h.dtype != o.dtype or h.numel() != n * n or not h.is_contiguous():
+            raise ValueError("host_out: contiguous page-locked N x N tensors of the output dtype")
+    ws = _workspace(pcf_workspace_size(x, None, precision), dev, workspace)
+    cx = x.csr()
+    req = _requests(metrics, out)
+    od = abi.PCF_F64 if out[0].dtype == torch.float64 else abi.PCF_F32
+    ptrs = (ctypes.c_void_p * len(metrics))(*[h.data_ptr() for h in host_out])
+    if copy_stream is None:
+        copy_stream = torch.cuda.Stream(dev)
+    rc = lib.pcf_pairwise_to_host(ctypes.byref(cx), req, len(metrics), _prec(precision), od,
+                                  _schedule(schedule), ptrs, int(bands),
+                                  ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                  _stream_handle(stream), ctypes.c_void_p(copy_stream.cuda_stream))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_pairwise_to_host")
+    if check:
+        pcf_check(ws, stream, "pcf_pairwise_to_host")
+    return host_out
+
+
 def pcf_cross_to_host(a: PcfTensors, b: PcfTensors, metrics=("l1",), precision="f32c",
                       block_rows=2048, out_dtype=torch.float32, host_out=None, schedule=None,
                       check=True):

@@ -43,7 +43,57 @@ __global__ void init_header_kernel(Header* h, int keep_set1)
     h->tiles = 0;
 }
 
-__global__ void reset_tiles_kernel(Header* h) { h->tiles = 0; }
+// The persistent walks take work units from h->tiles upward; starting the
+// counter at u0 makes a launch walk units u0 .. (its tile count) x units - 1.
+__global__ void reset_tiles_kernel(Header* h, unsigned long long u0) { h->tiles = u0; }
+
+// Rows of the FULL matrices whose pairs have all been written, copied from
+// the device matrices to page-locked host matrices (device-accessible
+// pointers): sorted positions s0 .. s1 - 1, i.e. original rows perm[s], each
+// row_bytes long.  A CTA copies one row at a time, 16 bytes per thread (4
+// when rows do not start on 16-byte boundaries).  128 threads at up to 32
+// registers: one warp per SM sub-partition fits beside three 512-thread walk
+// CTAs (40 registers), which leave 1,024 of each sub-partition's 16,384
+// registers free.  The grid covers half the SMs: stores to host memory in
+// flight on an SM slow the walk CTAs beside them, so the copy keeps about
+// 150 KB in flight, enough to hide it behind the walk (measured: more in
+// flight slowed the walk more than it sped the copy).
+struct RowCopy {
+    const char* src[PCF_MAX_INTEGRALS];
+    char* dst[PCF_MAX_INTEGRALS];
+    int n;
+};
+
+template <typename V>
+__device__ __forceinline__ void copy_row(const V* __restrict__ src, V* __restrict__ dst, int nv)
+{
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) dst[k] = __ldcs(src + k);
+}
+
+// After a data error the permutation was never written: nothing is copied
+// (pcf_check reports the error), and a row index outside [0, n) is skipped.
+__global__ void __launch_bounds__(128, 16) copy_rows_kernel(RowCopy rc, const int32_t* __restrict__ perm,
+                                                            int64_t n, int64_t s0, int64_t s1,
+                                                            int64_t row_bytes, int vec16,
+                                                            const Header* hdr)
+{
+    if (block_sees_error(hdr)) return;
+    for (int64_t s = s0 + blockIdx.x; s < s1; s += gridDim.x) {
+        const int64_t row = perm[s];
+        if (row < 0 || row >= n) continue;
+        const int64_t off = row * row_bytes;
+#pragma unroll
+        for (int m = 0; m < PCF_MAX_INTEGRALS; ++m) {   // static indices: no local copy
+            if (m >= rc.n) break;
+            if (vec16)
+                copy_row(reinterpret_cast<const int4*>(rc.src[m] + off),
+                         reinterpret_cast<int4*>(rc.dst[m] + off), (int)(row_bytes / 16));
+            else
+                copy_row(reinterpret_cast<const int*>(rc.src[m] + off),
+                         reinterpret_cast<int*>(rc.dst[m] + off), (int)(row_bytes / 4));
+        }
+    }
+}
 
 __global__ void zero_kernel(double* a, int64_t n)
 {
@@ -162,8 +212,11 @@ int check_window(const pcf_window* w)
     return PCF_OK;
 }
 
+// kernel_out: the schedule kernel the call resolves to (AUTO decided here).
+// unit0: first work unit (tile schedules; the launch ends at wa.ntiles).
 int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int elem_bytes,
-              const pcf_schedule* sched, const pcf_window* win, cudaStream_t s)
+              const pcf_schedule* sched, const pcf_window* win, cudaStream_t s,
+              int64_t unit0 = 0, int* kernel_out = nullptr)
 {
     const int sms = device_sm_count();
     wa.lo = win ? win->a : 0.0;
@@ -178,6 +231,8 @@ int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int el
         kernel = (wa.ntiles * 2 < sms && !windowed) ? PCF_SCHED_MERGEPATH : PCF_SCHED_TILE_1024;
     if (windowed && kernel == PCF_SCHED_MERGEPATH) return PCF_EUNSUPPORTED;
     if (weighted && kernel != PCF_SCHED_TILE_1024) return PCF_EUNSUPPORTED;
+    if (kernel_out) *kernel_out = kernel;
+    if (kernel == PCF_SCHED_MERGEPATH && unit0 != 0) return PCF_EINVAL;
 
     int64_t grid = 0;
     size_t smem = 0;
@@ -206,7 +261,7 @@ int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int el
         wa.window = W;
         smem = (size_t)regions * (size_t)W * kGroup * (size_t)elem_bytes;
         grid = (int64_t)sms * ctas;
-        const int64_t units = wa.ntiles * (half ? 2 : 1);
+        const int64_t units = wa.ntiles * (half ? 2 : 1) - unit0;
         if (grid > units) grid = units;
         if (grid < 1) return PCF_OK;
     }
@@ -219,7 +274,7 @@ int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int el
             wa.root[k] = f.apply_root ? 1 : 0;
             wa.p[k] = f.metric == PCF_LP ? f.p : (f.metric == PCF_L2 ? 2.0 : 1.0);
         }
-        reset_tiles_kernel<<<1, 1, 0, s>>>(wa.hdr);
+        reset_tiles_kernel<<<1, 1, 0, s>>>(wa.hdr, (unsigned long long)unit0);
         cudaError_t e;
         const int g = (int)grid;
         if (kernel == PCF_SCHED_MERGEPATH) {
@@ -251,6 +306,33 @@ int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int el
         if (e != cudaSuccess) return PCF_ECUDA;
     }
     return PCF_OK;
+}
+
+// Bands of the symmetric tile order for streaming a matrix to the host.  The
+// walk takes the tiles (bi, bj), bi <= bj, column by column from the last
+// column block (bj = NB - 1) down; once columns NB - 1 .. b are done, every
+// pair of the sorted blocks b .. NB - 1 has been written, so their rows are
+// final.  Returns the cumulative column counts 0 = M_0 < M_1 < ... = NB.
+// The first bands (the longest PCFs) and the last ones (whose rows are copied
+// after the walk ends) are a quarter and a half of the others.
+std::vector<int64_t> plan_bands(int64_t NB, int nbands)
+{
+    std::vector<int64_t> cuts{0};
+    int64_t left = NB;
+    auto take = [&](int64_t w) {
+        if (w > left) w = left;
+        if (w > 0) { cuts.push_back(cuts.back() + w); left -= w; }
+    };
+    if (nbands <= 1) { take(NB); return cuts; }
+    const int64_t B = (NB + nbands - 1) / nbands;
+    const int64_t q = B / 4 > 0 ? B / 4 : 1, h = B / 2 > 0 ? B / 2 : 1;
+    take(q);
+    take(h);
+    while (left > h + q) take(B < left - (h + q) ? B : left - (h + q));
+    take(h);
+    take(q);
+    take(left);
+    return cuts;
 }
 
 }  // namespace
@@ -354,6 +436,126 @@ int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precisi
     wa.out_f64 = out_dtype == PCF_F64;
     wa.ld_out = x->n;
     return run_walks(wa, F, nF, precision, es, schedule, window, stream);
+}
+
+int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int precision,
+                         int out_dtype, const pcf_schedule* schedule, void* const* host_out,
+                         int nbands, void* workspace, size_t workspace_bytes,
+                         cudaStream_t stream, cudaStream_t copy_stream)
+{
+    if (!csr_ok(x)) return PCF_EINVAL;
+    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32_BLOCK) return PCF_EINVAL;
+    if (out_dtype != PCF_F32 && out_dtype != PCF_F64) return PCF_EINVAL;
+    if (nbands < 0) return PCF_EINVAL;
+    if (check_schedule(schedule) != PCF_OK) return PCF_EINVAL;
+    if (schedule && schedule->shard_count > 1) return PCF_EINVAL;
+    int rc = check_requests(F, nF, x->n > 0);
+    if (rc != PCF_OK) return rc;
+    Header* hdr;
+    SetView sv;
+    rc = pairwise_common(x, precision, workspace, workspace_bytes, &hdr, &sv);
+    if (rc != PCF_OK) return rc;
+    if (x->n == 0) return PCF_OK;
+    if (!host_out) return PCF_EINVAL;
+    RowCopy cp;
+    memset(&cp, 0, sizeof cp);
+    cp.n = nF;
+    const int64_t N = x->n;
+    const int64_t row_bytes = N * (out_dtype == PCF_F64 ? 8 : 4);
+    bool vec16 = row_bytes % 16 == 0;
+    for (int k = 0; k < nF; ++k) {
+        void* dp = nullptr;
+        if (!host_out[k] || cudaHostGetDevicePointer(&dp, host_out[k], 0) != cudaSuccess || !dp) {
+            cudaGetLastError();   // the failed query's error is not sticky: clear it
+            return PCF_EINVAL;
+        }
+        cp.src[k] = reinterpret_cast<const char*>(F[k].out);
+        cp.dst[k] = reinterpret_cast<char*>(dp);
+        vec16 = vec16 && (uintptr_t)cp.src[k] % 16 == 0 && (uintptr_t)cp.dst[k] % 16 == 0;
+    }
+
+    init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
+    if (prepare_set(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz, true,
+                    precision == PCF_PREC_F64, hdr, sv, stream) != cudaSuccess)
+        return PCF_ECUDA;
+    WalkArgs wa;
+    memset(&wa, 0, sizeof wa);
+    wa.pack_r = wa.pack_c = sv.packed;
+    wa.poff_r = wa.poff_c = sv.poff;
+    wa.slen_r = wa.slen_c = sv.slen;
+    wa.perm_r = wa.perm_c = sv.perm;
+    wa.n_r = wa.n_c = N;
+    wa.nb_r = wa.nb_c = (N + kTile - 1) / kTile;
+    wa.ntiles = wa.nb_r * (wa.nb_r + 1) / 2;
+    wa.symmetric = 1;
+    wa.hdr = hdr;
+    wa.layout = PCF_OUT_FULL;
+    wa.out_f64 = out_dtype == PCF_F64;
+    wa.ld_out = N;
+    const int es = elem_bytes_for(precision);
+    const int sms = device_sm_count();
+    const bool two = copy_stream != stream;
+    // the walks run with the largest shared-memory carve-out; a CTA that asks
+    // for another split of L1 cannot join an SM they occupy
+    if (cudaFuncSetAttribute(copy_rows_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        return PCF_ECUDA;
+
+    // copies of sorted rows [s0, s1) once everything before on `stream` is done
+    auto copy_rows = [&](int64_t s0, int64_t s1) -> bool {
+        if (s1 <= s0) return true;
+        cudaStream_t cs = stream;
+        if (two) {
+            cudaEvent_t ev;
+            if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return false;
+            const bool ok = cudaEventRecord(ev, stream) == cudaSuccess &&
+                            cudaStreamWaitEvent(copy_stream, ev, 0) == cudaSuccess;
+            cudaEventDestroy(ev);
+            if (!ok) return false;
+            cs = copy_stream;
+        }
+        const int64_t cap = sms / 2 > 0 ? sms / 2 : 1;
+        const int64_t grid = (s1 - s0) < cap ? (s1 - s0) : cap;
+        copy_rows_kernel<<<(int)grid, 128, 0, cs>>>(cp, sv.perm, N, s0, s1, row_bytes, vec16 ? 1 : 0,
+                                                    hdr);
+        return cudaGetLastError() == cudaSuccess;
+    };
+
+    // the schedule, decided once for the whole matrix (a band alone is smaller)
+    pcf_schedule sch;
+    memset(&sch, 0, sizeof sch);
+    if (schedule) sch = *schedule;
+    if (sch.kernel == PCF_SCHED_AUTO)
+        sch.kernel = wa.ntiles * 2 < sms ? PCF_SCHED_MERGEPATH : PCF_SCHED_TILE_1024;
+    if (sch.kernel == PCF_SCHED_MERGEPATH || nbands == 1) {
+        rc = run_walks(wa, F, nF, precision, es, &sch, nullptr, stream);
+        if (rc != PCF_OK) return rc;
+        if (!copy_rows(0, N)) return PCF_ECUDA;
+    } else {
+        const int64_t units = (sch.kernel == PCF_SCHED_TILE_512X2 || sch.kernel == PCF_SCHED_TILE_512X3)
+                                  ? 2 : 1;
+        const int64_t NB = wa.nb_r;
+        auto first_tile = [&](int64_t m) { return m * NB - m * (m - 1) / 2; };
+        const std::vector<int64_t> cuts = plan_bands(NB, nbands == 0 ? 16 : nbands);
+        for (size_t k = 0; k + 1 < cuts.size(); ++k) {
+            const int64_t m0 = cuts[k], m1 = cuts[k + 1];
+            wa.ntiles = first_tile(m1);
+            rc = run_walks(wa, F, nF, precision, es, &sch, nullptr, stream, first_tile(m0) * units);
+            if (rc != PCF_OK) return rc;
+            const int64_t s0 = (NB - m1) * kTile;
+            const int64_t s1 = (NB - m0) * kTile < N ? (NB - m0) * kTile : N;
+            if (!copy_rows(s0, s1)) return PCF_ECUDA;
+        }
+    }
+    if (two) {   // `stream` continues after the last copy
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return PCF_ECUDA;
+        const bool ok = cudaEventRecord(ev, copy_stream) == cudaSuccess &&
+                        cudaStreamWaitEvent(stream, ev, 0) == cudaSuccess;
+        cudaEventDestroy(ev);
+        if (!ok) return PCF_ECUDA;
+    }
+    return cudaGetLastError() == cudaSuccess ? PCF_OK : PCF_ECUDA;
 }
 
 int pcf_cross(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row_end,

@@ -1,0 +1,102 @@
+"""Pairwise matrices streamed to page-locked host memory band by band
+(needs a GPU): the host copies equal the device matrices of pcf_pairwise bit
+for bit, for every band count and schedule, and match the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_07183_gb300 import synth
+
+from conftest import gpu_available, max_rel_error
+
+pytestmark = pytest.mark.gpu
+
+METRICS = ["l1", "l2", "gram"]
+
+
+@pytest.fixture(scope="module")
+def pcf():
+    if not gpu_available():
+        pytest.skip("no CUDA device")
+    import paper_2404_07183_gb300 as P
+    P.build.build()
+    return P
+
+
+@pytest.fixture(scope="module")
+def stable700(pcf):
+    s = synth.stable_rank(n_pcfs=700, seed=71)      # 22 blocks of 32, the last ragged
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    return s, x
+
+
+@pytest.mark.parametrize("schedule", [None, "tile512x3", "tile512x2", "tile1024"])
+@pytest.mark.parametrize("bands", [0, 1, 3, 7, 1000])
+def test_to_host_equals_device_matrices(pcf, stable700, schedule, bands):
+    import torch
+    s, x = stable700
+    want = pcf.pcf_pairwise(x, METRICS, precision="f32c", schedule=schedule)
+    got = pcf.pcf_pairwise_to_host(x, METRICS, precision="f32c", bands=bands, schedule=schedule)
+    for w, g in zip(want, got):
+        assert g.is_pinned() and g.device.type == "cpu"
+        np.testing.assert_array_equal(g.numpy(), w.cpu().numpy())
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32c"])
+def test_to_host_vs_oracle_float64_output(pcf, prec):
+    import torch
+    s = synth.random_set(150, seed=72, max_len=60)
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    got = pcf.pcf_pairwise_to_host(x, METRICS, precision=prec, out_dtype=torch.float64, bands=4)
+    tol = 1e-12 if prec == "f64" else 1e-5
+    for m, g in zip(METRICS, got):
+        want = oracle.matrix(s, metric=m)
+        diag = np.array([oracle.segment_sq(*s.pcf(i)) for i in range(s.n)]) if m == "gram" else None
+        assert max_rel_error(m, g.numpy(), want, diag) <= tol, m
+
+
+@pytest.mark.parametrize("n", [1, 5, 33, 64])
+def test_to_host_small_sets(pcf, n):
+    """Few tiles: AUTO takes the merge-path kernel (one walk, then one copy)."""
+    s = synth.random_set(n, seed=73 + n, max_len=40)
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    want = pcf.pcf_pairwise(x, METRICS, precision="f32c")
+    got = pcf.pcf_pairwise_to_host(x, METRICS, precision="f32c")
+    for w, g in zip(want, got):
+        np.testing.assert_array_equal(g.numpy(), w.cpu().numpy())
+
+
+def test_to_host_same_stream_and_given_buffers(pcf, stable700):
+    """copy_stream = the compute stream (no overlap) and caller buffers; a
+    second call overwrites them with the second set's matrices."""
+    import torch
+    s, x = stable700
+    s2 = synth.PcfSet(s.offsets, s.times * 0.5, s.values[::-1].copy())
+    x2 = pcf.PcfTensors.from_numpy(s2, "cuda")
+    host = [torch.empty((s.n, s.n), dtype=torch.float32).pin_memory() for _ in METRICS]
+    dev = [torch.empty((s.n, s.n), dtype=torch.float32, device="cuda") for _ in METRICS]
+    cur = torch.cuda.current_stream()
+    for xx in (x, x2):
+        pcf.pcf_pairwise_to_host(xx, METRICS, precision="f32c", host_out=host, out=dev,
+                                 bands=5, copy_stream=cur)
+        want = pcf.pcf_pairwise(xx, METRICS, precision="f32c")
+        for w, h in zip(want, host):
+            np.testing.assert_array_equal(h.numpy(), w.cpu().numpy())
+
+
+def test_to_host_rejects_pageable_buffers(pcf, stable700):
+    import torch
+    s, x = stable700
+    with pytest.raises(ValueError):
+        pcf.pcf_pairwise_to_host(x, ["l1"], host_out=[torch.empty((s.n, s.n))])
+
+
+def test_to_host_reports_invalid_input(pcf):
+    s = synth.random_set(100, seed=74, max_len=30)
+    t = s.times.copy()
+    k = int(s.offsets[40]) + 1
+    t[k] = t[k - 1]
+    x = pcf.PcfTensors.from_numpy(synth.PcfSet(s.offsets, t, s.values), "cuda")
+    with pytest.raises(pcf.PcfError) as e:
+        pcf.pcf_pairwise_to_host(x, ["l1"])
+    assert e.value.index == k
