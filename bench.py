@@ -204,11 +204,13 @@ def run_reference(args):
 def cpu_baseline(s, seconds_target=12.0):
     import oracle
     cores = len(os.sched_getaffinity(0))
-    rows = 8
+    oracle.matrix(s, metric="l1", rows=(1000, 1002), nthreads=cores)   # load + thread start
+    rows = 16
     t0 = time.perf_counter()
-    oracle.matrix(s, metric="l1", rows=(0, rows), nthreads=cores)
+    oracle.matrix(s, metric="l1", rows=(1000, 1000 + rows), nthreads=cores)
     dt = time.perf_counter() - t0
-    rows = int(max(8, min(s.n, rows * (seconds_target / 3.0) / max(dt, 1e-3))))
+    # three metrics of about seconds_target / 3 each, on the calibrated rows
+    rows = int(max(16, min(s.n - 1000, rows * (seconds_target / 3.0) / max(dt, 1e-3))))
     t0 = time.perf_counter()
     for m in METRICS:
         oracle.matrix(s, metric=m, rows=(1000, 1000 + rows), nthreads=cores)
