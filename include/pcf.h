@@ -231,9 +231,9 @@ int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precisi
 /*
  * FULL pairwise matrices (Sec. 3.1, as pcf_pairwise with PCF_OUT_FULL)
  * streamed to host memory while they are computed.  The walk runs in bands
- * of its tile order; when a band ends, the rows whose pairs are all written
- * are copied by a copy kernel on copy_stream into host_out, while the next
- * band is computed on stream.
+ * of row blocks of the length-sorted PCFs, shortest first; when a band ends,
+ * the rows whose pairs are all written are copied by a copy kernel on
+ * copy_stream into host_out, while the next band is computed on stream.
  *   F[k].out:    device N x N matrix of out_dtype (written as by pcf_pairwise).
  *   host_out[k]: host N x N matrix of out_dtype, row-major, page-locked and
  *                device-accessible (cudaHostAlloc, or cudaHostRegister'd);

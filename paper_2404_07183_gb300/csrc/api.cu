@@ -309,12 +309,17 @@ int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int el
 }
 
 // Bands of the symmetric tile order for streaming a matrix to the host.  The
-// walk takes the tiles (bi, bj), bi <= bj, column by column from the last
-// column block (bj = NB - 1) down; once columns NB - 1 .. b are done, every
-// pair of the sorted blocks b .. NB - 1 has been written, so their rows are
-// final.  Returns the cumulative column counts 0 = M_0 < M_1 < ... = NB.
-// The first bands (the longest PCFs) and the last ones (whose rows are copied
-// after the walk ends) are a quarter and a half of the others.
+// walk takes the tiles (bi, bj), bi <= bj, row block by row block from the
+// first (shortest PCFs) up (WalkArgs::tile_order = 1); once row blocks
+// 0 .. b are done, every pair of the sorted blocks 0 .. b has been written,
+// so their rows are final.  Rows then complete at a nearly even rate over
+// the walk (a row block's work, n_b (NB - b) + sum of the longer blocks, falls
+// only near the end), whereas the walk's default order (column blocks from
+// the longest down) finishes the shortest quarter of the rows in the last
+// few percent of the work, leaving their copies after the walk.  Returns the
+// cumulative row-block counts 0 = M_0 < M_1 < ... = NB.  The first bands
+// (copies start early) and the last ones (copied after the walk ends) are a
+// quarter and a half of the others.
 std::vector<int64_t> plan_bands(int64_t NB, int nbands)
 {
     std::vector<int64_t> cuts{0};
@@ -535,15 +540,17 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
         const int64_t units = (sch.kernel == PCF_SCHED_TILE_512X2 || sch.kernel == PCF_SCHED_TILE_512X3)
                                   ? 2 : 1;
         const int64_t NB = wa.nb_r;
+        // first tile of row block m in the row order (row block i holds NB - i tiles)
         auto first_tile = [&](int64_t m) { return m * NB - m * (m - 1) / 2; };
         const std::vector<int64_t> cuts = plan_bands(NB, nbands == 0 ? 16 : nbands);
+        wa.tile_order = 1;
         for (size_t k = 0; k + 1 < cuts.size(); ++k) {
             const int64_t m0 = cuts[k], m1 = cuts[k + 1];
             wa.ntiles = first_tile(m1);
             rc = run_walks(wa, F, nF, precision, es, &sch, nullptr, stream, first_tile(m0) * units);
             if (rc != PCF_OK) return rc;
-            const int64_t s0 = (NB - m1) * kTile;
-            const int64_t s1 = (NB - m0) * kTile < N ? (NB - m0) * kTile : N;
+            const int64_t s0 = m0 * kTile;
+            const int64_t s1 = m1 * kTile < N ? m1 * kTile : N;
             if (!copy_rows(s0, s1)) return PCF_ECUDA;
         }
     }

@@ -104,6 +104,9 @@ struct WalkArgs {
     int64_t nb_r, nb_c;      // tile blocks
     int64_t ntiles;
     int symmetric;           // pairwise: upper-triangle tiles, R == C
+    int tile_order;          // symmetric tile order: 0 = column blocks from the last
+                             // down, 1 = row blocks from the first up (each with its
+                             // longest partner first)
     int window;              // W: staged elements per PCF per window
     Header* hdr;
     // outputs

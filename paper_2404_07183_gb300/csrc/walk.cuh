@@ -247,8 +247,13 @@ __device__ __forceinline__ void decode_tile(const WalkArgs& a, int64_t t, int64_
         while (m > 0 && m * NB - m * (m - 1) / 2 > t) --m;
         while ((m + 1) * NB - (m + 1) * m / 2 <= t) ++m;
         const int64_t within = t - (m * NB - m * (m - 1) / 2);
-        bj = NB - 1 - m;
-        bi = bj - within;
+        if (a.tile_order) {          // row block m, columns NB - 1 down to m
+            bi = m;
+            bj = NB - 1 - within;
+        } else {                     // column block NB - 1 - m, rows down from it
+            bj = NB - 1 - m;
+            bi = bj - within;
+        }
     } else {
         const int64_t q = t / a.nb_c, r = t - q * a.nb_c;
         bi = a.nb_r - 1 - q;

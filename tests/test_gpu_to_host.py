@@ -100,3 +100,42 @@ def test_to_host_reports_invalid_input(pcf):
     with pytest.raises(pcf.PcfError) as e:
         pcf.pcf_pairwise_to_host(x, ["l1"])
     assert e.value.index == k
+
+
+def test_to_host_captured_in_cuda_graph(pcf, stable700):
+    """The banded walk and the copies on the second stream are captured in one
+    CUDA graph (the copy stream forks from and joins the capturing stream);
+    replays after new input contents give the matrices of direct calls."""
+    import torch
+    s, x = stable700
+    n = s.n
+    host = [torch.empty((n, n), dtype=torch.float32).pin_memory() for _ in METRICS]
+    dev = [torch.empty((n, n), dtype=torch.float32, device="cuda") for _ in METRICS]
+    ws = torch.empty(pcf.pcf_workspace_size(x, None, "f32c"), dtype=torch.uint8, device="cuda")
+    copy = torch.cuda.Stream()
+
+    def step():
+        pcf.pcf_pairwise_to_host(x, METRICS, precision="f32c", host_out=host, out=dev,
+                                 workspace=ws, bands=6, copy_stream=copy, check=False,
+                                 schedule="tile512x3")
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        step()
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step()
+    for vals in (-s.values, s.values * 0.25):
+        x.values.copy_(torch.from_numpy(np.ascontiguousarray(vals)))
+        for h in host:
+            h.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        pcf.pcf_check(ws)
+        want = pcf.pcf_pairwise(x, METRICS, precision="f32c", schedule="tile512x3")
+        for w, h in zip(want, host):
+            np.testing.assert_array_equal(h.numpy(), w.cpu().numpy())
+    x.values.copy_(torch.from_numpy(np.ascontiguousarray(s.values)))
