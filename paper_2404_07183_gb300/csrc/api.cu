@@ -532,10 +532,22 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
     if (schedule) sch = *schedule;
     if (sch.kernel == PCF_SCHED_AUTO)
         sch.kernel = wa.ntiles * 2 < sms ? PCF_SCHED_MERGEPATH : PCF_SCHED_TILE_1024;
+    // `stream` continues after the last copy enqueued, also when a later
+    // step fails (the caller may reuse the buffers after an error)
+    auto join = [&]() -> bool {
+        if (!two) return true;
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return false;
+        const bool ok = cudaEventRecord(ev, copy_stream) == cudaSuccess &&
+                        cudaStreamWaitEvent(stream, ev, 0) == cudaSuccess;
+        cudaEventDestroy(ev);
+        return ok;
+    };
+    auto fail = [&](int code) { join(); return code; };
     if (sch.kernel == PCF_SCHED_MERGEPATH || nbands == 1) {
         rc = run_walks(wa, F, nF, precision, es, &sch, nullptr, stream);
         if (rc != PCF_OK) return rc;
-        if (!copy_rows(0, N)) return PCF_ECUDA;
+        if (!copy_rows(0, N)) return fail(PCF_ECUDA);
     } else {
         const int64_t units = (sch.kernel == PCF_SCHED_TILE_512X2 || sch.kernel == PCF_SCHED_TILE_512X3)
                                   ? 2 : 1;
@@ -548,20 +560,13 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
             const int64_t m0 = cuts[k], m1 = cuts[k + 1];
             wa.ntiles = first_tile(m1);
             rc = run_walks(wa, F, nF, precision, es, &sch, nullptr, stream, first_tile(m0) * units);
-            if (rc != PCF_OK) return rc;
+            if (rc != PCF_OK) return fail(rc);
             const int64_t s0 = m0 * kTile;
             const int64_t s1 = m1 * kTile < N ? m1 * kTile : N;
-            if (!copy_rows(s0, s1)) return PCF_ECUDA;
+            if (!copy_rows(s0, s1)) return fail(PCF_ECUDA);
         }
     }
-    if (two) {   // `stream` continues after the last copy
-        cudaEvent_t ev;
-        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return PCF_ECUDA;
-        const bool ok = cudaEventRecord(ev, copy_stream) == cudaSuccess &&
-                        cudaStreamWaitEvent(stream, ev, 0) == cudaSuccess;
-        cudaEventDestroy(ev);
-        if (!ok) return PCF_ECUDA;
-    }
+    if (!join()) return PCF_ECUDA;
     return cudaGetLastError() == cudaSuccess ? PCF_OK : PCF_ECUDA;
 }
 

@@ -95,6 +95,29 @@ def test_argument_errors_return_before_any_device_work(lib):
                                      ctypes.c_void_p(0x1000), None, 0, s) == abi.PCF_EINVAL
 
 
+def test_to_host_argument_errors_return_before_any_device_work(lib):
+    x = _csr(10, 100)
+    req = (abi.PcfIntegral * 1)()
+    req[0].metric, req[0].p, req[0].out = abi.PCF_L1, 1.0, 0x2000
+    host = (ctypes.c_void_p * 1)(0x3000)
+    s = ctypes.c_void_p(0)
+    ws, wsb = ctypes.c_void_p(0x1000), 1 << 20
+    f = lib.pcf_pairwise_to_host
+    assert f(None, req, 1, 1, 0, None, host, 0, ws, wsb, s, s) == abi.PCF_EINVAL
+    assert f(ctypes.byref(x), req, 1, 9, 0, None, host, 0, ws, wsb, s, s) == abi.PCF_EINVAL
+    assert f(ctypes.byref(x), req, 1, 1, 5, None, host, 0, ws, wsb, s, s) == abi.PCF_EINVAL
+    assert f(ctypes.byref(x), req, 1, 1, 0, None, host, -1, ws, wsb, s, s) == abi.PCF_EINVAL
+    assert f(ctypes.byref(x), req, 0, 1, 0, None, host, 0, ws, wsb, s, s) == abi.PCF_EINVAL
+    sched = abi.PcfSchedule()
+    sched.shard_index, sched.shard_count = 0, 2      # no shards when streaming
+    assert f(ctypes.byref(x), req, 1, 1, 0, ctypes.byref(sched), host, 0, ws, wsb, s,
+             s) == abi.PCF_EINVAL
+    assert f(ctypes.byref(x), req, 1, 1, 0, None, host, 0, None, wsb, s, s) == abi.PCF_ENOWS
+    assert f(ctypes.byref(x), req, 1, 1, 0, None, None, 0, ws, wsb, s, s) == abi.PCF_EINVAL
+    empty = _csr(0, 0)
+    assert f(ctypes.byref(empty), req, 1, 1, 0, None, None, 0, ws, wsb, s, s) == abi.PCF_OK
+
+
 def test_empty_collection_is_a_no_op(lib):
     x = _csr(0, 0)
     req = (abi.PcfIntegral * 1)()
