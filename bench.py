@@ -23,6 +23,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -276,7 +277,7 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
         sampler, sfh = (None, None)
-        clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_{prec}_r{rank}.csv")
+        clk_path = os.path.join(tempfile.gettempdir(), f"pcf_bench_clocks_{prec}_r{rank}.csv")
         if prec == args.precision:
             os.makedirs(os.path.dirname(clk_path), exist_ok=True)
             sampler, sfh = start_clock_sampler(clk_path)
@@ -911,7 +912,7 @@ def main():
         for nm in names:
             # clocks sampled over the whole workload run (its timed steps are
             # too short for the 200 ms sampling period alone)
-            clk_path = os.path.join(ROOT, "gpurun_out", f"clocks_{nm}.csv")
+            clk_path = os.path.join(tempfile.gettempdir(), f"pcf_bench_clocks_{nm}.csv")
             os.makedirs(os.path.dirname(clk_path), exist_ok=True)
             sampler, sfh = start_clock_sampler(clk_path)
             d = run_workload(nm, args)
