@@ -506,6 +506,12 @@ def l2_kernel(x: PcfTensors, precision="f64", out_dtype=torch.float64):
     return pcf_pairwise(x, ["gram"], precision=precision, out_dtype=out_dtype)[0]
 
 
+# Short names of the two matrix calls (pairwise matrix of one collection,
+# cross matrix of two; Sec. 3.1)
+pairwise = pcf_pairwise
+cross = pcf_cross
+
+
 def _csr_out(n_out, capacity, device):
     off = torch.empty(n_out + 1, dtype=torch.int64, device=device)
     t = torch.empty(max(capacity, 1), dtype=torch.float64, device=device)
