@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import brute
 from paper_2404_07183_gb300 import synth
 
 from conftest import gpu_available, max_rel_error
@@ -139,3 +140,30 @@ def test_to_host_captured_in_cuda_graph(pcf, stable700):
         for w, h in zip(want, host):
             np.testing.assert_array_equal(h.numpy(), w.cpu().numpy())
     x.values.copy_(torch.from_numpy(np.ascontiguousarray(s.values)))
+
+
+def test_to_host_full_size_sampled(pcf):
+    """The benchmark's end-to-end configuration: N = 20,000 stable-rank PCFs,
+    L1 + L2 + Gram, the default 16 bands, three 512-thread CTAs per SM.
+    Sampled pairs against the oracle (the error measure of the device
+    matrices), and sampled rows of every band equal to the device matrices."""
+    import torch
+    s = synth.stable_rank()
+    n = s.n
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    dev = [torch.empty((n, n), dtype=torch.float32, device="cuda") for _ in METRICS]
+    host = pcf.pcf_pairwise_to_host(x, METRICS, precision="f32c", out=dev, schedule="tile512x3")
+    rng = np.random.default_rng(8)
+    ii, jj = rng.integers(0, n, 200), rng.integers(0, n, 200)
+    diag = {int(k): oracle.segment_sq(*s.pcf(int(k))) for k in np.concatenate([ii, jj])}
+    for m, h in zip(METRICS, host):
+        H = h.numpy()
+        p = {"l1": 1.0, "l2": 2.0, "gram": 1.0}[m]
+        for i, j in zip(ii, jj):
+            I = oracle.integral(*s.pcf(int(i)), *s.pcf(int(j)), m, p)
+            want = I if m == "gram" else brute.root(m, p, I)
+            scale = (np.sqrt(diag[int(i)] * diag[int(j)]) if m == "gram" else abs(want)) or 1.0
+            assert abs(float(H[i, j]) - want) / scale <= 1e-5, (m, i, j, H[i, j], want)
+    rows = np.sort(rng.choice(n, 64, replace=False))
+    for d, h in zip(dev, host):
+        np.testing.assert_array_equal(h.numpy()[rows], d[torch.from_numpy(rows).cuda()].cpu().numpy())
