@@ -320,7 +320,10 @@ int pcf_pairwise_backward_ex(const pcf_csr* x, int metric, double p, int apply_r
  * pcf_pairwise (pcf_check reports invalid data).  Workspace:
  * pcf_workspace_size(x, NULL, PCF_PREC_F64, PCF_WS_FORWARD).  precision:
  * PCF_PREC_F64 (float64 arithmetic) or PCF_PREC_F32_COMP (float32 arithmetic,
- * Kahan-compensated per segment; float64 input rounded to float32).
+ * Kahan-compensated per segment; float64 input rounded to float32).  PCFs of
+ * any length: one longer than 30,720 breakpoints is integrated in pieces by
+ * several CTAs whose partial sums are added in a fixed order, so repeated
+ * calls give the same bits.
  */
 int pcf_segment_integrals(const pcf_csr* x, int functional, double p, int apply_root,
                           double a, double b, int precision, void* out, int out_dtype,
