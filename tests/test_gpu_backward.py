@@ -1,6 +1,6 @@
 """Adjoint kernel vs the oracle adjoint (needs a GPU).
 
-Error measure per gradient array: max |g - g*| / max |g*| <= 1e-10 for random
+Error measure per gradient array: max |g - g*| / max |g*| <= 1e-12 for random
 inputs; bit-exact on dyadic inputs with shared breakpoints (every term is an
 exact small dyadic number, so the order of the float64 atomics cannot change
 the sums).
@@ -53,8 +53,8 @@ def test_backward_vs_oracle(pcf, metric, p, root):
                              out_dtype=torch.float64)[0]
     gv, gt = pcf.pcf_pairwise_backward(x, _spec(metric, p, root), Gt, fwd_out=F)
     ov, ot = oracle.backward(s, G, metric=metric, p=p, apply_root=root)
-    assert _rel(gv.cpu().numpy(), ov) <= 1e-10
-    assert _rel(gt.cpu().numpy(), ot) <= 1e-10
+    assert _rel(gv.cpu().numpy(), ov) <= 1e-12
+    assert _rel(gt.cpu().numpy(), ot) <= 1e-12
 
 
 @pytest.mark.parametrize("metric", ["l2", "gram", "l1"])
@@ -80,10 +80,10 @@ def test_autograd_function(pcf):
     loss = (torch.from_numpy(G).cuda() * F).sum()
     loss.backward()
     ov, ot = oracle.backward(s, G, metric="l2", p=2.0)
-    assert _rel(values.grad.cpu().numpy(), ov) <= 1e-10
-    assert _rel(times.grad.cpu().numpy(), ot) <= 1e-10
+    assert _rel(values.grad.cpu().numpy(), ov) <= 1e-12
+    assert _rel(times.grad.cpu().numpy(), ot) <= 1e-12
     want = float(np.sum(G * oracle.matrix(s, metric="l2", apply_root=False)))
-    assert abs(loss.item() - want) <= 1e-10 * abs(want)
+    assert abs(loss.item() - want) <= 1e-12 * abs(want)
 
 
 def test_gradient_workload_full_size_sampled(pcf):
@@ -112,8 +112,8 @@ def test_gradient_workload_full_size_sampled(pcf):
             acc_v += ov[:ti.size]
             acc_t += ot[:ti.size]
         a, b = int(s.offsets[i]), int(s.offsets[i + 1])
-        assert _rel(gv[a:b], acc_v) <= 1e-10
-        assert _rel(gt[a:b], acc_t) <= 1e-10
+        assert _rel(gv[a:b], acc_v) <= 1e-12
+        assert _rel(gt[a:b], acc_t) <= 1e-12
 
 
 @pytest.mark.parametrize("world", [2, 3])

@@ -83,8 +83,7 @@ def test_random_sets_vs_oracle(pcf, prec, m):
     want = _oracle(s, m)
     got = pcf.pcf_pairwise(_dev(pcf, s), [m], precision=prec, out_dtype=torch.float64)[0]
     err = max_rel_error(_metric_name(m), got.cpu().numpy(), want, _gram_diag(s))
-    tol = TOL[prec] * (20 if (_metric_name(m) == "lp" and prec != "f64") else 1)
-    assert err <= tol, (err, tol)
+    assert err <= TOL[prec], (err, TOL[prec])
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32c", "f32b"])
@@ -273,22 +272,6 @@ def _sampled_check(s, mats, metrics, prec, npairs, seed, layout="full", gram_dia
             else:
                 scale = abs(want) or 1.0
             assert abs(got - want) / scale <= TOL[prec], (name, i, j, got, want)
-
-
-@pytest.mark.parametrize("prec", ["f32c", "f32b", "f64"])
-def test_stable_rank_full_size_sampled(pcf, prec):
-    """N = 20,000 stable-rank-like PCFs, L1 + L2 + Gram in one fused walk."""
-    import torch
-    s = synth.stable_rank()
-    x = _dev(pcf, s)
-    mats = pcf.pcf_pairwise(x, ["l1", "l2", "gram"], precision=prec, out_dtype=torch.float32)
-    mats = [m.cpu().numpy() for m in mats]
-    diag = np.array([oracle.segment_sq(*s.pcf(i)) for i in range(s.n)])
-    _sampled_check(s, mats, ["l1", "l2", "gram"], "f32c", 300, 7,
-                   gram_diag=diag)
-    for M in mats[:2]:
-        assert np.all(np.diag(M) == 0)
-    np.testing.assert_allclose(np.diag(mats[2]), diag, rtol=1e-6)
 
 
 def test_lognormal_sampled_upper_packed(pcf):

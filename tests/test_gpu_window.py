@@ -79,8 +79,7 @@ def test_window_pairwise(pcf, prec, sched, win):
             np.testing.assert_array_equal(np.isinf(g), np.isinf(want))
             fin = np.isfinite(want)
             g, want = np.where(fin, g, 0.0), np.where(fin, want, 0.0)
-        tol = TOL[prec] * (20 if name == "lp" and prec != "f64" else 1)
-        assert _err(name, g, want, scale) <= tol, (name, _err(name, g, want, scale))
+        assert _err(name, g, want, scale) <= TOL[prec], (name, _err(name, g, want, scale))
 
 
 def test_window_dyadic_bitwise(pcf):
