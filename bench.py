@@ -46,6 +46,19 @@ TALLY = {"f32c": 5 + 1 + (1 + 3) + (2 + 3) + (2 + 3), "f32": 5 + 1 + 1 + 2 + 2,
          "f64": 5 + 1 + 1 + 2 + 2,
          # block-compensated: plain FMA terms + one 4-op Kahan add per metric per 16 steps
          "f32b": 5 + 1 + 1 + 2 + 2 + 3 * 4 / 16}
+# float64 input walked in float32 with exact comparisons (order keys): the
+# rectangle end is selected as hi and lo (one more select) and its width is
+# (hi_n - hi_c) + (lo_n - lo_c) (two more operations): common part 8 instead of 5
+KEYED_EXTRA = 3
+# float64 times rounded to float32 when packed (opt-in): the round-1 form
+for _p in ("f32c", "f32b", "f32"):
+    TALLY[_p + "_round"] = TALLY[_p]
+
+
+def tally(prec, input_f64=True):
+    """Operations per merge step of the walk a precision name runs on this input."""
+    keyed = input_f64 and prec in ("f32c", "f32b", "f32")
+    return TALLY[prec] + (KEYED_EXTRA if keyed else 0)
 FP64_OPS_PER_STEP = 1 + 1 + 1 + 2 + 2   # dt, d, L1 fma, L2 mul+fma, Gram mul+fma
 
 # DRAM bytes (read + write) per launch of the benchmark's compensated walk,
@@ -70,6 +83,39 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def resolve_launch(gpus, env, device_count):
+    """What to do with ``--gpus N`` in this process: ("run", world) when the
+    process is one of the N ranks (WORLD_SIZE == N under torchrun, or N == 1),
+    ("spawn", N) when N > 1 ranks must be started (no torchrun around us), or
+    ("error", message) when the launch cannot give N ranks on this node."""
+    world = int(env.get("WORLD_SIZE", "1"))
+    under_launcher = "RANK" in env and "WORLD_SIZE" in env
+    if gpus < 1:
+        return "error", f"--gpus {gpus}: need at least one GPU"
+    if under_launcher:
+        if world != gpus:
+            return "error", f"--gpus {gpus} but the launcher started WORLD_SIZE={world} ranks"
+        return "run", world
+    if gpus == 1:
+        return "run", 1
+    if device_count < gpus:
+        return "error", f"--gpus {gpus} but this node has {device_count} GPU(s)"
+    return "spawn", gpus
+
+
+def spawn_command(gpus, argv, port):
+    """torchrun command that starts ``gpus`` ranks of this script (one per GPU)."""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+            f"--nproc-per-node={gpus}", "--master-addr", "127.0.0.1", "--master-port", str(port),
+            os.path.abspath(__file__)] + list(argv)
+
+
+def split_value(pairs, step_ms_per_rank):
+    """Whole-matrix throughput of one matrix split over ranks: all of its
+    pairs over the slowest rank's step time (strong scaling)."""
+    return pairs / (max(step_ms_per_rank) * 1e-3)
 
 
 def exact_walk_steps(s):
@@ -202,24 +248,82 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline(s, seconds_target=15.0):
+SAMPLE_ROW0 = 1000        # first row of the oracle's timed sample (and of the error check)
+
+
+def cpu_baseline(s, seconds_target=15.0, max_rows=None):
+    """The oracle timed on a bounded row sample of the workload (all host
+    cores).  Returns (record, oracle rows per metric, Gram diagonal): the
+    sampled rows are also the reference of the per-matrix error check."""
     import oracle
     cores = len(os.sched_getaffinity(0))
-    oracle.matrix(s, metric="l1", rows=(1000, 1002), nthreads=cores)   # load + thread start
+    r0 = SAMPLE_ROW0
+    oracle.matrix(s, metric="l1", rows=(r0, r0 + 2), nthreads=cores)   # load + thread start
     rows = 16
     t0 = time.perf_counter()
-    oracle.matrix(s, metric="l1", rows=(1000, 1000 + rows), nthreads=cores)
+    oracle.matrix(s, metric="l1", rows=(r0, r0 + rows), nthreads=cores)
     dt = time.perf_counter() - t0
     # three metrics of about seconds_target / 3 each, on the calibrated rows
-    rows = int(max(16, min(s.n - 1000, rows * (seconds_target / 3.0) / max(dt, 1e-3))))
+    rows = int(max(16, min(s.n - r0, rows * (seconds_target / 3.0) / max(dt, 1e-3))))
+    if max_rows:
+        rows = min(rows, max_rows)
     t0 = time.perf_counter()
-    for m in METRICS:
-        oracle.matrix(s, metric=m, rows=(1000, 1000 + rows), nthreads=cores)
+    want = {m: oracle.matrix(s, metric=m, rows=(r0, r0 + rows), nthreads=cores) for m in METRICS}
     dt = time.perf_counter() - t0
-    return {"value": 3 * rows * s.n / dt, "unit": "pair-integrals/s", "cores": cores,
-            "kind": "oracle", "seconds": dt,
-            "sample": f"rows 1000..{1000 + rows} x all {s.n} columns, L1+L2+Gram, "
-                      "float64 oracle walk, one thread per core"}
+    diag = np.array([oracle.segment_sq(*s.pcf(i)) for i in range(s.n)])
+    rec = {"value": 3 * rows * s.n / dt, "unit": "pair-integrals/s", "cores": cores,
+           "kind": "oracle", "seconds": dt,
+           "sample": f"rows {r0}..{r0 + rows} x all {s.n} columns, L1+L2+Gram, "
+                     "float64 oracle walk, one thread per core"}
+    return rec, want, diag
+
+
+def matrix_errors(got, want, diag, r0):
+    """Per-matrix error of GPU rows against the oracle's rows: distances
+    max |x - x*| / |x*| (x* = 0 only on the diagonal, which must be exactly 0);
+    Gram max |x - x*| / sqrt(G*_ii G*_jj)."""
+    out = {}
+    for m in METRICS:
+        g = np.asarray(got[m], dtype=np.float64)
+        w = np.asarray(want[m], dtype=np.float64)
+        rows = g.shape[0]
+        if m == "gram":
+            d = np.sqrt(np.abs(diag))
+            scale = np.outer(d[r0:r0 + rows], d)
+            scale = np.where(scale > 0, scale, 1.0)
+            out[m] = float(np.max(np.abs(g - w) / scale))
+        else:
+            zero = w == 0
+            if np.any(g[zero] != 0):
+                out[m] = float("inf")
+                continue
+            out[m] = float(np.max(np.abs(g - w)[~zero] / np.abs(w[~zero])))
+    return out
+
+
+def _broadcast_set(s, local, world, rank):
+    """The collection on every rank: rank 0's arrays broadcast over NCCL (the
+    other ranks pass s = None)."""
+    import torch
+    import torch.distributed as dist
+    import paper_2404_07183_gb300 as P
+    dev = f"cuda:{local}"
+    if rank == 0:
+        x = P.PcfTensors.from_numpy(s, dev)
+        sizes = torch.tensor([x.n, x.nnz, 1 if x.times.dtype == torch.float64 else 0],
+                             dtype=torch.int64, device=dev)
+    else:
+        sizes = torch.zeros(3, dtype=torch.int64, device=dev)
+    dist.broadcast(sizes, 0)
+    n, nnz, f64 = (int(v) for v in sizes.tolist())
+    if rank != 0:
+        dt = torch.float64 if f64 else torch.float32
+        x = P.PcfTensors(torch.empty(n + 1, dtype=torch.int64, device=dev),
+                         torch.empty(nnz, dtype=dt, device=dev),
+                         torch.empty(nnz, dtype=dt, device=dev))
+    for t in (x.offsets, x.times, x.values):
+        dist.broadcast(t, 0)
+    return x
 
 
 def run_ours(args):
@@ -228,27 +332,37 @@ def run_ours(args):
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    split = world > 1 and not args.replicas
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     P.build.build()
 
-    s = workload(rank, args.n)
-    N = s.n
-    walk_steps, diag_steps = exact_walk_steps(s)
+    # split: one matrix over all ranks, broadcast from rank 0 (strong scaling);
+    # replicas: an independent batch per rank (weak scaling)
+    s = workload(0 if split else rank, args.n) if (rank == 0 or not split) else None
+    if split:
+        x = _broadcast_set(s, local, world, rank)
+    else:
+        x = P.PcfTensors.from_numpy(s, f"cuda:{local}")
+    N = x.n
+    shard = (rank, world) if split else None
+    walk_steps, diag_steps = exact_walk_steps(s) if s is not None else (0, 0)
     pairs = 2 * (N * (N - 1) // 2) + N * (N + 1) // 2      # distances i<j, Gram i<=j
-    x = P.PcfTensors.from_numpy(s, f"cuda:{local}")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
     stream = torch.cuda.current_stream()
+    check_rows = (SAMPLE_ROW0, min(N, SAMPLE_ROW0 + args.check_rows))
+    check = (world == 1 and not args.no_cpu and N > SAMPLE_ROW0)
 
     def make_outs():
         return [torch.empty((N, N), dtype=torch.float32, device=f"cuda:{local}") for _ in METRICS]
 
     results = {}
     tuned = {}
+    samples = {}
     forms = [args.precision]
     if not args.no_fp64:
-        forms += [f for f in ("f32b", "f64") if f != args.precision]
+        forms += [f for f in ("f32b", "f64", "f32c_round") if f != args.precision]
     for prec in forms:
         if args.schedule:
             sched = args.schedule
@@ -256,6 +370,11 @@ def run_ours(args):
             from paper_2404_07183_gb300 import autotune
             sched, timings = autotune.tune_pairwise(x, METRICS, prec, repeats=1)
             tuned[prec] = {"schedule": sched, "timings_ms": timings}
+            if split:
+                # every rank walks its shard with rank 0's choice
+                obj = [sched]
+                torch.distributed.broadcast_object_list(obj, 0)
+                sched = obj[0]
         outs = make_outs()
         ws = torch.empty(P.pcf_workspace_size(x, None, prec), dtype=torch.uint8,
                          device=f"cuda:{local}")
@@ -265,7 +384,7 @@ def run_ours(args):
             e_mid = torch.cuda.Event(enable_timing=True)
             e_mid.record(stream)
             P.pcf_pairwise(x, METRICS, precision=prec, out=outs, workspace=ws, prepared=True,
-                           check=False, schedule=sched, layout=args.layout)
+                           check=False, schedule=sched, layout=args.layout, shard=shard)
             return e_mid
 
         steps = args.steps if prec == args.precision else max(1, min(args.steps, 2))
@@ -292,6 +411,8 @@ def run_ours(args):
             e2.record(stream)
             evs.append((e0, e1, e2))
         torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
         t_wall = time.perf_counter() - t_wall
         clocks = stop_clock_sampler(sampler, sfh, clk_path, local) if sampler else None
         P.pcf_check(ws)
@@ -306,12 +427,15 @@ def run_ours(args):
                          "walk_ms": float(np.mean(walk_ms)),
                          "prepare_ms": float(np.mean([a.elapsed_time(b) for a, b, c in evs])),
                          "steps": steps, "wall_s": t_wall, "clocks": clocks}
+        if check and args.layout == "full":
+            r0, r1 = check_rows
+            samples[prec] = {m: o[r0:r1].double().cpu().numpy() for m, o in zip(METRICS, outs)}
         del outs, ws
 
     # same walk writing the matrices in the library's sort order (tiles land in
     # contiguous blocks instead of being scattered by the permutation)
     sorted_walk = None
-    if not args.no_fp64 and args.layout == "full":
+    if not args.no_fp64 and args.layout == "full" and world == 1:
         prec = args.precision
         outs_s = make_outs()
         ws_s = torch.empty(P.pcf_workspace_size(x, None, prec), dtype=torch.uint8,
@@ -329,13 +453,17 @@ def run_ours(args):
     if args.no_e2e:
         if rank == 0:
             print(json.dumps({"results": results, "N": N, "walk_steps": walk_steps}), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return
     # end-to-end through the public API with host buffers (pinned), every step:
-    # H2D of the CSR, the whole path with the three matrices streamed to the
-    # host band by band while the walk runs (pcf_pairwise_to_host)
+    # H2D of the CSR, the whole path, the matrices read back to the host.  One
+    # GPU: the three matrices streamed to the host band by band while the walk
+    # runs (pcf_pairwise_to_host).  A split matrix: each rank walks its shard
+    # and reads back its matrices (entries outside its shard are not its own).
     prec = args.precision
-    host_in = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-               for a in (s.offsets, s.times, s.values)]
+    host_in = [torch.from_numpy(np.ascontiguousarray(a.cpu().numpy())).pin_memory()
+               for a in (x.offsets, x.times, x.values)]
     host_out = [torch.empty((N, N), dtype=torch.float32).pin_memory() for _ in METRICS]
     dev_in = [torch.empty_like(h, device=f"cuda:{local}") for h in host_in]
     outs = make_outs()
@@ -354,14 +482,22 @@ def run_ours(args):
         ev[1].record()
         xd = P.PcfTensors(*dev_in)
         ev[2].record()
-        P.pcf_pairwise_to_host(xd, METRICS, precision=prec, out=outs, host_out=host_out,
-                               workspace=ws, check=False, schedule=results[prec]["schedule"],
-                               copy_stream=copy_stream)
+        if split:
+            P.pcf_pairwise(xd, METRICS, precision=prec, out=outs, workspace=ws, check=False,
+                           schedule=results[prec]["schedule"], shard=shard)
+            for h, o in zip(host_out, outs):
+                h.copy_(o, non_blocking=True)
+        else:
+            P.pcf_pairwise_to_host(xd, METRICS, precision=prec, out=outs, host_out=host_out,
+                                   workspace=ws, check=False, schedule=results[prec]["schedule"],
+                                   copy_stream=copy_stream)
         ev[3].record()
 
     for _ in range(2):
         e2e_step()
     torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
     e2e_steps = max(1, min(args.steps, 3))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
@@ -369,6 +505,10 @@ def run_ours(args):
         torch.cuda.synchronize()
         phases.append([ev[0].elapsed_time(ev[1]), ev[2].elapsed_time(ev[3])])
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device=f"cuda:{local}")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
     P.pcf_check(ws)
 
     if rank != 0:
@@ -381,45 +521,54 @@ def run_ours(args):
     sms = pp["sms"]
     fmax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
     head = results[prec]
-    value = world * pairs / (head["ms_per_step"] * 1e-3)
-    walk_rate = walk_steps / (head["walk_ms"] * 1e-3)
-    issue_peak = sms * 128 * fmax / TALLY[prec]
+    units = 1 if split else world           # matrices computed per step by the whole job
+    value = units * pairs / (head["ms_per_step"] * 1e-3)
+    walk_rate = walk_steps / (head["walk_ms"] * 1e-3) if not split else None
+    issue_peak = sms * 128 * fmax / tally(prec)
     line = {
         "metric": HEADLINE_METRIC,
         "value": value, "unit": "pair-integrals/s", "n_gpus": world, "steps": head["steps"],
         "warmup": args.warmup, "ms_per_step": head["ms_per_step"], "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (compensated)",
-        "data": "synthetic",
+        "scaling": "strong" if split else "weak", "vs_baseline": None,
+        "dtype": "f32 (compensated)", "data": "synthetic",
         "config": {"workload": HEADLINE_WORKLOAD,
-                   "N": N, "nnz": s.nnz, "metrics": METRICS, "precision": prec,
+                   "N": N, "nnz": x.nnz, "metrics": METRICS, "precision": prec,
+                   "comparisons": "exact in float64 (order keys ranked from the float64 times)"
+                                  if "round" not in prec else "on float32-rounded times",
                    "layout": "full N x N", "out_dtype": "f32",
-                   "pair_integrals_per_step": pairs, "merge_steps_per_step": walk_steps + diag_steps,
+                   "pair_integrals_per_step": units * pairs,
+                   "merge_steps_per_step": units * (walk_steps + diag_steps),
                    "l2": "flushed by a 256 MiB write before each timed step (outside the timing)",
-                   "parallelism": f"{world} independent replicas (one per GPU)",
+                   "parallelism": (f"one matrix split over {world} GPUs (strided 32x32 tile "
+                                   "shards, input broadcast from rank 0)" if split
+                                   else f"{world} independent replicas (one per GPU)"),
                    "schedule": head["schedule"], "autotune": tuned or None},
-        "merge_steps_per_s": world * (walk_steps + diag_steps) / (head["ms_per_step"] * 1e-3),
+        "merge_steps_per_s": units * (walk_steps + diag_steps) / (head["ms_per_step"] * 1e-3),
         "walk": {"ms": head["walk_ms"], "prepare_ms": head["prepare_ms"],
                  "merge_steps_per_s": walk_rate},
-        "roofline": {"bound": "alu", "achieved": walk_rate, "peak": issue_peak,
-                     "unit": "merge-steps/s", "frac": walk_rate / issue_peak,
-                     "traffic": (TRAFFIC_RECORD["by_schedule_layout"].get(
-                                     (head["schedule"], args.layout))
-                                 if (walk_source_id() == TRAFFIC_RECORD["source_sha256_16"]
-                                     and N == 20000) else None),
-                     "traffic_unit": "DRAM bytes per walk launch (ncu)",
-                     "peak_basis": f"{sms} SMs x 128 lanes x {fmax/1e6:.0f} MHz / {TALLY[prec]} "
-                                   "ops per merge step (fused L1+L2+Gram tally)"},
-        "gpu_launches": head["steps"] * (4 + 2),
-        "e2e": {"value": world * pairs / e2e_s, "unit": "pair-integrals/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+        "gpu_launches": head["steps"] * (4 + 2 + (23 if "round" not in prec else 0)),
+        "e2e": {"value": units * pairs / e2e_s, "unit": "pair-integrals/s",
+                "h2d_bytes_per_step": world * h2d, "d2h_bytes_per_step": world * d2h,
                 "ms_per_step": e2e_s * 1e3,
-                "phases_ms": dict(zip(("h2d", "prepare_walk_and_streamed_d2h"),
+                "phases_ms": dict(zip(("h2d", "prepare_walk_and_d2h"),
                                       np.mean(np.array(phases), axis=0).round(3).tolist())),
-                "d2h": "rows streamed to pinned host memory by a copy kernel on a second "
-                       "stream while later bands of the walk run"},
+                "d2h": ("rows streamed to pinned host memory by a copy kernel on a second "
+                        "stream while later bands of the walk run" if not split else
+                        "each rank reads back its whole matrices after its shard")},
         "pipe_peaks": pp,
         "clocks": head["clocks"],
     }
+    if walk_rate is not None:
+        line["roofline"] = {
+            "bound": "alu", "achieved": walk_rate, "peak": issue_peak,
+            "unit": "merge-steps/s", "frac": walk_rate / issue_peak,
+            "traffic": (TRAFFIC_RECORD["by_schedule_layout"].get((head["schedule"], args.layout))
+                        if (walk_source_id() == TRAFFIC_RECORD["source_sha256_16"]
+                            and N == 20000) else None),
+            "traffic_unit": "DRAM bytes per walk launch (ncu)",
+            "peak_basis": f"{sms} SMs x 128 lanes x {fmax/1e6:.0f} MHz / {tally(prec)} "
+                          "ops per merge step (fused L1+L2+Gram tally; exact float64 "
+                          "comparisons by order keys)"}
     if sorted_walk is not None:
         line["sorted_output"] = {"walk_ms": sorted_walk,
                                  "traffic": (TRAFFIC_RECORD["by_schedule_layout"].get(
@@ -429,33 +578,54 @@ def run_ours(args):
                                  "merge_steps_per_s": walk_steps / (sorted_walk * 1e-3),
                                  "note": "layout PCF_OUT_FULL_SORTED: same walk, matrices in "
                                          "the library's sort order (perm from pcf_sort_order)"}
-    if "f32b" in results and prec != "f32b":
-        f = results["f32b"]
+
+    def side(name, note, bound="alu"):
+        f = results[name]
         wr = walk_steps / (f["walk_ms"] * 1e-3)
-        pk = sms * 128 * fmax / TALLY["f32b"]
-        line["f32b"] = {"value": pairs / (f["ms_per_step"] * 1e-3), "unit": "pair-integrals/s",
-                        "ms_per_step": f["ms_per_step"], "walk_ms": f["walk_ms"],
-                        "merge_steps_per_s": wr, "schedule": f["schedule"],
-                        "roofline": {"bound": "alu", "achieved": wr, "peak": pk,
-                                     "unit": "merge-steps/s", "frac": wr / pk,
-                                     "peak_basis": f"tally {TALLY['f32b']} ops per merge step"},
-                        "note": "float32 walk, FMA block sums of <= 16 rectangles, Kahan across "
-                                "blocks (error <= ~18u sum|terms|)"}
-    if "f64" in results:
-        f = results["f64"]
-        r64 = pp["fp64"]["lane_ops_per_clk_per_sm"]
-        fp64_peak = sms * r64 * fmax / FP64_OPS_PER_STEP
-        wr = walk_steps / (f["walk_ms"] * 1e-3)
-        line["fp64"] = {"value": pairs / (f["ms_per_step"] * 1e-3), "unit": "pair-integrals/s",
-                        "ms_per_step": f["ms_per_step"], "walk_ms": f["walk_ms"],
-                        "merge_steps_per_s": wr,
-                        "roofline": {"bound": "fp64 pipe", "achieved": wr, "peak": fp64_peak,
-                                     "unit": "merge-steps/s", "frac": wr / fp64_peak,
-                                     "peak_basis": f"{sms} SMs x {r64:.2f} FP64 lane-ops/clk x "
-                                                   f"{fmax/1e6:.0f} MHz / {FP64_OPS_PER_STEP} FP64 "
-                                                   "ops per step"}}
-    if not args.no_cpu:
-        line["cpu_baseline"] = cpu_baseline(s)
+        if bound == "alu":
+            pk = sms * 128 * fmax / tally(name)
+            basis = f"tally {tally(name)} ops per merge step"
+        else:
+            r64 = pp["fp64"]["lane_ops_per_clk_per_sm"]
+            pk = sms * r64 * fmax / FP64_OPS_PER_STEP
+            basis = (f"{sms} SMs x {r64:.2f} FP64 lane-ops/clk x {fmax/1e6:.0f} MHz / "
+                     f"{FP64_OPS_PER_STEP} FP64 ops per step")
+        d = {"value": units * pairs / (f["ms_per_step"] * 1e-3), "unit": "pair-integrals/s",
+             "ms_per_step": f["ms_per_step"], "walk_ms": f["walk_ms"], "prepare_ms": f["prepare_ms"],
+             "merge_steps_per_s": wr, "schedule": f["schedule"],
+             "roofline": {"bound": bound, "achieved": wr, "peak": pk, "unit": "merge-steps/s",
+                          "frac": wr / pk, "peak_basis": basis}}
+        if note:
+            d["note"] = note
+        return d
+
+    if not split:
+        if "f32b" in results and prec != "f32b":
+            line["f32b"] = side("f32b", "float32 walk, FMA block sums of <= 16 rectangles, Kahan "
+                                        "across blocks (error <= ~18u sum|terms|)")
+        if "f32c_round" in results and prec != "f32c_round":
+            line["f32c_round"] = side("f32c_round", "opt-in PCF_PREC_ROUND_TIMES: float64 times "
+                                                    "rounded to float32 when packed (8-byte "
+                                                    "elements; comparisons and widths on the "
+                                                    "rounded times)")
+        if "f64" in results:
+            line["fp64"] = side("f64", None, bound="fp64 pipe")
+    if not args.no_cpu and world == 1:
+        rec, want, diag = cpu_baseline(s)
+        line["cpu_baseline"] = rec
+        if samples:
+            nrows = min(want["l1"].shape[0], check_rows[1] - check_rows[0])
+            err = {}
+            for name, got in samples.items():
+                err[name] = matrix_errors({m: got[m][:nrows] for m in METRICS},
+                                          {m: want[m][:nrows] for m in METRICS}, diag,
+                                          SAMPLE_ROW0)
+            line["error"] = {
+                "vs": "float64 oracle walk", "rows": f"{SAMPLE_ROW0}..{SAMPLE_ROW0 + nrows} x all "
+                                                    f"{N} columns",
+                "measure": "distances max |x - x*| / |x*|; Gram max |x - x*| / sqrt(G*_ii G*_jj)",
+                "output_dtype": "float32 (its rounding, <= 6e-8, is included)",
+                "by_form": err}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -882,13 +1052,19 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="f32c", choices=["f32c", "f32b", "f32", "f64"])
+    ap.add_argument("--precision", default="f32c",
+                    choices=["f32c", "f32b", "f32", "f64", "f32c_round", "f32b_round", "f32_round"])
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--ref-rows", type=int, default=48)
     ap.add_argument("--n", type=int, default=None,
                     help="smaller stable-rank collection (profiling runs); default 20000")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--replicas", action="store_true",
+                    help="with several GPUs: an independent batch per GPU (weak scaling) "
+                         "instead of one matrix split over them")
+    ap.add_argument("--check-rows", type=int, default=256,
+                    help="rows of every form's matrices compared with the oracle's")
     ap.add_argument("--layout", default="full", choices=["full", "sorted"],
                     help="output layout of the timed walk (profiling runs)")
     ap.add_argument("--schedule", default=None,
@@ -900,6 +1076,19 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    try:
+        import torch
+        ndev = torch.cuda.device_count()
+    except Exception:
+        ndev = 0
+    action, what = resolve_launch(args.gpus, os.environ, ndev)
+    if action == "error":
+        print(json.dumps({"error": what}), flush=True)
+        sys.exit(2)
+    if action == "spawn":
+        import random
+        cmd = spawn_command(what, sys.argv[1:], 29500 + random.randrange(1000))
+        sys.exit(subprocess.call(cmd))
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "stable_rank":

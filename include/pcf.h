@@ -19,6 +19,9 @@
  *  - All array pointers are DEVICE pointers owned by the caller.  The library
  *    allocates nothing and keeps no state between calls; scratch memory is the
  *    caller's `workspace` (size from pcf_workspace_size, 256-byte aligned).
+ *    The one exception is pcf_pairwise_noalloc (at the end of this header):
+ *    its scratch is a fixed device array inside the library, and it caches
+ *    that array's device address per device.
  *  - Work is enqueued on `stream` and returns without synchronizing.  The
  *    return value reports argument errors found on the host.  Problems that
  *    can only be seen in device data (an invalid PCF) are recorded in the
@@ -64,7 +67,7 @@ enum pcf_metric {
     PCF_GRAM = 3   /* h = a*b,      r = id (L2 inner product / Gram matrix)     */
 };
 
-/* Arithmetic of the walk.  Breakpoint comparisons are exact in the walk type. */
+/* Arithmetic of the walk.  Breakpoint comparisons are exact in the input type. */
 enum pcf_precision {
     PCF_PREC_F64 = 0,      /* float64 walk and accumulation                     */
     PCF_PREC_F32_COMP = 1, /* float32 walk, every rectangle's term added by Kahan's
@@ -77,9 +80,29 @@ enum pcf_precision {
                               18u * sum|terms| (a fraction of the work of
                               PCF_PREC_F32_COMP)                               */
 };
-/* float64 input walked in a float32 precision is rounded to nearest float32
- * when packed (times keep their order; times that round together become one
- * breakpoint of both PCFs).  The p-th root is always taken in float64. */
+/* float64 input walked in a float32 precision keeps every comparison of the
+ * walk exact in float64 (Alg. 1 decides which interval ends first, and ties,
+ * on the input's times): each interval end gets a 32-bit order key, its rank
+ * among the call's interval ends from a device-wide sort of their float64
+ * values, and the walk compares keys.  Each rectangle's width is formed from
+ * the difference of its ends, each time carried as float32 hi + lo (about 48
+ * significant bits), so distinct breakpoints closer than one float32 ulp stay
+ * distinct and a width w ending at time t is exact to about u*w + 2^-48*t
+ * instead of u*t.  Inputs whose widths must be resolved beyond that (gaps
+ * below about 1e-9 relative to their times) need PCF_PREC_F64.  Values are
+ * rounded to float32
+ * (the walk's arithmetic).  Such a call needs nnz (both collections together
+ * for a cross call) below 2^31, else PCF_EUNSUPPORTED.  The p-th root is
+ * always taken in float64.
+ *
+ * PCF_PREC_ROUND_TIMES, or-ed into a float32 precision, asks for the faster
+ * packed form instead: float64 times rounded to nearest float32 when packed
+ * (8-byte elements; order is kept, times that round together become one
+ * breakpoint of both PCFs, and widths carry the rounding of the times, about
+ * u * t per breakpoint).  It has no effect on float32 input and is invalid
+ * with PCF_PREC_F64.  Every call that shares a prepared workspace
+ * (pcf_prepare, PCF_PAIRWISE_PREPARED) must pass the same precision value. */
+#define PCF_PREC_ROUND_TIMES 0x100
 
 /* Output layout of the pairwise matrix. */
 enum pcf_layout {
@@ -108,7 +131,10 @@ enum pcf_pairwise_flags {
 enum pcf_cross_flags {
     PCF_CROSS_REUSE_B = 1  /* skip validating/packing B: the workspace still holds
                               B packed by the previous pcf_cross call made with
-                              the same B, precision and workspace */
+                              the same B, precision and workspace.  (float64 input
+                              in a float32 precision: B's validation and length
+                              sort are reused and B is packed again, because its
+                              order keys are ranks among A's rows and B) */
 };
 
 /* Work decomposition of the walk (pcf_pairwise_ex / pcf_cross_ex).
@@ -343,7 +369,8 @@ int pcf_sort_order(const pcf_csr* x, int precision, const void* workspace,
  * workspace by the last call: PCF_OK, or PCF_EINVAL with *detail set to the
  * reason code (1 offsets, 2 t_0 != 0, 3 times not increasing, 4 time not
  * finite, 5 value not finite, 6 time or value outside float32 range for a
- * float32 walk, 7 more coincident float32 times than one window holds) and
+ * float32 walk, 7 more coincident float32 times than one window holds:
+ * only with PCF_PREC_ROUND_TIMES) and
  * *index to the offending entry: an offsets error (reason 1, PCF index) is
  * reported before element errors, and among element errors the smallest
  * element index wins.  Reductions and combinations also report PCF_ENOWS

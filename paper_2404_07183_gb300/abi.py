@@ -15,6 +15,7 @@ PCF_OK, PCF_EINVAL, PCF_ENOWS, PCF_ECUDA, PCF_ETIMEOUT, PCF_EUNSUPPORTED = range
 PCF_F32, PCF_F64 = 0, 1
 PCF_L1, PCF_L2, PCF_LP, PCF_GRAM = 0, 1, 2, 3
 PCF_PREC_F64, PCF_PREC_F32_COMP, PCF_PREC_F32, PCF_PREC_F32_BLOCK = 0, 1, 2, 3
+PCF_PREC_ROUND_TIMES = 0x100
 PCF_OUT_FULL, PCF_OUT_UPPER_PACKED, PCF_OUT_FULL_SORTED = 0, 1, 2
 PCF_WS_FORWARD, PCF_WS_BACKWARD = 0, 1
 PCF_CROSS_REUSE_B = 1

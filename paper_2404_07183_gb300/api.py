@@ -30,7 +30,11 @@ __all__ = ["PcfError", "PcfTensors", "pcf_workspace_size", "pcf_prepare", "pcf_s
            "parse_metric", "PRECISIONS", "REDUCTIONS", "OPS"]
 
 PRECISIONS = {"f64": abi.PCF_PREC_F64, "f32c": abi.PCF_PREC_F32_COMP, "f32": abi.PCF_PREC_F32,
-              "f32b": abi.PCF_PREC_F32_BLOCK}
+              "f32b": abi.PCF_PREC_F32_BLOCK,
+              # float64 times rounded to float32 when packed (opt-in, faster)
+              "f32c_round": abi.PCF_PREC_F32_COMP | abi.PCF_PREC_ROUND_TIMES,
+              "f32_round": abi.PCF_PREC_F32 | abi.PCF_PREC_ROUND_TIMES,
+              "f32b_round": abi.PCF_PREC_F32_BLOCK | abi.PCF_PREC_ROUND_TIMES}
 REDUCTIONS = {"sum": abi.PCF_RED_SUM, "mean": abi.PCF_RED_MEAN, "max": abi.PCF_RED_MAX,
               "min": abi.PCF_RED_MIN, "std": abi.PCF_RED_STD}
 OPS = {"add": abi.PCF_OP_ADD, "sub": abi.PCF_OP_SUB, "mul": abi.PCF_OP_MUL, "max": abi.PCF_OP_MAX,

@@ -71,7 +71,10 @@ def _class_of(x: api.PcfTensors, metrics, precision, layout) -> str:
     lens = (x.offsets[1:] - x.offsets[:-1])
     mean = float(lens.double().mean().item()) if x.n else 1.0
     mx = int(lens.max().item()) if x.n else 1
-    return input_class(x.n, mean, mx, metrics, precision, layout,
+    # float64 input walked in float32 runs the keyed form (16-byte elements),
+    # float32 input the 8-byte form: different best schedules
+    prec_form = f"{precision}/{str(x.times.dtype).replace('torch.', '')}"
+    return input_class(x.n, mean, mx, metrics, prec_form, layout,
                        torch.cuda.get_device_name(x.times.device))
 
 

@@ -120,7 +120,47 @@ bool csr_ok(const pcf_csr* x)
     return true;
 }
 
-int elem_bytes_for(int precision) { return precision == PCF_PREC_F64 ? 16 : 8; }
+// Precision argument: a base precision, optionally with PCF_PREC_ROUND_TIMES
+// (float32 walks only).  Returns false for anything else.
+struct Prec {
+    int base = PCF_PREC_F64;
+    bool round = false;
+};
+
+bool parse_prec(int precision, Prec* out)
+{
+    const int base = precision & ~PCF_PREC_ROUND_TIMES;
+    if (base < PCF_PREC_F64 || base > PCF_PREC_F32_BLOCK) return false;
+    const bool round = (precision & PCF_PREC_ROUND_TIMES) != 0;
+    if (round && base == PCF_PREC_F64) return false;
+    out->base = base;
+    out->round = round;
+    return true;
+}
+
+// How the call's collections are packed: float64 walk; float32 walk of
+// float32 input (or of float64 input with rounded times, on request); or the
+// keyed float32 walk when any collection holds float64 times.
+int call_form(const Prec& p, const pcf_csr* x, const pcf_csr* y)
+{
+    if (p.base == PCF_PREC_F64) return kPackF64;
+    if (!p.round && ((x && x->dtype == PCF_F64) || (y && y->dtype == PCF_F64))) return kPackKeyed;
+    return kPackF32;
+}
+
+// Interval ends the key sort may have to rank (an upper bound).
+int64_t key_capacity(const pcf_csr* x, const pcf_csr* y)
+{
+    return (x ? x->nnz : 0) + (y ? y->nnz : 0);
+}
+
+// float32 hi + lo split of a float64 time (as the keyed pack does on the device).
+void split_time(double t, float out[2])
+{
+    if (std::isinf(t)) { out[0] = (float)t; out[1] = 0.f; return; }
+    out[0] = (float)t;
+    out[1] = (float)(t - (double)out[0]);
+}
 
 // Internal metric of one request: what the walk has to accumulate.
 enum ReqKind { RK_L1, RK_L2, RK_L3, RK_LP, RK_GRAM };
@@ -214,10 +254,12 @@ int check_window(const pcf_window* w)
 
 // kernel_out: the schedule kernel the call resolves to (AUTO decided here).
 // unit0: first work unit (tile schedules; the launch ends at wa.ntiles).
-int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int elem_bytes,
+int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int form,
               const pcf_schedule* sched, const pcf_window* win, cudaStream_t s,
               int64_t unit0 = 0, int* kernel_out = nullptr)
 {
+    const int elem_bytes = pack_elem_bytes(form);
+    const bool keyed = form == kPackKeyed;
     const int sms = device_sm_count();
     wa.lo = win ? win->a : 0.0;
     wa.hi = win ? win->b : (double)INFINITY;
@@ -277,32 +319,28 @@ int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int el
         reset_tiles_kernel<<<1, 1, 0, s>>>(wa.hdr, (unsigned long long)unit0);
         cudaError_t e;
         const int g = (int)grid;
+        // launcher of (schedule, precision, form)
+#define PCF_PICK(sfx)                                                                       \
+        (precision == PCF_PREC_F64 ? launch_walk_f64_##sfx                                  \
+         : precision == PCF_PREC_F32_COMP ? (keyed ? launch_walk_f32ck_##sfx : launch_walk_f32c_##sfx) \
+         : precision == PCF_PREC_F32_BLOCK ? (keyed ? launch_walk_f32bk_##sfx : launch_walk_f32b_##sfx) \
+         : (keyed ? launch_walk_f32k_##sfx : launch_walk_f32_##sfx))
         if (kernel == PCF_SCHED_MERGEPATH) {
-            if (precision == PCF_PREC_F64) e = launch_mergepath_f64(L.combo, wa, npairs, g, s);
-            else if (precision == PCF_PREC_F32_COMP) e = launch_mergepath_f32c(L.combo, wa, npairs, g, s);
-            else if (precision == PCF_PREC_F32_BLOCK) e = launch_mergepath_f32b(L.combo, wa, npairs, g, s);
-            else e = launch_mergepath_f32(L.combo, wa, npairs, g, s);
+            auto mp = precision == PCF_PREC_F64 ? launch_mergepath_f64
+                    : precision == PCF_PREC_F32_COMP ? (keyed ? launch_mergepath_f32ck : launch_mergepath_f32c)
+                    : precision == PCF_PREC_F32_BLOCK ? (keyed ? launch_mergepath_f32bk : launch_mergepath_f32b)
+                    : (keyed ? launch_mergepath_f32k : launch_mergepath_f32);
+            e = mp(L.combo, wa, npairs, g, s);
         } else if (kernel == PCF_SCHED_TILE_512X3) {
-            if (precision == PCF_PREC_F64) e = launch_walk_f64_t512x3(L.combo, wa, g, smem, s);
-            else if (precision == PCF_PREC_F32_COMP) e = launch_walk_f32c_t512x3(L.combo, wa, g, smem, s);
-            else if (precision == PCF_PREC_F32_BLOCK) e = launch_walk_f32b_t512x3(L.combo, wa, g, smem, s);
-            else e = launch_walk_f32_t512x3(L.combo, wa, g, smem, s);
+            e = PCF_PICK(t512x3)(L.combo, wa, g, smem, s);
         } else if (kernel == PCF_SCHED_TILE_512X2) {
-            if (precision == PCF_PREC_F64) e = launch_walk_f64_t512(L.combo, wa, g, smem, s);
-            else if (precision == PCF_PREC_F32_COMP) e = launch_walk_f32c_t512(L.combo, wa, g, smem, s);
-            else if (precision == PCF_PREC_F32_BLOCK) e = launch_walk_f32b_t512(L.combo, wa, g, smem, s);
-            else e = launch_walk_f32_t512(L.combo, wa, g, smem, s);
+            e = PCF_PICK(t512)(L.combo, wa, g, smem, s);
         } else if (weighted) {
-            if (precision == PCF_PREC_F64) e = launch_walk_f64_t1024w(L.combo, wa, g, smem, s);
-            else if (precision == PCF_PREC_F32_COMP) e = launch_walk_f32c_t1024w(L.combo, wa, g, smem, s);
-            else if (precision == PCF_PREC_F32_BLOCK) e = launch_walk_f32b_t1024w(L.combo, wa, g, smem, s);
-            else e = launch_walk_f32_t1024w(L.combo, wa, g, smem, s);
+            e = PCF_PICK(t1024w)(L.combo, wa, g, smem, s);
         } else {
-            if (precision == PCF_PREC_F64) e = launch_walk_f64_t1024(L.combo, wa, g, smem, s);
-            else if (precision == PCF_PREC_F32_COMP) e = launch_walk_f32c_t1024(L.combo, wa, g, smem, s);
-            else if (precision == PCF_PREC_F32_BLOCK) e = launch_walk_f32b_t1024(L.combo, wa, g, smem, s);
-            else e = launch_walk_f32_t1024(L.combo, wa, g, smem, s);
+            e = PCF_PICK(t1024)(L.combo, wa, g, smem, s);
         }
+#undef PCF_PICK
         if (e != cudaSuccess) return PCF_ECUDA;
     }
     return PCF_OK;
@@ -349,44 +387,86 @@ int pcf_workspace_size(const pcf_csr* x, const pcf_csr* y, int precision, int pu
 {
     if (!bytes || !x || x->n < 0 || x->nnz < 0 || x->n > 0x7fffffffLL) return PCF_EINVAL;
     if (y && (y->n < 0 || y->nnz < 0 || y->n > 0x7fffffffLL)) return PCF_EINVAL;
-    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32_BLOCK) return PCF_EINVAL;
+    Prec pr;
+    if (!parse_prec(precision, &pr)) return PCF_EINVAL;
     if (purpose != PCF_WS_FORWARD && purpose != PCF_WS_BACKWARD) return PCF_EINVAL;
-    const int es = purpose == PCF_WS_BACKWARD ? 16 : elem_bytes_for(precision);
+    const int form = purpose == PCF_WS_BACKWARD ? kPackF64 : call_form(pr, x, y);
+    const int es = pack_elem_bytes(form);
     size_t b = sizeof(Header);
     if (y) b += set_bytes(y->n, y->nnz, es);
     b += set_bytes(x->n, x->nnz, es);
+    if (form == kPackKeyed) b += keysort_bytes(key_capacity(x, y));
     if (purpose == PCF_WS_BACKWARD) b += 2 * align_up(sizeof(double) * (size_t)x->nnz);
     *bytes = b;
     return PCF_OK;
 }
 
 static int pairwise_common(const pcf_csr* x, int precision, void* workspace,
-                           size_t workspace_bytes, Header** hdr_out, SetView* sv_out)
+                           size_t workspace_bytes, Header** hdr_out, SetView* sv_out,
+                           KeySort* ks_out = nullptr, int* form_out = nullptr)
 {
+    Prec pr;
+    if (!parse_prec(precision, &pr)) return PCF_EINVAL;
+    const int form = call_form(pr, x, nullptr);
+    if (form == kPackKeyed && key_capacity(x, nullptr) > 0x7fffffffLL) return PCF_EUNSUPPORTED;
     size_t need = 0;
     pcf_workspace_size(x, nullptr, precision, PCF_WS_FORWARD, &need);
     if (!workspace || ((uintptr_t)workspace % kAlign) != 0 || workspace_bytes < need) return PCF_ENOWS;
     char* cur = (char*)workspace;
     *hdr_out = (Header*)cur;
     cur += sizeof(Header);
-    *sv_out = carve_set(cur, x->n, x->nnz, elem_bytes_for(precision), 0);
+    *sv_out = carve_set(cur, x->n, x->nnz, pack_elem_bytes(form), 0);
+    if (form == kPackKeyed && ks_out) *ks_out = carve_keysort(cur, key_capacity(x, nullptr));
+    if (form_out) *form_out = form;
     return PCF_OK;
+}
+
+// Validate, length-sort and pack one collection for a pairwise call; the
+// keyed form also ranks its interval ends.
+static cudaError_t prepare_pairwise(const pcf_csr* x, int form, Header* hdr, SetView& sv,
+                                    const KeySort& ks, cudaStream_t s)
+{
+    KeyOut ko;
+    if (form == kPackKeyed) { ko.key = ks.key[0]; ko.pay = ks.pay[0]; }
+    cudaError_t e = prepare_set(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz, true,
+                                form, hdr, sv, s, form == kPackKeyed ? &ko : nullptr);
+    if (e != cudaSuccess || form != kPackKeyed) return e;
+    return rank_keys(ks, reinterpret_cast<KElem*>(sv.packed), sv.poff, x->n, nullptr, nullptr, 0,
+                     hdr, s);
+}
+
+// Order keys of a window's bounds for a keyed walk (after the ranks exist).
+static void keyed_bounds(WalkArgs& wa, const pcf_window* win, int form, const KeySort& ks,
+                         KElem* pack0, KElem* pack1, Header* hdr, cudaStream_t s)
+{
+    if (form != kPackKeyed) return;
+    const double lo = win ? win->a : 0.0;
+    const double hi = win ? win->b : (double)INFINITY;
+    split_time(lo, wa.lo_hl);
+    split_time(hi, wa.hi_hl);
+    if (lo > 0.0 || !std::isinf(hi)) {
+        bound_keys(ks, pack0, pack1, lo, hi, hdr, s);
+        wa.bound_keys = hdr->bound_key;
+    } else {
+        wa.bound_keys = nullptr;
+    }
 }
 
 int pcf_prepare(const pcf_csr* x, int precision, void* workspace, size_t workspace_bytes,
                 cudaStream_t stream)
 {
     if (!csr_ok(x)) return PCF_EINVAL;
-    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32_BLOCK) return PCF_EINVAL;
+    Prec pr;
+    if (!parse_prec(precision, &pr)) return PCF_EINVAL;
     Header* hdr;
     SetView sv;
-    int rc = pairwise_common(x, precision, workspace, workspace_bytes, &hdr, &sv);
+    KeySort ks;
+    int form = kPackF64;
+    int rc = pairwise_common(x, precision, workspace, workspace_bytes, &hdr, &sv, &ks, &form);
     if (rc != PCF_OK) return rc;
     init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
     if (x->n == 0) return cudaGetLastError() == cudaSuccess ? PCF_OK : PCF_ECUDA;
-    if (prepare_set(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz, true,
-                    precision == PCF_PREC_F64, hdr, sv, stream) != cudaSuccess)
-        return PCF_ECUDA;
+    if (prepare_pairwise(x, form, hdr, sv, ks, stream) != cudaSuccess) return PCF_ECUDA;
     return PCF_OK;
 }
 
@@ -404,7 +484,8 @@ int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precisi
                     cudaStream_t stream)
 {
     if (!csr_ok(x)) return PCF_EINVAL;
-    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32_BLOCK) return PCF_EINVAL;
+    Prec pr;
+    if (!parse_prec(precision, &pr)) return PCF_EINVAL;
     if (layout != PCF_OUT_FULL && layout != PCF_OUT_UPPER_PACKED && layout != PCF_OUT_FULL_SORTED)
         return PCF_EINVAL;
     if (out_dtype != PCF_F32 && out_dtype != PCF_F64) return PCF_EINVAL;
@@ -415,15 +496,14 @@ int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precisi
     if (rc != PCF_OK) return rc;
     Header* hdr;
     SetView sv;
-    rc = pairwise_common(x, precision, workspace, workspace_bytes, &hdr, &sv);
+    KeySort ks;
+    int form = kPackF64;
+    rc = pairwise_common(x, precision, workspace, workspace_bytes, &hdr, &sv, &ks, &form);
     if (rc != PCF_OK) return rc;
     if (x->n == 0) return PCF_OK;
-    const int es = elem_bytes_for(precision);
     if (!(flags & PCF_PAIRWISE_PREPARED)) {
         init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
-        if (prepare_set(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz, true,
-                        precision == PCF_PREC_F64, hdr, sv, stream) != cudaSuccess)
-            return PCF_ECUDA;
+        if (prepare_pairwise(x, form, hdr, sv, ks, stream) != cudaSuccess) return PCF_ECUDA;
     }
 
     WalkArgs wa;
@@ -440,7 +520,9 @@ int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precisi
     wa.layout = layout;
     wa.out_f64 = out_dtype == PCF_F64;
     wa.ld_out = x->n;
-    return run_walks(wa, F, nF, precision, es, schedule, window, stream);
+    KElem* kp = reinterpret_cast<KElem*>(sv.packed);
+    keyed_bounds(wa, window, form, ks, kp, kp, hdr, stream);
+    return run_walks(wa, F, nF, pr.base, form, schedule, window, stream);
 }
 
 int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int precision,
@@ -449,7 +531,8 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
                          cudaStream_t stream, cudaStream_t copy_stream)
 {
     if (!csr_ok(x)) return PCF_EINVAL;
-    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32_BLOCK) return PCF_EINVAL;
+    Prec pr;
+    if (!parse_prec(precision, &pr)) return PCF_EINVAL;
     if (out_dtype != PCF_F32 && out_dtype != PCF_F64) return PCF_EINVAL;
     if (nbands < 0) return PCF_EINVAL;
     if (check_schedule(schedule) != PCF_OK) return PCF_EINVAL;
@@ -458,7 +541,9 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
     if (rc != PCF_OK) return rc;
     Header* hdr;
     SetView sv;
-    rc = pairwise_common(x, precision, workspace, workspace_bytes, &hdr, &sv);
+    KeySort ks;
+    int form = kPackF64;
+    rc = pairwise_common(x, precision, workspace, workspace_bytes, &hdr, &sv, &ks, &form);
     if (rc != PCF_OK) return rc;
     if (x->n == 0) return PCF_OK;
     if (!host_out) return PCF_EINVAL;
@@ -480,9 +565,7 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
     }
 
     init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
-    if (prepare_set(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz, true,
-                    precision == PCF_PREC_F64, hdr, sv, stream) != cudaSuccess)
-        return PCF_ECUDA;
+    if (prepare_pairwise(x, form, hdr, sv, ks, stream) != cudaSuccess) return PCF_ECUDA;
     WalkArgs wa;
     memset(&wa, 0, sizeof wa);
     wa.pack_r = wa.pack_c = sv.packed;
@@ -497,7 +580,10 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
     wa.layout = PCF_OUT_FULL;
     wa.out_f64 = out_dtype == PCF_F64;
     wa.ld_out = N;
-    const int es = elem_bytes_for(precision);
+    {
+        KElem* kp = reinterpret_cast<KElem*>(sv.packed);
+        keyed_bounds(wa, nullptr, form, ks, kp, kp, hdr, stream);
+    }
     const int sms = device_sm_count();
     const bool two = copy_stream != stream;
     // the walks run with the largest shared-memory carve-out; a CTA that asks
@@ -545,7 +631,7 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
     };
     auto fail = [&](int code) { join(); return code; };
     if (sch.kernel == PCF_SCHED_MERGEPATH || nbands == 1) {
-        rc = run_walks(wa, F, nF, precision, es, &sch, nullptr, stream);
+        rc = run_walks(wa, F, nF, pr.base, form, &sch, nullptr, stream);
         if (rc != PCF_OK) return rc;
         if (!copy_rows(0, N)) return fail(PCF_ECUDA);
     } else {
@@ -559,7 +645,7 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
         for (size_t k = 0; k + 1 < cuts.size(); ++k) {
             const int64_t m0 = cuts[k], m1 = cuts[k + 1];
             wa.ntiles = first_tile(m1);
-            rc = run_walks(wa, F, nF, precision, es, &sch, nullptr, stream, first_tile(m0) * units);
+            rc = run_walks(wa, F, nF, pr.base, form, &sch, nullptr, stream, first_tile(m0) * units);
             if (rc != PCF_OK) return fail(rc);
             const int64_t s0 = m0 * kTile;
             const int64_t s1 = m1 * kTile < N ? m1 * kTile : N;
@@ -584,7 +670,8 @@ int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t 
                  void* workspace, size_t workspace_bytes, cudaStream_t stream)
 {
     if (!csr_ok(a) || !csr_ok(b)) return PCF_EINVAL;
-    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32_BLOCK) return PCF_EINVAL;
+    Prec pr;
+    if (!parse_prec(precision, &pr)) return PCF_EINVAL;
     if (out_dtype != PCF_F32 && out_dtype != PCF_F64) return PCF_EINVAL;
     if (row_begin < 0 || row_end < row_begin || row_end > a->n) return PCF_EINVAL;
     if (ld_out < b->n) return PCF_EINVAL;
@@ -594,6 +681,8 @@ int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t 
     const int64_t rows = row_end - row_begin;
     int rc = check_requests(F, nF, rows > 0 && b->n > 0);
     if (rc != PCF_OK) return rc;
+    const int form = call_form(pr, a, b);
+    if (form == kPackKeyed && key_capacity(a, b) > 0x7fffffffLL) return PCF_EUNSUPPORTED;
     size_t need = 0;
     pcf_workspace_size(a, b, precision, PCF_WS_FORWARD, &need);
     if (!workspace || ((uintptr_t)workspace % kAlign) != 0 || workspace_bytes < need) return PCF_ENOWS;
@@ -602,19 +691,42 @@ int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t 
     char* cur = (char*)workspace;
     Header* hdr = (Header*)cur;
     cur += sizeof(Header);
-    const int es = elem_bytes_for(precision);
+    const int es = pack_elem_bytes(form);
     SetView sb = carve_set(cur, b->n, b->nnz, es, 1);
     SetView sa = carve_set(cur, rows, a->nnz, es, 0);
+    KeySort ks;
+    if (form == kPackKeyed) ks = carve_keysort(cur, key_capacity(a, b));
     const bool reuse = (flags & PCF_CROSS_REUSE_B) != 0;
     init_header_kernel<<<1, 1, 0, stream>>>(hdr, reuse ? 1 : 0);
+    // keyed: B's interval ends first in the sort input, then A's; both are
+    // ranked together every call (A's rows change, so B's ranks do too: a
+    // reused B keeps its validation and length sort and is packed again)
+    KeyOut kb, ka;
+    if (form == kPackKeyed) {
+        kb.key = ka.key = ks.key[0];
+        kb.pay = ka.pay = ks.pay[0];
+        kb.set_bit = 0x80000000u;
+        ka.base_poff = sb.poff;
+        ka.base_n = b->n;
+    }
+    const KeyOut* pkb = form == kPackKeyed ? &kb : nullptr;
+    const KeyOut* pka = form == kPackKeyed ? &ka : nullptr;
     if (!reuse) {
-        if (prepare_set(b->offsets, b->times, b->values, b->dtype, b->n, b->nnz, true,
-                        precision == PCF_PREC_F64, hdr, sb, stream) != cudaSuccess)
+        if (prepare_set(b->offsets, b->times, b->values, b->dtype, b->n, b->nnz, true, form, hdr, sb,
+                        stream, pkb) != cudaSuccess)
+            return PCF_ECUDA;
+    } else if (form == kPackKeyed) {
+        if (pack_set(b->offsets, b->times, b->values, b->dtype, b->n, form, hdr, sb, stream, pkb) !=
+            cudaSuccess)
             return PCF_ECUDA;
     }
     if (prepare_set(a->offsets + row_begin, a->times, a->values, a->dtype, rows, a->nnz,
-                    row_begin == 0 && row_end == a->n, precision == PCF_PREC_F64, hdr, sa,
-                    stream) != cudaSuccess)
+                    row_begin == 0 && row_end == a->n, form, hdr, sa, stream, pka) != cudaSuccess)
+        return PCF_ECUDA;
+    KElem* kpa = reinterpret_cast<KElem*>(sa.packed);
+    KElem* kpb = reinterpret_cast<KElem*>(sb.packed);
+    if (form == kPackKeyed &&
+        rank_keys(ks, kpa, sa.poff, rows, kpb, sb.poff, b->n, hdr, stream) != cudaSuccess)
         return PCF_ECUDA;
 
     WalkArgs wa;
@@ -631,7 +743,8 @@ int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t 
     wa.layout = PCF_OUT_FULL;
     wa.out_f64 = out_dtype == PCF_F64;
     wa.ld_out = ld_out;
-    return run_walks(wa, F, nF, precision, es, schedule, window, stream);
+    keyed_bounds(wa, window, form, ks, kpa, kpb, hdr, stream);
+    return run_walks(wa, F, nF, pr.base, form, schedule, window, stream);
 }
 
 int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root,
@@ -685,8 +798,8 @@ int pcf_pairwise_backward_ex(const pcf_csr* x, int metric, double p, int apply_r
     cur += align_up(sizeof(double) * (size_t)x->nnz);
     double* gt = (double*)cur;
     init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
-    if (prepare_set(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz, true, 1, hdr, sv,
-                    stream) != cudaSuccess)
+    if (prepare_set(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz, true, kPackF64, hdr,
+                    sv, stream) != cudaSuccess)
         return PCF_ECUDA;
     {
         int64_t blocks = (x->nnz + 255) / 256;
@@ -744,7 +857,8 @@ int pcf_sort_order(const pcf_csr* x, int precision, const void* workspace,
                    size_t workspace_bytes, int32_t* perm_out, cudaStream_t stream)
 {
     if (!csr_ok(x)) return PCF_EINVAL;
-    if (precision < PCF_PREC_F64 || precision > PCF_PREC_F32_BLOCK) return PCF_EINVAL;
+    Prec pr;
+    if (!parse_prec(precision, &pr)) return PCF_EINVAL;
     if (x->n > 0 && !perm_out) return PCF_EINVAL;
     Header* hdr;
     SetView sv;

@@ -12,7 +12,11 @@
 //              packed[nnz]        "interval elements" in sorted order:
 //                                 element k of PCF s = (te_k, v_k), the value
 //                                 v_k on [t_k, te_k) with te_k = t_{k+1} and
-//                                 te_{n-1} = +inf; float or double pairs
+//                                 te_{n-1} = +inf; float or double pairs, or
+//                                 for float64 input walked in float32, KElem
+//                                 (rank of te_k, te_k as float32 hi + lo, v_k)
+//   key sort : (float64 bits of te, packed position) pairs, ping-pong, and
+//              the radix histograms (keyed float32 walks only)
 //   backward : gv[nnz], gt[nnz] float64 gradient accumulators (packed order)
 #pragma once
 
@@ -43,7 +47,9 @@ struct Header {
     unsigned long long err;      // error key
     unsigned int maxlen[2];      // max PCF length of set 0 / set 1
     unsigned long long tiles;    // persistent-kernel tile counter
-    unsigned long long pad[29];
+    unsigned long long nkeys;    // keyed walks: interval ends ranked by the key sort
+    unsigned int bound_key[2];   // keyed walks: order keys of the bounds a, b
+    unsigned long long pad[27];
 };
 static_assert(sizeof(Header) == 256, "header is 256 bytes");
 
@@ -66,6 +72,49 @@ __device__ __forceinline__ bool block_sees_error(const Header* h)
 }
 #endif
 
+// Interval element of the keyed float32 walk (float64 input): the end time
+// te as an exact order key (rank among the call's interval ends, see keys.cu)
+// and as float32 hi + lo (hi = te rounded to float32, lo = te - hi rounded),
+// and the value on the interval.  16 bytes, one vector load.
+struct __align__(16) KElem {
+    uint32_t k;
+    float hi;
+    float lo;
+    float v;
+};
+constexpr uint32_t kKeyInf = 0xFFFFFFFFu;   // order key of te = +inf
+
+// How a collection is packed for the walk.
+enum PackForm : int {
+    kPackF64 = 0,     // double2 (te, v): the float64 walk
+    kPackF32 = 1,     // float2 (te, v): float32 walks of float32 input, or of
+                      // float64 input with the times rounded (opt-in)
+    kPackKeyed = 2    // KElem: float32 walks of float64 input
+};
+inline int pack_elem_bytes(int form) { return form == kPackF32 ? 8 : 16; }
+
+// Scratch of the key sort (keys.cu): capacity `cap` interval ends.
+struct KeySort {
+    int64_t cap = 0;
+    int64_t tiles = 0;
+    uint64_t* key[2] = {nullptr, nullptr};
+    uint32_t* pay[2] = {nullptr, nullptr};
+    uint32_t* hist = nullptr;   // 256 x tiles digit counts
+    uint32_t* tsum = nullptr;   // tiles + 1 distinct-key counts
+    uint32_t* dsum = nullptr;   // 256 digit totals
+};
+size_t keysort_bytes(int64_t cap);
+KeySort carve_keysort(char*& cursor, int64_t cap);
+// Ranks of the interval ends of one or two packed keyed collections, written
+// into their KElem.k fields.  The sort input (key[0], pay[0]) is written by
+// the pack; the sorted keys end in key[0], pay[0].
+cudaError_t rank_keys(const KeySort& ks, KElem* pack0, const int64_t* poff0, int64_t n0,
+                      KElem* pack1, const int64_t* poff1, int64_t n1, Header* hdr, cudaStream_t s);
+// Order keys of the integration bounds a, b into hdr->bound_key (after
+// rank_keys, while the sorted keys are still in the workspace).
+cudaError_t bound_keys(const KeySort& ks, const KElem* pack0, const KElem* pack1, double a, double b,
+                       Header* hdr, cudaStream_t s);
+
 // Device pointers of one prepared (validated, sorted, packed) collection.
 struct SetView {
     int64_t n = 0;          // number of PCFs
@@ -79,8 +128,20 @@ struct SetView {
     int32_t* kv[2] = {nullptr, nullptr};
     int64_t* poff = nullptr;
     void* packed = nullptr;
-    int elem_bytes = 8;     // 8 (float pairs) or 16 (double pairs)
+    int elem_bytes = 8;     // 8 (float pairs) or 16 (double pairs, KElem)
     int slot = 0;           // which Header::maxlen entry
+};
+
+// Where the keyed pack writes its sort input: entry key_base + poff[s] - s + k
+// of `key` / `pay` for the finite interval end k of sorted PCF s, with
+// payload = set_bit | packed position.  key_base = base_poff[base_n] - base_n
+// (the keys of a set packed before, read on the device), or 0.
+struct KeyOut {
+    uint64_t* key = nullptr;
+    uint32_t* pay = nullptr;
+    uint32_t set_bit = 0;
+    const int64_t* base_poff = nullptr;   // keys of another set come first
+    int64_t base_n = 0;
 };
 
 size_t set_bytes(int64_t n, int64_t nnz, int elem_bytes);
@@ -93,7 +154,13 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // offsets[0] must be 0 and offsets[n] must equal nnz_total.
 cudaError_t prepare_set(const int64_t* offsets, const void* times, const void* values,
                         int in_dtype, int64_t n, int64_t nnz_total, bool whole,
-                        int walk_f64, Header* hdr, SetView& sv, cudaStream_t s);
+                        int form, Header* hdr, SetView& sv, cudaStream_t s,
+                        const KeyOut* ko = nullptr);
+// The pack step alone (validation and length sort already done): used by
+// cross calls that reuse B's sort but must re-rank its keys.
+cudaError_t pack_set(const int64_t* offsets, const void* times, const void* values, int in_dtype,
+                     int64_t n, int form, Header* hdr, SetView& sv, cudaStream_t s,
+                     const KeyOut* ko);
 
 // Arguments of the tile walk kernels.
 struct WalkArgs {
@@ -122,6 +189,9 @@ struct WalkArgs {
     int64_t shard_count;     // >= 1
     double lo, hi;           // integration bounds [lo, hi], 0 <= lo < hi <= inf
     double lambda;           // weight exp(-lambda t) (weighted kernels only)
+    float lo_hl[2], hi_hl[2];    // keyed walks: lo and hi as float32 hi + lo
+    const unsigned int* bound_keys;  // keyed walks with bounds: order keys of lo,
+                                     // hi (device); null = [0, inf)
 };
 
 // Metric combination codes compiled into the walk kernels.
@@ -142,6 +212,9 @@ PCF_DECL_WALK(f64)
 PCF_DECL_WALK(f32c)
 PCF_DECL_WALK(f32)
 PCF_DECL_WALK(f32b)
+PCF_DECL_WALK(f32ck)
+PCF_DECL_WALK(f32k)
+PCF_DECL_WALK(f32bk)
 #undef PCF_DECL_WALK
 size_t walk_smem_bytes(int window, int elem_bytes);
 
@@ -164,7 +237,7 @@ cudaError_t launch_segments(const pcf_csr* x, int functional, double p, int appl
                             double lo, double hi, int precision, void* out, int out_f64,
                             Header* hdr, void* scratch, cudaStream_t s);
 cudaError_t launch_validate(const int64_t* offsets, const void* times, const void* values,
-                            int in_dtype, int64_t n, int64_t nnz_total, int walk_f64,
+                            int in_dtype, int64_t n, int64_t nnz_total, int form,
                             Header* hdr, SetView& sv, cudaStream_t s);
 
 int device_sm_count();

@@ -15,7 +15,8 @@
 //
 // Loads go through the read-only data cache; each lane streams two
 // contiguous ranges, one interval element (an 8- or 16-byte vector: end time
-// and value) per advance.
+// and value, or the keyed element of float64 input walked in float32: order
+// key, end time as float32 hi + lo, value) per advance.
 #pragma once
 
 #include "walk.cuh"
@@ -42,16 +43,30 @@ __device__ __forceinline__ void decode_pair(const WalkArgs& a, int64_t t, int64_
     }
 }
 
-template <typename T>
-__device__ __forceinline__ typename ElemOf<T>::type ldg_elem(const typename ElemOf<T>::type* p)
+template <typename E>
+__device__ __forceinline__ E ldg_elem(const E* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ KElem ldg_elem<KElem>(const KElem* p)
 {
-    return __ldg(p);
+    const uint4 u = __ldg(reinterpret_cast<const uint4*>(p));
+    KElem e;
+    e.k = u.x;
+    e.hi = __uint_as_float(u.y);
+    e.lo = __uint_as_float(u.z);
+    e.v = __uint_as_float(u.w);
+    return e;
 }
 
-template <typename T, int PREC, int COMBO>
+// End-time order of the two walk forms: values (float64 through the integer
+// pipe) or order keys.
+template <typename K> __device__ __forceinline__ bool key_after(K x, K y) { return ends_after(x, y); }
+template <> __device__ __forceinline__ bool key_after<uint32_t>(uint32_t x, uint32_t y) { return x > y; }
+
+template <typename T, int PREC, int COMBO, bool KEYED = false>
 __global__ void __launch_bounds__(256, 4) mergepath_kernel(const WalkArgs a, int64_t npairs)
 {
-    using E = typename ElemOf<T>::type;
+    using WF = WalkForm<T, KEYED>;
+    using E = typename WF::E;
     constexpr int NM = combo_n(COMBO);
     if (a.hdr->err != kNoError) return;
     const int lane = threadIdx.x & 31;
@@ -78,27 +93,52 @@ __global__ void __launch_bounds__(256, 4) mergepath_kernel(const WalkArgs a, int
             int64_t lo = s0 - ly > 0 ? s0 - ly : 0, hi = s0 < lx ? s0 : lx;
             while (lo < hi) {
                 const int64_t mid = (lo + hi) >> 1;
-                const T x = ldg_elem<T>(F + mid).x;
-                const T y = ldg_elem<T>(G + (s0 - 1 - mid)).x;
-                if (!ends_after(x, y)) lo = mid + 1; else hi = mid;
+                const auto x = WF::key(ldg_elem(F + mid));
+                const auto y = WF::key(ldg_elem(G + (s0 - 1 - mid)));
+                if (!key_after(x, y)) lo = mid + 1; else hi = mid;
             }
             int kf = (int)lo, kg = (int)(s0 - lo);
-            T tc = T(0);
-            if (kf > 0) tc = ldg_elem<T>(F + kf - 1).x;
-            if (kg > 0) { const T y = ldg_elem<T>(G + kg - 1).x; tc = ends_after(y, tc) ? y : tc; }
-            E ef = ldg_elem<T>(F + kf), eg = ldg_elem<T>(G + kg);
-            for (int64_t s = s0; s < s1; ++s) {
-                if (((s - s0) & 15) == 0) {
-#pragma unroll
-                    for (int m = 0; m < NM; ++m) acc[m].flush();
+            E ef = ldg_elem(F + kf), eg = ldg_elem(G + kg);
+            if constexpr (KEYED) {
+                // start time: the later of the two interval ends passed so far
+                float tc = 0.f, tcl = 0.f;
+                uint32_t kc = 0;
+                if (kf > 0) { const KElem e = ldg_elem(F + kf - 1); tc = e.hi; tcl = e.lo; kc = e.k; }
+                if (kg > 0) {
+                    const KElem e = ldg_elem(G + kg - 1);
+                    if (e.k > kc) { tc = e.hi; tcl = e.lo; }
                 }
-                const bool adv_f = !ends_after(ef.x, eg.x);
-                const T tn = adv_f ? ef.x : eg.x;
-                const T dt = tn - tc;
-                tc = tn;
-                accumulate<COMBO, PREC, T>(acc, ef.y, eg.y, dt, p0);
-                if (adv_f) ef = ldg_elem<T>(F + (++kf));
-                else eg = ldg_elem<T>(G + (++kg));
+                for (int64_t s = s0; s < s1; ++s) {
+                    if (((s - s0) & 15) == 0) {
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) acc[m].flush();
+                    }
+                    const bool adv_f = ef.k <= eg.k;
+                    const float hn = adv_f ? ef.hi : eg.hi, ln = adv_f ? ef.lo : eg.lo;
+                    const float dt = __fadd_rn(__fsub_rn(hn, tc), __fsub_rn(ln, tcl));
+                    tc = hn;
+                    tcl = ln;
+                    accumulate<COMBO, PREC, T>(acc, ef.v, eg.v, dt, p0);
+                    if (adv_f) ef = ldg_elem(F + (++kf));
+                    else eg = ldg_elem(G + (++kg));
+                }
+            } else {
+                T tc = T(0);
+                if (kf > 0) tc = ldg_elem(F + kf - 1).x;
+                if (kg > 0) { const T y = ldg_elem(G + kg - 1).x; tc = ends_after(y, tc) ? y : tc; }
+                for (int64_t s = s0; s < s1; ++s) {
+                    if (((s - s0) & 15) == 0) {
+#pragma unroll
+                        for (int m = 0; m < NM; ++m) acc[m].flush();
+                    }
+                    const bool adv_f = !ends_after(ef.x, eg.x);
+                    const T tn = adv_f ? ef.x : eg.x;
+                    const T dt = tn - tc;
+                    tc = tn;
+                    accumulate<COMBO, PREC, T>(acc, ef.y, eg.y, dt, p0);
+                    if (adv_f) ef = ldg_elem(F + (++kf));
+                    else eg = ldg_elem(G + (++kg));
+                }
             }
         }
 #pragma unroll
@@ -113,12 +153,12 @@ __global__ void __launch_bounds__(256, 4) mergepath_kernel(const WalkArgs a, int
             I[m] = v;
         }
         if (lane == 0) {
-            const E lf = ldg_elem<T>(F + nf - 1), lg = ldg_elem<T>(G + ng - 1);
+            const T lfv = WF::val(ldg_elem(F + nf - 1)), lgv = WF::val(ldg_elem(G + ng - 1));
             const int64_t i = a.perm_r[gi], j = a.perm_c[gj];
 #pragma unroll
             for (int m = 0; m < NM; ++m) {
                 const int MI = combo_metric(COMBO, m);
-                const T h = (MI == MI_GRAM) ? lf.y * lg.y : fabs(lf.y - lg.y);
+                const T h = (MI == MI_GRAM) ? lfv * lgv : fabs(lfv - lgv);
                 double Iv = I[m];
                 if (h != T(0)) Iv = (h > T(0)) ? (double)INFINITY : -(double)INFINITY;
                 const double Fv = finalize_root(a.metric[m], a.root[m], a.p[m], Iv);
@@ -145,17 +185,17 @@ __global__ void __launch_bounds__(256, 4) mergepath_kernel(const WalkArgs a, int
     }
 }
 
-template <typename T, int PREC>
+template <typename T, int PREC, bool KEYED = false>
 cudaError_t launch_mergepath_t(int combo, const WalkArgs& a, int64_t npairs, int grid, cudaStream_t s)
 {
     switch (combo) {
-    case kComboL1: mergepath_kernel<T, PREC, kComboL1><<<grid, 256, 0, s>>>(a, npairs); break;
-    case kComboL2: mergepath_kernel<T, PREC, kComboL2><<<grid, 256, 0, s>>>(a, npairs); break;
-    case kComboGram: mergepath_kernel<T, PREC, kComboGram><<<grid, 256, 0, s>>>(a, npairs); break;
-    case kComboLP: mergepath_kernel<T, PREC, kComboLP><<<grid, 256, 0, s>>>(a, npairs); break;
-    case kComboL3: mergepath_kernel<T, PREC, kComboL3><<<grid, 256, 0, s>>>(a, npairs); break;
-    case kComboL1L2Gram: mergepath_kernel<T, PREC, kComboL1L2Gram><<<grid, 256, 0, s>>>(a, npairs); break;
-    case kComboL1L2L3: mergepath_kernel<T, PREC, kComboL1L2L3><<<grid, 256, 0, s>>>(a, npairs); break;
+    case kComboL1: mergepath_kernel<T, PREC, kComboL1, KEYED><<<grid, 256, 0, s>>>(a, npairs); break;
+    case kComboL2: mergepath_kernel<T, PREC, kComboL2, KEYED><<<grid, 256, 0, s>>>(a, npairs); break;
+    case kComboGram: mergepath_kernel<T, PREC, kComboGram, KEYED><<<grid, 256, 0, s>>>(a, npairs); break;
+    case kComboLP: mergepath_kernel<T, PREC, kComboLP, KEYED><<<grid, 256, 0, s>>>(a, npairs); break;
+    case kComboL3: mergepath_kernel<T, PREC, kComboL3, KEYED><<<grid, 256, 0, s>>>(a, npairs); break;
+    case kComboL1L2Gram: mergepath_kernel<T, PREC, kComboL1L2Gram, KEYED><<<grid, 256, 0, s>>>(a, npairs); break;
+    case kComboL1L2L3: mergepath_kernel<T, PREC, kComboL1L2L3, KEYED><<<grid, 256, 0, s>>>(a, npairs); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

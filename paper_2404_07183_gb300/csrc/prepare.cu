@@ -258,6 +258,53 @@ __global__ void pack_kernel(const int64_t* __restrict__ offsets, const Tin* __re
     }
 }
 
+// Keyed pack (float64 input, float32 walk), one warp per sorted PCF: element
+// k gets te_k split into float32 hi = RN(te_k) and lo = RN(te_k - hi) (the
+// difference is exact in float64) and v_k rounded to float32; its order key
+// is filled in by the key sort (keys.cu), which reads the float64 bits of
+// every finite te_k and the element's packed position from the sort input
+// written here.  The last element (te = +inf) takes the largest key.  A
+// float32 collection walked against a float64 one is packed the same way
+// (its times are exact in float64: lo = 0).
+template <typename Tin>
+__global__ void pack_keyed_kernel(const int64_t* __restrict__ offsets,
+                                  const Tin* __restrict__ times, const Tin* __restrict__ values,
+                                  int64_t n, const int32_t* __restrict__ perm,
+                                  const int32_t* __restrict__ slen, const int64_t* __restrict__ poff,
+                                  KElem* __restrict__ packed, KeyOut ko, const Header* hdr)
+{
+    if (hdr->err != kNoError) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int64_t kbase = ko.base_poff ? ko.base_poff[ko.base_n] - ko.base_n : 0;
+    for (int64_t s = warp0; s < n; s += nwarps) {
+        const int64_t src = perm[s];
+        const int64_t o = offsets[src];
+        const int64_t len = slen[s];
+        const int64_t dst = poff[s];
+        for (int64_t k = lane; k < len; k += 32) {
+            KElem e;
+            e.v = (float)values[o + k];
+            if (k + 1 < len) {
+                const double te = (double)times[o + k + 1];
+                const float hi = __double2float_rn(te);
+                e.k = 0;
+                e.hi = hi;
+                e.lo = __double2float_rn(te - (double)hi);
+                const int64_t j = kbase + dst - s + k;
+                ko.key[j] = (uint64_t)__double_as_longlong(te + 0.0);   // -0 -> +0 (not a te)
+                ko.pay[j] = ko.set_bit | (uint32_t)(dst + k);
+            } else {
+                e.k = kKeyInf;
+                e.hi = INFINITY;
+                e.lo = 0.f;
+            }
+            packed[dst + k] = e;
+        }
+    }
+}
+
 size_t set_bytes(int64_t n, int64_t nnz, int elem_bytes)
 {
     size_t b = 0;
@@ -296,46 +343,47 @@ static int grid_for_warps(int64_t warps)
 }
 
 cudaError_t launch_validate(const int64_t* offsets, const void* times, const void* values,
-                            int in_dtype, int64_t n, int64_t nnz_total, int walk_f64,
+                            int in_dtype, int64_t n, int64_t nnz_total, int form,
                             Header* hdr, SetView& sv, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
     const int g = grid_for_warps(n);
+    const int walk_f32 = form != kPackF64;
     if (in_dtype == PCF_F64) {
         validate_kernel<double><<<g, 256, 0, s>>>(offsets, (const double*)times,
-            (const double*)values, n, nnz_total, 1, !walk_f64, sv.lens, sv.skey, hdr, sv.slot);
+            (const double*)values, n, nnz_total, 1, walk_f32, sv.lens, sv.skey, hdr, sv.slot);
     } else {
         validate_kernel<float><<<g, 256, 0, s>>>(offsets, (const float*)times,
-            (const float*)values, n, nnz_total, 1, !walk_f64, sv.lens, sv.skey, hdr, sv.slot);
+            (const float*)values, n, nnz_total, 1, walk_f32, sv.lens, sv.skey, hdr, sv.slot);
     }
     return cudaGetLastError();
 }
 
-cudaError_t prepare_set(const int64_t* offsets, const void* times, const void* values,
-                        int in_dtype, int64_t n, int64_t nnz_total, bool whole,
-                        int walk_f64, Header* hdr, SetView& sv, cudaStream_t s)
+cudaError_t pack_set(const int64_t* offsets, const void* times, const void* values, int in_dtype,
+                     int64_t n, int form, Header* hdr, SetView& sv, cudaStream_t s,
+                     const KeyOut* ko)
 {
     if (n == 0) return cudaSuccess;
     const int g = grid_for_warps(n);
-    if (in_dtype == PCF_F64) {
-        validate_kernel<double><<<g, 256, 0, s>>>(offsets, (const double*)times,
-            (const double*)values, n, nnz_total, whole, !walk_f64, sv.lens, sv.skey, hdr, sv.slot);
-    } else {
-        validate_kernel<float><<<g, 256, 0, s>>>(offsets, (const float*)times,
-            (const float*)values, n, nnz_total, whole, !walk_f64, sv.lens, sv.skey, hdr, sv.slot);
-    }
-    sort_scan_kernel<<<1, kSortThreads, 0, s>>>(sv.lens, sv.skey, n, hdr, sv.slot, sv.perm, sv.slen,
-                                                 sv.khi[0], sv.klo[0], sv.kv[0], sv.khi[1],
-                                                 sv.klo[1], sv.kv[1], sv.poff);
-    if (in_dtype == PCF_F64) {
-        if (walk_f64)
+    if (form == kPackKeyed) {
+        if (!ko) return cudaErrorInvalidValue;
+        if (in_dtype == PCF_F64)
+            pack_keyed_kernel<double><<<g, 256, 0, s>>>(offsets, (const double*)times,
+                (const double*)values, n, sv.perm, sv.slen, sv.poff,
+                reinterpret_cast<KElem*>(sv.packed), *ko, hdr);
+        else
+            pack_keyed_kernel<float><<<g, 256, 0, s>>>(offsets, (const float*)times,
+                (const float*)values, n, sv.perm, sv.slen, sv.poff,
+                reinterpret_cast<KElem*>(sv.packed), *ko, hdr);
+    } else if (in_dtype == PCF_F64) {
+        if (form == kPackF64)
             pack_kernel<double, double><<<g, 256, 0, s>>>(offsets, (const double*)times,
                 (const double*)values, n, sv.perm, sv.slen, sv.poff, sv.packed, hdr);
         else
             pack_kernel<double, float><<<g, 256, 0, s>>>(offsets, (const double*)times,
                 (const double*)values, n, sv.perm, sv.slen, sv.poff, sv.packed, hdr);
     } else {
-        if (walk_f64)
+        if (form == kPackF64)
             pack_kernel<float, double><<<g, 256, 0, s>>>(offsets, (const float*)times,
                 (const float*)values, n, sv.perm, sv.slen, sv.poff, sv.packed, hdr);
         else
@@ -343,6 +391,28 @@ cudaError_t prepare_set(const int64_t* offsets, const void* times, const void* v
                 (const float*)values, n, sv.perm, sv.slen, sv.poff, sv.packed, hdr);
     }
     return cudaGetLastError();
+}
+
+cudaError_t prepare_set(const int64_t* offsets, const void* times, const void* values,
+                        int in_dtype, int64_t n, int64_t nnz_total, bool whole,
+                        int form, Header* hdr, SetView& sv, cudaStream_t s, const KeyOut* ko)
+{
+    if (n == 0) return cudaSuccess;
+    const int g = grid_for_warps(n);
+    const int walk_f32 = form != kPackF64;
+    if (in_dtype == PCF_F64) {
+        validate_kernel<double><<<g, 256, 0, s>>>(offsets, (const double*)times,
+            (const double*)values, n, nnz_total, whole, walk_f32, sv.lens, sv.skey, hdr, sv.slot);
+    } else {
+        validate_kernel<float><<<g, 256, 0, s>>>(offsets, (const float*)times,
+            (const float*)values, n, nnz_total, whole, walk_f32, sv.lens, sv.skey, hdr, sv.slot);
+    }
+    sort_scan_kernel<<<1, kSortThreads, 0, s>>>(sv.lens, sv.skey, n, hdr, sv.slot, sv.perm, sv.slen,
+                                                 sv.khi[0], sv.klo[0], sv.kv[0], sv.khi[1],
+                                                 sv.klo[1], sv.kv[1], sv.poff);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return pack_set(offsets, times, values, in_dtype, n, form, hdr, sv, s, ko);
 }
 
 }  // namespace pcfgb

@@ -591,7 +591,7 @@ cudaError_t rp_validate_pack(const pcf_csr* x, Header* hdr, int32_t* lens, uint3
 {
     SetView sv;
     sv.n = x->n; sv.nnz = x->nnz; sv.lens = lens; sv.skey = skey; sv.slot = slot;
-    cudaError_t e = launch_validate(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz, 1,
+    cudaError_t e = launch_validate(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz, kPackF64,
                                     hdr, sv, s);
     if (e != cudaSuccess) return e;
     if (x->nnz == 0) return cudaSuccess;

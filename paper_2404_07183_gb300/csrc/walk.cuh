@@ -30,8 +30,18 @@
 // tie).  The two loads are predicated per lane: f-loads only touch the row
 // regions and g-loads only the column regions, so each stays bank-conflict
 // free.  A breakpoint shared by both PCFs costs one extra step whose rectangle
-// has width 0 and adds an exact zero.  The step count of a pair is
-// n_f + n_g - 2 plus the tail, known before the walk starts.
+// has width 0 (h * 0 = 0 added to the accumulator).  The step count of a pair
+// is n_f + n_g - 2 plus the tail, known before the walk starts.
+//
+// Keyed form (KEYED = 1: float64 input walked in float32).  Interval elements
+// are KElem: the end time's exact order key (its rank among the call's
+// interval ends, keys.cu), the end time as float32 hi + lo, and the value.
+// The advancing side is chosen by one unsigned compare of the keys, so every
+// comparison is decided on the float64 times, and a rectangle's width is
+// (hi_n - hi_c) + (lo_n - lo_c): hi_n - hi_c is exact when the hi parts are
+// within a factor 2 of each other (Sterbenz) and the lo parts carry the rest
+// of the float64 difference, so the width is within about u * w + 2^-48 * t
+// of the exact one (hi + lo holds about 48 bits of t) instead of u * t.
 #pragma once
 
 #include <cmath>
@@ -62,6 +72,20 @@ __host__ __device__ constexpr int combo_metric(int c, int slot)
 template <typename T> struct ElemOf;
 template <> struct ElemOf<float> { using type = float2; };
 template <> struct ElemOf<double> { using type = double2; };
+
+// Element type, order-key type and accessors of a walk form.
+template <typename T, bool KEYED> struct WalkForm {
+    using E = typename ElemOf<T>::type;
+    using K = T;                 // interval ends are compared as values
+    static __device__ __forceinline__ K key(const E& e) { return e.x; }
+    static __device__ __forceinline__ T val(const E& e) { return e.y; }
+};
+template <> struct WalkForm<float, true> {
+    using E = KElem;
+    using K = uint32_t;          // interval ends are compared by their order keys
+    static __device__ __forceinline__ K key(const E& e) { return e.k; }
+    static __device__ __forceinline__ float val(const E& e) { return e.v; }
+};
 
 // h(a, b) of Sec. 2.2 for one metric, in the walk type.
 template <int MI, typename T>
@@ -205,6 +229,28 @@ __device__ __forceinline__ void advance_cursor(unsigned& af, double& tf, double&
                  : "memory");
 }
 
+// Keyed form: the side whose interval ends first is the one with the smaller
+// order key (f on equal keys, i.e. equal float64 times); it advances and its
+// next KElem (key, hi, lo, value) is loaded in place.
+template <unsigned kRowBytes>
+__device__ __forceinline__ void advance_cursor_keyed(unsigned& af, uint32_t& kf, float& hf,
+                                                     float& lf, float& vf, unsigned& ag,
+                                                     uint32_t& kg, float& hg, float& lg, float& vg)
+{
+    asm volatile("{\n\t"
+                 ".reg .pred p;\n\t"
+                 "setp.le.u32 p, %1, %6;\n\t"
+                 "@p add.u32 %0, %0, %10;\n\t"
+                 "@p ld.shared.v4.b32 {%1, %2, %3, %4}, [%0];\n\t"
+                 "@!p add.u32 %5, %5, %10;\n\t"
+                 "@!p ld.shared.v4.b32 {%6, %7, %8, %9}, [%5];\n\t"
+                 "}"
+                 : "+r"(af), "+r"(kf), "+f"(hf), "+f"(lf), "+f"(vf),
+                   "+r"(ag), "+r"(kg), "+f"(hg), "+f"(lg), "+f"(vg)
+                 : "n"(kRowBytes)
+                 : "memory");
+}
+
 __device__ __forceinline__ float first_end(float a, float b) { return fminf(a, b); }
 __device__ __forceinline__ double first_end(double a, double b)
 {
@@ -272,21 +318,24 @@ __device__ __forceinline__ void decode_tile(const WalkArgs& a, int64_t t, int64_
 // same shard.
 // WEIGHT: 0 = plain integrals, 1 = integrands weighted by exp(-lambda t).
 // Integration bounds [lo, hi] (WalkArgs) apply to every variant.
-template <typename T, int PREC, int COMBO, int THREADS, int CTAS, int WEIGHT = 0>
+template <typename T, int PREC, int COMBO, int THREADS, int CTAS, int WEIGHT = 0, bool KEYED = false>
 __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
 {
-    using E = typename ElemOf<T>::type;
+    using WF = WalkForm<T, KEYED>;
+    using E = typename WF::E;
+    using K = typename WF::K;                       // order key of an interval end
     constexpr int NM = combo_n(COMBO);
     constexpr int TCOLS = THREADS / 32;             // columns per work unit (32 or 16)
     constexpr int UNITS = kTile / TCOLS;            // work units per 32 x 32 tile
     constexpr int NPCF = kTile + TCOLS;             // staged PCFs: 32 rows + TCOLS columns
     constexpr unsigned kRow = kGroup * sizeof(E);   // bytes between element k and k+1 of a PCF
     static_assert(THREADS == 1024 || THREADS == 512, "thread count");
+    static_assert(!KEYED || sizeof(T) == 4, "keyed walks are float32 walks");
 
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int32_t sS[kTilePcfs], sNext[kTilePcfs], sLen[kTilePcfs], sStaged[kTilePcfs];
     __shared__ int64_t sOff[kTilePcfs];
-    __shared__ T sT1part[2];
+    __shared__ K sT1part[2];
     __shared__ int64_t sTile;
 
     if (block_sees_error(a.hdr)) return;
@@ -298,11 +347,24 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
     const unsigned smem_base = (unsigned)__cvta_generic_to_shared(smem);
     const E* packR = reinterpret_cast<const E*>(a.pack_r);
     const E* packC = reinterpret_cast<const E*>(a.pack_c);
-    const T lo = (T)a.lo, hi = (T)a.hi;             // bounds in the walk type
+    // bounds as order keys: the values themselves, or (keyed) the keys the
+    // key sort gave a and b; [0, inf) needs no lookup (1 orders below every
+    // end, kKeyInf is the key of te = +inf)
+    K lo, hi;
+    if constexpr (KEYED) {
+        lo = a.bound_keys ? (K)a.bound_keys[0] : (K)1u;
+        hi = a.bound_keys ? (K)a.bound_keys[1] : (K)kKeyInf;
+    } else {
+        lo = (T)a.lo;
+        hi = (T)a.hi;
+    }
     // the walk closes at hi (no tail rule) when hi is finite or the weight
     // makes the last rectangle [t_last, inf) finite: exp(-lam t_last) / lam
-    const bool bounded = hi < T(INFINITY) || WEIGHT != 0;
+    bool bounded;
+    if constexpr (KEYED) bounded = !isinf(a.hi) || WEIGHT != 0;
+    else bounded = hi < T(INFINITY) || WEIGHT != 0;
     const T lam = (T)a.lambda, inv_lam = WEIGHT ? T(1) / (T)a.lambda : T(0);
+    const K k_start = lo;                           // key of the walk's first time
 
     // this lane's pair inside every work unit
     const int my_r = (lane + warp) & 31;
@@ -338,13 +400,13 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                 sOff[tid] = 0;
             }
             int start = 0;
-            if (lo > T(0) && sLen[tid] > 0) {
+            if (a.lo > 0.0 && sLen[tid] > 0) {
                 // first element whose interval ends at or after lo
                 const E* src = (is_row ? packR : packC) + sOff[tid];
                 int l = 0, h = sLen[tid] - 1;
                 while (l < h) {
                     const int m = (l + h) >> 1;
-                    if (src[m].x < lo) l = m + 1; else h = m;
+                    if (WF::key(src[m]) < lo) l = m + 1; else h = m;
                 }
                 start = l;
             }
@@ -355,30 +417,34 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
         const bool lane_valid = (bi * kTile + my_r < a.n_r) && (col0 + my_c < a.n_c);
 
         typename AccFor<PREC, COMBO>::type acc;
-        T tc = lo;
-        T T0 = lo;              // start of the current window (block-uniform)
+        // the current time tc: a value, or (keyed) float32 hi + lo
+        T tc = T(0), tcl = T(0);
+        if constexpr (KEYED) { tc = a.lo_hl[0]; tcl = a.lo_hl[1]; }
+        else tc = (T)a.lo;
+        K T0 = k_start;         // start of the current window (block-uniform)
         __syncthreads();
 
         for (bool first = true;; first = false) {
             // ---- advance the window starts; window end T1 = min over PCFs of
             //      te[S + W - 1] (clamped to the last element) ----
             if (tid < 64) {
-                T cand = T(INFINITY);
+                K cand;
+                if constexpr (KEYED) cand = (K)kKeyInf; else cand = T(INFINITY);
                 const int len = tid < NPCF ? sLen[tid] : 0;
                 if (len > 0) {
                     if (!first) sS[tid] = sNext[tid];
                     int idx = sS[tid] + W - 1;
                     if (idx > len - 1) idx = len - 1;
-                    cand = (tid < kTile ? packR : packC)[sOff[tid] + idx].x;
+                    cand = WF::key((tid < kTile ? packR : packC)[sOff[tid] + idx]);
                 }
                 for (int o = 16; o > 0; o >>= 1) {
-                    T other = __shfl_xor_sync(0xffffffffu, cand, o);
+                    K other = __shfl_xor_sync(0xffffffffu, cand, o);
                     cand = other < cand ? other : cand;
                 }
                 if (lane == 0) sT1part[warp] = cand;
             }
             __syncthreads();
-            T T1 = sT1part[0] < sT1part[1] ? sT1part[0] : sT1part[1];
+            K T1 = sT1part[0] < sT1part[1] ? sT1part[0] : sT1part[1];
             if (T1 > hi) T1 = hi;
             const bool last = !(T1 < hi);
             if (!(T1 > T0)) {
@@ -437,13 +503,13 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                     int cnt = len - sS[tid];
                     if (cnt > W) cnt = W;
                     const unsigned colbase = (unsigned)(tid >> 4) * regionBytes + (unsigned)(tid & 15) * sizeof(E);
-                    int lo = 0, hi = cnt - 1;          // te[hi] >= T1 holds by the choice of T1
-                    while (lo < hi) {
-                        int mid = (lo + hi) >> 1;
-                        T te = reinterpret_cast<const E*>(smem + colbase + (unsigned)mid * kRow)->x;
-                        if (te < T1) lo = mid + 1; else hi = mid;
+                    int lo2 = 0, hi2 = cnt - 1;        // te[hi2] >= T1 holds by the choice of T1
+                    while (lo2 < hi2) {
+                        int mid = (lo2 + hi2) >> 1;
+                        const K te = WF::key(*reinterpret_cast<const E*>(smem + colbase + (unsigned)mid * kRow));
+                        if (te < T1) lo2 = mid + 1; else hi2 = mid;
                     }
-                    next = sS[tid] + lo;
+                    next = sS[tid] + lo2;
                 }
                 sNext[tid] = next;
                 sStaged[tid] = sS[tid];
@@ -456,32 +522,68 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                 unsigned af = smem_base + base_f, ag = smem_base + base_g;
                 const E ef = *reinterpret_cast<const E*>(smem + base_f);
                 const E eg = *reinterpret_cast<const E*>(smem + base_g);
-                T tf = ef.x, tg = eg.x, vf = ef.y, vg = eg.y;
+                if constexpr (KEYED) {
+                    uint32_t kf = ef.k, kg = eg.k;
+                    float hf = ef.hi, lf = ef.lo, vf = ef.v;
+                    float hg = eg.hi, lg = eg.lo, vg = eg.v;
+                    // width of [tc, te_n) from the hi and lo parts of both ends
 #define PCF_WALK_STEP()                                                           \
-                {                                                                 \
-                    const T tn = first_end(tf, tg);                               \
-                    const T dt = weight_span<WEIGHT>(tc, tn - tc, lam, inv_lam);   \
-                    tc = tn;                                                      \
-                    acc.add(vf, vg, dt, p0);                                      \
-                    advance_cursor<kRow>(af, tf, vf, ag, tg, vg);                 \
-                }
+                    {                                                             \
+                        const bool fe = kf <= kg;                                 \
+                        const float hn = fe ? hf : hg, ln = fe ? lf : lg;         \
+                        const float w = __fadd_rn(__fsub_rn(hn, tc), __fsub_rn(ln, tcl)); \
+                        const float dt = weight_span<WEIGHT>(tc, w, lam, inv_lam); \
+                        tc = hn;                                                  \
+                        tcl = ln;                                                 \
+                        acc.add(vf, vg, dt, p0);                                  \
+                        advance_cursor_keyed<kRow>(af, kf, hf, lf, vf, ag, kg, hg, lg, vg); \
+                    }
 #pragma unroll 1
-                for (; cnt >= 16; cnt -= 16) {
-                    PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
-                    PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
-                    PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
-                    PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
-                    acc.flush();
-                }
+                    for (; cnt >= 16; cnt -= 16) {
+                        PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
+                        PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
+                        PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
+                        PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
+                        acc.flush();
+                    }
 #pragma unroll 1
-                for (; cnt > 0; --cnt) PCF_WALK_STEP()
-                if (last && bounded) {
-                    // closing rectangle [tc, hi) with the values holding at hi
-                    acc.add(vf, vg, weight_span<WEIGHT>(tc, hi - tc, lam, inv_lam), p0);
-                    tc = hi;
+                    for (; cnt > 0; --cnt) PCF_WALK_STEP()
+#undef PCF_WALK_STEP
+                    if (last && bounded) {
+                        // closing rectangle [tc, hi) with the values holding at hi
+                        const float w = __fadd_rn(__fsub_rn(a.hi_hl[0], tc), __fsub_rn(a.hi_hl[1], tcl));
+                        acc.add(vf, vg, weight_span<WEIGHT>(tc, w, lam, inv_lam), p0);
+                        tc = a.hi_hl[0];
+                        tcl = a.hi_hl[1];
+                    }
+                } else {
+                    T tf = ef.x, tg = eg.x, vf = ef.y, vg = eg.y;
+#define PCF_WALK_STEP()                                                           \
+                    {                                                             \
+                        const T tn = first_end(tf, tg);                           \
+                        const T dt = weight_span<WEIGHT>(tc, tn - tc, lam, inv_lam); \
+                        tc = tn;                                                  \
+                        acc.add(vf, vg, dt, p0);                                  \
+                        advance_cursor<kRow>(af, tf, vf, ag, tg, vg);             \
+                    }
+#pragma unroll 1
+                    for (; cnt >= 16; cnt -= 16) {
+                        PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
+                        PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
+                        PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
+                        PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP() PCF_WALK_STEP()
+                        acc.flush();
+                    }
+#pragma unroll 1
+                    for (; cnt > 0; --cnt) PCF_WALK_STEP()
+#undef PCF_WALK_STEP
+                    if (last && bounded) {
+                        // closing rectangle [tc, hi) with the values holding at hi
+                        acc.add(vf, vg, weight_span<WEIGHT>(tc, hi - tc, lam, inv_lam), p0);
+                        tc = hi;
+                    }
                 }
                 acc.flush();
-#undef PCF_WALK_STEP
             }
             __syncthreads();
             if (last) break;
@@ -493,8 +595,8 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
             const int64_t gi = bi * kTile + my_r, gj = col0 + my_c;
             const int64_t i = a.perm_r[gi], j = a.perm_c[gj];
             // values on the last intervals [t_last, inf) of both PCFs
-            const T vlf = packR[sOff[pf] + sLen[pf] - 1].y;
-            const T vlg = packC[sOff[pg] + sLen[pg] - 1].y;
+            const T vlf = WF::val(packR[sOff[pf] + sLen[pf] - 1]);
+            const T vlg = WF::val(packC[sOff[pg] + sLen[pg] - 1]);
 #pragma unroll
             for (int m = 0; m < NM; ++m) {
                 const int MI = combo_metric(COMBO, m);
@@ -517,8 +619,8 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                     if (bi != bj) put(gj * a.ld_out + gi);
                 } else {
                     const int64_t N = a.ld_out;
-                    const int64_t lo = i < j ? i : j, hi = i < j ? j : i;
-                    if (bi != bj || i <= j) put(lo * N - lo * (lo - 1) / 2 + (hi - lo));
+                    const int64_t lo2 = i < j ? i : j, hi2 = i < j ? j : i;
+                    if (bi != bj || i <= j) put(lo2 * N - lo2 * (lo2 - 1) / 2 + (hi2 - lo2));
                 }
             }
         }
@@ -526,7 +628,8 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
     }
 }
 
-template <typename T, int PREC, int THREADS, int CTAS = 1024 / THREADS, int WEIGHT = 0>
+template <typename T, int PREC, int THREADS, int CTAS = 1024 / THREADS, int WEIGHT = 0,
+          bool KEYED = false>
 cudaError_t launch_walk_tt(int combo, const WalkArgs& a, int grid, size_t smem, cudaStream_t s)
 {
     auto go = [&](auto kern) -> cudaError_t {
@@ -536,13 +639,13 @@ cudaError_t launch_walk_tt(int combo, const WalkArgs& a, int grid, size_t smem, 
         return cudaGetLastError();
     };
     switch (combo) {
-    case kComboL1: return go(walk_kernel<T, PREC, kComboL1, THREADS, CTAS, WEIGHT>);
-    case kComboL2: return go(walk_kernel<T, PREC, kComboL2, THREADS, CTAS, WEIGHT>);
-    case kComboGram: return go(walk_kernel<T, PREC, kComboGram, THREADS, CTAS, WEIGHT>);
-    case kComboLP: return go(walk_kernel<T, PREC, kComboLP, THREADS, CTAS, WEIGHT>);
-    case kComboL3: return go(walk_kernel<T, PREC, kComboL3, THREADS, CTAS, WEIGHT>);
-    case kComboL1L2Gram: return go(walk_kernel<T, PREC, kComboL1L2Gram, THREADS, CTAS, WEIGHT>);
-    case kComboL1L2L3: return go(walk_kernel<T, PREC, kComboL1L2L3, THREADS, CTAS, WEIGHT>);
+    case kComboL1: return go(walk_kernel<T, PREC, kComboL1, THREADS, CTAS, WEIGHT, KEYED>);
+    case kComboL2: return go(walk_kernel<T, PREC, kComboL2, THREADS, CTAS, WEIGHT, KEYED>);
+    case kComboGram: return go(walk_kernel<T, PREC, kComboGram, THREADS, CTAS, WEIGHT, KEYED>);
+    case kComboLP: return go(walk_kernel<T, PREC, kComboLP, THREADS, CTAS, WEIGHT, KEYED>);
+    case kComboL3: return go(walk_kernel<T, PREC, kComboL3, THREADS, CTAS, WEIGHT, KEYED>);
+    case kComboL1L2Gram: return go(walk_kernel<T, PREC, kComboL1L2Gram, THREADS, CTAS, WEIGHT, KEYED>);
+    case kComboL1L2L3: return go(walk_kernel<T, PREC, kComboL1L2L3, THREADS, CTAS, WEIGHT, KEYED>);
     default: return cudaErrorInvalidValue;
     }
 }
