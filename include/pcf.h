@@ -104,6 +104,18 @@ enum pcf_precision {
  * (pcf_prepare, PCF_PAIRWISE_PREPARED) must pass the same precision value. */
 #define PCF_PREC_ROUND_TIMES 0x100
 
+/* PCF_PREC_AUTO64, or-ed into a float32 precision: walk in that float32
+ * precision unless the input's dynamic range asks for float64, decided on
+ * the device during validation with no host synchronization (both walks are
+ * enqueued; the one not needed returns at once).  A float64 collection needs
+ * the float64 walk when a time or value lies outside float32's normal range
+ * (above FLT_MAX, or nonzero below FLT_MIN; without this bit such input is
+ * rejected, reason 6) or when a gap t_{k+1} - t_k is below 2^-30 t_{k+1} (the
+ * float32 walk resolves widths to about 2^-48 t).  The float64 walk's results
+ * are those of PCF_PREC_F64.  pcf_walk_promoted reports which walk ran.  The
+ * workspace is sized for both forms.  Invalid with PCF_PREC_F64. */
+#define PCF_PREC_AUTO64 0x200
+
 /* Output layout of the pairwise matrix. */
 enum pcf_layout {
     PCF_OUT_FULL = 0,          /* N x N row-major, both triangles written      */
@@ -505,6 +517,14 @@ int pcf_selftest_wait_timeout(int64_t polls, void* workspace, size_t workspace_b
  */
 int pcf_pairwise_noalloc(const pcf_csr* x, const pcf_integral* F, int nF, int precision,
                          int layout, int out_dtype, cudaStream_t stream);
+
+/*
+ * After a call made with PCF_PREC_AUTO64 on `workspace` (pcf_prepare,
+ * pcf_pairwise, pcf_pairwise_to_host, pcf_cross): synchronizes `stream` and
+ * sets *promoted to 1 when the float64 walk ran (the input's dynamic range
+ * asked for it), 0 when the float32 walk did.  PCF_EINVAL for null pointers.
+ */
+int pcf_walk_promoted(const void* workspace, cudaStream_t stream, int* promoted);
 
 /* Static text for a status code. */
 const char* pcf_status_string(int status);

@@ -16,6 +16,7 @@ PCF_F32, PCF_F64 = 0, 1
 PCF_L1, PCF_L2, PCF_LP, PCF_GRAM = 0, 1, 2, 3
 PCF_PREC_F64, PCF_PREC_F32_COMP, PCF_PREC_F32, PCF_PREC_F32_BLOCK = 0, 1, 2, 3
 PCF_PREC_ROUND_TIMES = 0x100
+PCF_PREC_AUTO64 = 0x200
 PCF_OUT_FULL, PCF_OUT_UPPER_PACKED, PCF_OUT_FULL_SORTED = 0, 1, 2
 PCF_WS_FORWARD, PCF_WS_BACKWARD = 0, 1
 PCF_CROSS_REUSE_B = 1
@@ -36,6 +37,7 @@ ERR_DETAIL = {
 
 SYMBOLS = ("pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross", "pcf_pairwise_backward",
            "pcf_check", "pcf_status_string", "pcf_version", "pcf_pairwise_noalloc",
+           "pcf_walk_promoted",
            "pcf_pairwise_ex", "pcf_cross_ex", "pcf_sort_order", "pcf_segment_integrals",
            "pcf_reduce_workspace_size", "pcf_reduce", "pcf_combine_workspace_size",
            "pcf_combine", "pcf_reduce_counters", "pcf_selftest_wait_timeout",
@@ -128,6 +130,8 @@ def load(build_if_missing: bool = False):
         lib.pcf_pairwise_backward_ex.argtypes = [CSR, I, D, I, P, P, I, P, P, SCH, P, SZ, P]
         lib.pcf_check.restype = I
         lib.pcf_check.argtypes = [P, P, ctypes.POINTER(I), ctypes.POINTER(I64)]
+        lib.pcf_walk_promoted.restype = I
+        lib.pcf_walk_promoted.argtypes = [P, P, ctypes.POINTER(I)]
         lib.pcf_status_string.restype = ctypes.c_char_p
         lib.pcf_status_string.argtypes = [I]
         lib.pcf_pairwise_noalloc.restype = I

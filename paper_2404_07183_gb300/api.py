@@ -25,7 +25,7 @@ __all__ = ["PcfError", "PcfTensors", "pcf_workspace_size", "pcf_prepare", "pcf_s
            "pcf_segment_integrals",
            "pcf_pairwise", "pcf_cross",
            "pcf_cross_to_host",
-           "pcf_pairwise_backward", "pcf_check", "PairwiseFn", "PairwiseGraph", "pdist",
+           "pcf_pairwise_backward", "pcf_check", "pcf_walk_promoted", "PairwiseFn", "PairwiseGraph", "pdist",
            "l2_kernel", "pcf_reduce", "pcf_combine", "pcf_reduce_counters", "mean", "std",
            "parse_metric", "PRECISIONS", "REDUCTIONS", "OPS"]
 
@@ -34,7 +34,11 @@ PRECISIONS = {"f64": abi.PCF_PREC_F64, "f32c": abi.PCF_PREC_F32_COMP, "f32": abi
               # float64 times rounded to float32 when packed (opt-in, faster)
               "f32c_round": abi.PCF_PREC_F32_COMP | abi.PCF_PREC_ROUND_TIMES,
               "f32_round": abi.PCF_PREC_F32 | abi.PCF_PREC_ROUND_TIMES,
-              "f32b_round": abi.PCF_PREC_F32_BLOCK | abi.PCF_PREC_ROUND_TIMES}
+              "f32b_round": abi.PCF_PREC_F32_BLOCK | abi.PCF_PREC_ROUND_TIMES,
+              # float32 walk unless the input's dynamic range needs float64
+              "f32c_auto64": abi.PCF_PREC_F32_COMP | abi.PCF_PREC_AUTO64,
+              "f32_auto64": abi.PCF_PREC_F32 | abi.PCF_PREC_AUTO64,
+              "f32b_auto64": abi.PCF_PREC_F32_BLOCK | abi.PCF_PREC_AUTO64}
 REDUCTIONS = {"sum": abi.PCF_RED_SUM, "mean": abi.PCF_RED_MEAN, "max": abi.PCF_RED_MAX,
               "min": abi.PCF_RED_MIN, "std": abi.PCF_RED_STD}
 OPS = {"add": abi.PCF_OP_ADD, "sub": abi.PCF_OP_SUB, "mul": abi.PCF_OP_MUL, "max": abi.PCF_OP_MAX,
@@ -183,6 +187,18 @@ def pcf_check(workspace: torch.Tensor, stream=None, what="pcf"):
                        ctypes.byref(detail), ctypes.byref(index))
     if rc != abi.PCF_OK:
         raise PcfError(rc, what, detail.value, index.value)
+
+
+def pcf_walk_promoted(workspace: torch.Tensor, stream=None) -> bool:
+    """True when the last PCF_PREC_AUTO64 call on `workspace` ran the float64
+    walk (synchronizes)."""
+    lib = abi.load()
+    out = ctypes.c_int(0)
+    rc = lib.pcf_walk_promoted(ctypes.c_void_p(workspace.data_ptr()), _stream_handle(stream),
+                               ctypes.byref(out))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_walk_promoted")
+    return bool(out.value)
 
 
 def _requests(metrics, outs):

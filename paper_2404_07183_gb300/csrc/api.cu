@@ -7,6 +7,7 @@
 // or, for the adjoint, the recomputing gradient walk and a scatter back to
 // the input order.  Nothing is allocated and nothing is synchronized.
 #include <cmath>
+#include <cstddef>
 #include <cstring>
 #include <vector>
 
@@ -40,6 +41,7 @@ __global__ void init_header_kernel(Header* h, int keep_set1)
     h->err = kNoError;
     h->maxlen[0] = 0;
     if (!keep_set1) h->maxlen[1] = 0;
+    h->need64 = keep_set1 ? (h->need64 & 2u) : 0u;   // a reused set 1 keeps its need
     h->tiles = 0;
 }
 
@@ -125,17 +127,27 @@ bool csr_ok(const pcf_csr* x)
 struct Prec {
     int base = PCF_PREC_F64;
     bool round = false;
+    bool auto64 = false;     // float32 walk unless the input needs the float64 one
 };
 
 bool parse_prec(int precision, Prec* out)
 {
-    const int base = precision & ~PCF_PREC_ROUND_TIMES;
+    const int base = precision & ~(PCF_PREC_ROUND_TIMES | PCF_PREC_AUTO64);
     if (base < PCF_PREC_F64 || base > PCF_PREC_F32_BLOCK) return false;
     const bool round = (precision & PCF_PREC_ROUND_TIMES) != 0;
-    if (round && base == PCF_PREC_F64) return false;
+    const bool auto64 = (precision & PCF_PREC_AUTO64) != 0;
+    if ((round || auto64) && base == PCF_PREC_F64) return false;
     out->base = base;
     out->round = round;
+    out->auto64 = auto64;
     return true;
+}
+
+// Element bytes of a call's packed buffers: an AUTO64 call may pack either
+// its float32 form or the float64 one into them.
+int call_elem_bytes(const Prec& p, int form)
+{
+    return p.auto64 ? 16 : pack_elem_bytes(form);
 }
 
 // How the call's collections are packed: float64 walk; float32 walk of
@@ -346,6 +358,27 @@ int run_walks(WalkArgs& wa, const pcf_integral* F, int nF, int precision, int fo
     return PCF_OK;
 }
 
+// The walks of a call: the float32 form, or for AUTO64 both the float32 and
+// the float64 walks, each gated on the device-side need (one of them returns
+// at once).
+int run_walks_for(WalkArgs& wa, const pcf_integral* F, int nF, const Prec& pr, int form,
+                  const pcf_schedule* sched, const pcf_window* win, cudaStream_t s,
+                  int64_t unit0 = 0)
+{
+    if (!pr.auto64 || form == kPackF64) {
+        wa.gate = nullptr;
+        return run_walks(wa, F, nF, pr.base, form, sched, win, s, unit0);
+    }
+    wa.gate = &wa.hdr->need64;
+    wa.gate_want64 = 0;
+    int rc = run_walks(wa, F, nF, pr.base, form, sched, win, s, unit0);
+    if (rc != PCF_OK) return rc;
+    WalkArgs w64 = wa;
+    w64.gate_want64 = 1;
+    w64.bound_keys = nullptr;
+    return run_walks(w64, F, nF, PCF_PREC_F64, kPackF64, sched, win, s, unit0);
+}
+
 // Bands of the symmetric tile order for streaming a matrix to the host.  The
 // walk takes the tiles (bi, bj), bi <= bj, row block by row block from the
 // first (shortest PCFs) up (WalkArgs::tile_order = 1); once row blocks
@@ -391,7 +424,7 @@ int pcf_workspace_size(const pcf_csr* x, const pcf_csr* y, int precision, int pu
     if (!parse_prec(precision, &pr)) return PCF_EINVAL;
     if (purpose != PCF_WS_FORWARD && purpose != PCF_WS_BACKWARD) return PCF_EINVAL;
     const int form = purpose == PCF_WS_BACKWARD ? kPackF64 : call_form(pr, x, y);
-    const int es = pack_elem_bytes(form);
+    const int es = purpose == PCF_WS_BACKWARD ? 16 : call_elem_bytes(pr, form);
     size_t b = sizeof(Header);
     if (y) b += set_bytes(y->n, y->nnz, es);
     b += set_bytes(x->n, x->nnz, es);
@@ -415,7 +448,7 @@ static int pairwise_common(const pcf_csr* x, int precision, void* workspace,
     char* cur = (char*)workspace;
     *hdr_out = (Header*)cur;
     cur += sizeof(Header);
-    *sv_out = carve_set(cur, x->n, x->nnz, pack_elem_bytes(form), 0);
+    *sv_out = carve_set(cur, x->n, x->nnz, call_elem_bytes(pr, form), 0);
     if (form == kPackKeyed && ks_out) *ks_out = carve_keysort(cur, key_capacity(x, nullptr));
     if (form_out) *form_out = form;
     return PCF_OK;
@@ -424,12 +457,12 @@ static int pairwise_common(const pcf_csr* x, int precision, void* workspace,
 // Validate, length-sort and pack one collection for a pairwise call; the
 // keyed form also ranks its interval ends.
 static cudaError_t prepare_pairwise(const pcf_csr* x, int form, Header* hdr, SetView& sv,
-                                    const KeySort& ks, cudaStream_t s)
+                                    const KeySort& ks, cudaStream_t s, bool auto64)
 {
     KeyOut ko;
     if (form == kPackKeyed) { ko.key = ks.key[0]; ko.pay = ks.pay[0]; }
     cudaError_t e = prepare_set(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz, true,
-                                form, hdr, sv, s, form == kPackKeyed ? &ko : nullptr);
+                                form, hdr, sv, s, form == kPackKeyed ? &ko : nullptr, auto64);
     if (e != cudaSuccess || form != kPackKeyed) return e;
     return rank_keys(ks, reinterpret_cast<KElem*>(sv.packed), sv.poff, x->n, nullptr, nullptr, 0,
                      hdr, s);
@@ -466,7 +499,7 @@ int pcf_prepare(const pcf_csr* x, int precision, void* workspace, size_t workspa
     if (rc != PCF_OK) return rc;
     init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
     if (x->n == 0) return cudaGetLastError() == cudaSuccess ? PCF_OK : PCF_ECUDA;
-    if (prepare_pairwise(x, form, hdr, sv, ks, stream) != cudaSuccess) return PCF_ECUDA;
+    if (prepare_pairwise(x, form, hdr, sv, ks, stream, pr.auto64) != cudaSuccess) return PCF_ECUDA;
     return PCF_OK;
 }
 
@@ -503,7 +536,7 @@ int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precisi
     if (x->n == 0) return PCF_OK;
     if (!(flags & PCF_PAIRWISE_PREPARED)) {
         init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
-        if (prepare_pairwise(x, form, hdr, sv, ks, stream) != cudaSuccess) return PCF_ECUDA;
+        if (prepare_pairwise(x, form, hdr, sv, ks, stream, pr.auto64) != cudaSuccess) return PCF_ECUDA;
     }
 
     WalkArgs wa;
@@ -522,7 +555,7 @@ int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precisi
     wa.ld_out = x->n;
     KElem* kp = reinterpret_cast<KElem*>(sv.packed);
     keyed_bounds(wa, window, form, ks, kp, kp, hdr, stream);
-    return run_walks(wa, F, nF, pr.base, form, schedule, window, stream);
+    return run_walks_for(wa, F, nF, pr, form, schedule, window, stream);
 }
 
 int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int precision,
@@ -565,7 +598,7 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
     }
 
     init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
-    if (prepare_pairwise(x, form, hdr, sv, ks, stream) != cudaSuccess) return PCF_ECUDA;
+    if (prepare_pairwise(x, form, hdr, sv, ks, stream, pr.auto64) != cudaSuccess) return PCF_ECUDA;
     WalkArgs wa;
     memset(&wa, 0, sizeof wa);
     wa.pack_r = wa.pack_c = sv.packed;
@@ -631,7 +664,7 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
     };
     auto fail = [&](int code) { join(); return code; };
     if (sch.kernel == PCF_SCHED_MERGEPATH || nbands == 1) {
-        rc = run_walks(wa, F, nF, pr.base, form, &sch, nullptr, stream);
+        rc = run_walks_for(wa, F, nF, pr, form, &sch, nullptr, stream);
         if (rc != PCF_OK) return rc;
         if (!copy_rows(0, N)) return fail(PCF_ECUDA);
     } else {
@@ -645,7 +678,7 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
         for (size_t k = 0; k + 1 < cuts.size(); ++k) {
             const int64_t m0 = cuts[k], m1 = cuts[k + 1];
             wa.ntiles = first_tile(m1);
-            rc = run_walks(wa, F, nF, pr.base, form, &sch, nullptr, stream, first_tile(m0) * units);
+            rc = run_walks_for(wa, F, nF, pr, form, &sch, nullptr, stream, first_tile(m0) * units);
             if (rc != PCF_OK) return fail(rc);
             const int64_t s0 = m0 * kTile;
             const int64_t s1 = m1 * kTile < N ? m1 * kTile : N;
@@ -691,7 +724,7 @@ int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t 
     char* cur = (char*)workspace;
     Header* hdr = (Header*)cur;
     cur += sizeof(Header);
-    const int es = pack_elem_bytes(form);
+    const int es = call_elem_bytes(pr, form);
     SetView sb = carve_set(cur, b->n, b->nnz, es, 1);
     SetView sa = carve_set(cur, rows, a->nnz, es, 0);
     KeySort ks;
@@ -711,18 +744,27 @@ int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t 
     }
     const KeyOut* pkb = form == kPackKeyed ? &kb : nullptr;
     const KeyOut* pka = form == kPackKeyed ? &ka : nullptr;
+    const bool a64 = pr.auto64 && form != kPackF64;
     if (!reuse) {
         if (prepare_set(b->offsets, b->times, b->values, b->dtype, b->n, b->nnz, true, form, hdr, sb,
-                        stream, pkb) != cudaSuccess)
+                        stream, pkb, a64) != cudaSuccess)
             return PCF_ECUDA;
-    } else if (form == kPackKeyed) {
+    }
+    if (prepare_set(a->offsets + row_begin, a->times, a->values, a->dtype, rows, a->nnz,
+                    row_begin == 0 && row_end == a->n, form, hdr, sa, stream, pka, a64) != cudaSuccess)
+        return PCF_ECUDA;
+    if (reuse && a64) {
+        // the new rows may change the choice: B packed again in both gated forms
+        if (pack_set(b->offsets, b->times, b->values, b->dtype, b->n, form, hdr, sb, stream, pkb,
+                     &hdr->need64, 0) != cudaSuccess ||
+            pack_set(b->offsets, b->times, b->values, b->dtype, b->n, kPackF64, hdr, sb, stream,
+                     nullptr, &hdr->need64, 1) != cudaSuccess)
+            return PCF_ECUDA;
+    } else if (reuse && form == kPackKeyed) {
         if (pack_set(b->offsets, b->times, b->values, b->dtype, b->n, form, hdr, sb, stream, pkb) !=
             cudaSuccess)
             return PCF_ECUDA;
     }
-    if (prepare_set(a->offsets + row_begin, a->times, a->values, a->dtype, rows, a->nnz,
-                    row_begin == 0 && row_end == a->n, form, hdr, sa, stream, pka) != cudaSuccess)
-        return PCF_ECUDA;
     KElem* kpa = reinterpret_cast<KElem*>(sa.packed);
     KElem* kpb = reinterpret_cast<KElem*>(sb.packed);
     if (form == kPackKeyed &&
@@ -744,7 +786,7 @@ int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t 
     wa.out_f64 = out_dtype == PCF_F64;
     wa.ld_out = ld_out;
     keyed_bounds(wa, window, form, ks, kpa, kpb, hdr, stream);
-    return run_walks(wa, F, nF, pr.base, form, schedule, window, stream);
+    return run_walks_for(wa, F, nF, pr, form, schedule, window, stream);
 }
 
 int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root,
@@ -889,6 +931,19 @@ int pcf_check(const void* workspace, cudaStream_t stream, int* detail, int64_t* 
     if (reason == kErrCapacity) return PCF_ENOWS;
     if (reason == kErrWait) return PCF_ETIMEOUT;
     return PCF_EINVAL;
+}
+
+int pcf_walk_promoted(const void* workspace, cudaStream_t stream, int* promoted)
+{
+    if (!workspace || !promoted) return PCF_EINVAL;
+    unsigned int need = 0;
+    const char* w = static_cast<const char*>(workspace);
+    if (cudaMemcpyAsync(&need, w + offsetof(Header, need64), sizeof need, cudaMemcpyDeviceToHost,
+                        stream) != cudaSuccess)
+        return PCF_ECUDA;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return PCF_ECUDA;
+    *promoted = need != 0u ? 1 : 0;
+    return PCF_OK;
 }
 
 const char* pcf_status_string(int status)

@@ -49,7 +49,10 @@ struct Header {
     unsigned long long tiles;    // persistent-kernel tile counter
     unsigned long long nkeys;    // keyed walks: interval ends ranked by the key sort
     unsigned int bound_key[2];   // keyed walks: order keys of the bounds a, b
-    unsigned long long pad[27];
+    unsigned int need64;         // PCF_PREC_AUTO64: bit s set when set s needs the
+                                 // float64 walk (range or time resolution)
+    unsigned int pad32;
+    unsigned long long pad[26];
 };
 static_assert(sizeof(Header) == 256, "header is 256 bytes");
 
@@ -152,15 +155,20 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // Validate + sort + pack one collection given by absolute CSR offsets
 // (offsets[0..n]) into arrays of total length nnz_total.  When `whole` is set
 // offsets[0] must be 0 and offsets[n] must equal nnz_total.
+// auto64: the float32 form `form` is packed unless the input needs float64
+// (Header::need64, set by the validation), in which case the float64 form is
+// packed into the same buffer instead (both kernels are enqueued; each
+// returns at once when the other form is the one needed).
 cudaError_t prepare_set(const int64_t* offsets, const void* times, const void* values,
                         int in_dtype, int64_t n, int64_t nnz_total, bool whole,
                         int form, Header* hdr, SetView& sv, cudaStream_t s,
-                        const KeyOut* ko = nullptr);
+                        const KeyOut* ko = nullptr, bool auto64 = false);
 // The pack step alone (validation and length sort already done): used by
-// cross calls that reuse B's sort but must re-rank its keys.
+// cross calls that reuse B's sort but must re-rank its keys.  gate: null,
+// or run only when (*gate != 0) == want64.
 cudaError_t pack_set(const int64_t* offsets, const void* times, const void* values, int in_dtype,
                      int64_t n, int form, Header* hdr, SetView& sv, cudaStream_t s,
-                     const KeyOut* ko);
+                     const KeyOut* ko, const unsigned int* gate = nullptr, int want64 = 0);
 
 // Arguments of the tile walk kernels.
 struct WalkArgs {
@@ -192,7 +200,17 @@ struct WalkArgs {
     float lo_hl[2], hi_hl[2];    // keyed walks: lo and hi as float32 hi + lo
     const unsigned int* bound_keys;  // keyed walks with bounds: order keys of lo,
                                      // hi (device); null = [0, inf)
+    const unsigned int* gate;    // PCF_PREC_AUTO64: the launch returns at once unless
+    int gate_want64;             // (*gate != 0) == gate_want64; null = always runs
 };
+
+#ifdef __CUDACC__
+// Device-side choice between the float32 and float64 walks of an AUTO64 call.
+__device__ __forceinline__ bool gated_off(const unsigned int* gate, int want64)
+{
+    return gate && ((*gate != 0u) != (want64 != 0));
+}
+#endif
 
 // Metric combination codes compiled into the walk kernels.
 enum Combo : int {
@@ -239,6 +257,12 @@ cudaError_t launch_segments(const pcf_csr* x, int functional, double p, int appl
 cudaError_t launch_validate(const int64_t* offsets, const void* times, const void* values,
                             int in_dtype, int64_t n, int64_t nnz_total, int form,
                             Header* hdr, SetView& sv, cudaStream_t s);
+
+// AUTO64 thresholds: a float64 collection needs the float64 walk when a time
+// or value lies outside float32's normal range (above FLT_MAX, or nonzero
+// below FLT_MIN) or when a gap t_{k+1} - t_k is below 2^-30 t_{k+1} (the
+// float32 hi + lo form resolves widths to about 2^-48 t).
+constexpr double kAuto64MinRelGap = 9.313225746154785e-10;   // 2^-30
 
 int device_sm_count();
 int device_smem_optin();

@@ -72,7 +72,8 @@ KeySort carve_keysort(char*& cur, int64_t cap)
 __global__ void count_keys_kernel(Header* hdr, const int64_t* poff0, int64_t n0,
                                   const int64_t* poff1, int64_t n1)
 {
-    if (hdr->err != kNoError) { hdr->nkeys = 0; return; }
+    // no keys after an input error, or when an AUTO64 call walks in float64
+    if (hdr->err != kNoError || hdr->need64 != 0u) { hdr->nkeys = 0; return; }
     unsigned long long m = 0;
     if (poff0) m += (unsigned long long)(poff0[n0] - n0);
     if (poff1) m += (unsigned long long)(poff1[n1] - n1);

@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(256, 4) mergepath_kernel(const WalkArgs a, int
     using WF = WalkForm<T, KEYED>;
     using E = typename WF::E;
     constexpr int NM = combo_n(COMBO);
+    if (gated_off(a.gate, a.gate_want64)) return;   // the other walk of an AUTO64 call
     if (a.hdr->err != kNoError) return;
     const int lane = threadIdx.x & 31;
     const T p0 = (T)a.p[0];

@@ -18,13 +18,18 @@ __device__ __forceinline__ bool finite_val(T x) { return isfinite(x); }
 
 // One warp per PCF: check offsets, t_0 = 0, strict increase, finiteness;
 // write lengths and the running maximum length.
+// auto64 (float64 input, PCF_PREC_AUTO64): instead of rejecting a time or
+// value outside float32's range, mark the set as needing the float64 walk
+// (Header::need64 bit `slot`), likewise for nonzero values below FLT_MIN and
+// for gaps below 2^-30 of their time.
 template <typename T>
 __global__ void validate_kernel(const int64_t* __restrict__ offsets,
                                 const T* __restrict__ times, const T* __restrict__ values,
                                 int64_t n, int64_t nnz_total, int whole, int walk_f32,
                                 int32_t* __restrict__ lens, uint32_t* __restrict__ skey,
-                                Header* hdr, int slot)
+                                Header* hdr, int slot, int auto64)
 {
+    bool need64 = false;
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -59,11 +64,21 @@ __global__ void validate_kernel(const int64_t* __restrict__ offsets,
                 if (!(t > tp)) record_error(hdr, kErrOrder, k);
             }
             if (walk_f32 && sizeof(T) == 8) {
-                if (fabs((double)t) > (double)FLT_MAX || fabs((double)v) > (double)FLT_MAX)
+                const double at = fabs((double)t), av = fabs((double)v);
+                const bool out = at > (double)FLT_MAX || av > (double)FLT_MAX;
+                if (auto64) {
+                    const bool tiny = (av != 0.0 && av < (double)FLT_MIN) ||
+                                      (at != 0.0 && at < (double)FLT_MIN);
+                    const bool dense = k > o0 &&
+                                       ((double)t - (double)times[k - 1]) < kAuto64MinRelGap * at;
+                    need64 = need64 || out || tiny || dense;
+                } else if (out) {
                     record_error(hdr, kErrRange32, k);
+                }
             }
         }
     }
+    if (__any_sync(0xffffffffu, need64) && lane == 0) atomicOr(&hdr->need64, 1u << slot);
     // warp max then one atomic per warp
     for (int o = 16; o > 0; o >>= 1) local_max = max(local_max, __shfl_xor_sync(0xffffffffu, local_max, o));
     if (lane == 0 && local_max) atomicMax(&hdr->maxlen[slot], local_max);
@@ -236,10 +251,11 @@ template <typename Tin, typename Tw>
 __global__ void pack_kernel(const int64_t* __restrict__ offsets, const Tin* __restrict__ times,
                             const Tin* __restrict__ values, int64_t n,
                             const int32_t* __restrict__ perm, const int32_t* __restrict__ slen,
-                            const int64_t* __restrict__ poff, void* packed_v, const Header* hdr)
+                            const int64_t* __restrict__ poff, void* packed_v, const Header* hdr,
+                            const unsigned int* gate, int want64)
 {
     using E = typename Elem<Tin, Tw>::type;
-    if (hdr->err != kNoError) return;
+    if (hdr->err != kNoError || gated_off(gate, want64)) return;
     E* packed = reinterpret_cast<E*>(packed_v);
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -271,9 +287,10 @@ __global__ void pack_keyed_kernel(const int64_t* __restrict__ offsets,
                                   const Tin* __restrict__ times, const Tin* __restrict__ values,
                                   int64_t n, const int32_t* __restrict__ perm,
                                   const int32_t* __restrict__ slen, const int64_t* __restrict__ poff,
-                                  KElem* __restrict__ packed, KeyOut ko, const Header* hdr)
+                                  KElem* __restrict__ packed, KeyOut ko, const Header* hdr,
+                                  const unsigned int* gate, int want64)
 {
-    if (hdr->err != kNoError) return;
+    if (hdr->err != kNoError || gated_off(gate, want64)) return;
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -351,17 +368,17 @@ cudaError_t launch_validate(const int64_t* offsets, const void* times, const voi
     const int walk_f32 = form != kPackF64;
     if (in_dtype == PCF_F64) {
         validate_kernel<double><<<g, 256, 0, s>>>(offsets, (const double*)times,
-            (const double*)values, n, nnz_total, 1, walk_f32, sv.lens, sv.skey, hdr, sv.slot);
+            (const double*)values, n, nnz_total, 1, walk_f32, sv.lens, sv.skey, hdr, sv.slot, 0);
     } else {
         validate_kernel<float><<<g, 256, 0, s>>>(offsets, (const float*)times,
-            (const float*)values, n, nnz_total, 1, walk_f32, sv.lens, sv.skey, hdr, sv.slot);
+            (const float*)values, n, nnz_total, 1, walk_f32, sv.lens, sv.skey, hdr, sv.slot, 0);
     }
     return cudaGetLastError();
 }
 
 cudaError_t pack_set(const int64_t* offsets, const void* times, const void* values, int in_dtype,
                      int64_t n, int form, Header* hdr, SetView& sv, cudaStream_t s,
-                     const KeyOut* ko)
+                     const KeyOut* ko, const unsigned int* gate, int want64)
 {
     if (n == 0) return cudaSuccess;
     const int g = grid_for_warps(n);
@@ -370,49 +387,58 @@ cudaError_t pack_set(const int64_t* offsets, const void* times, const void* valu
         if (in_dtype == PCF_F64)
             pack_keyed_kernel<double><<<g, 256, 0, s>>>(offsets, (const double*)times,
                 (const double*)values, n, sv.perm, sv.slen, sv.poff,
-                reinterpret_cast<KElem*>(sv.packed), *ko, hdr);
+                reinterpret_cast<KElem*>(sv.packed), *ko, hdr, gate, want64);
         else
             pack_keyed_kernel<float><<<g, 256, 0, s>>>(offsets, (const float*)times,
                 (const float*)values, n, sv.perm, sv.slen, sv.poff,
-                reinterpret_cast<KElem*>(sv.packed), *ko, hdr);
+                reinterpret_cast<KElem*>(sv.packed), *ko, hdr, gate, want64);
     } else if (in_dtype == PCF_F64) {
         if (form == kPackF64)
             pack_kernel<double, double><<<g, 256, 0, s>>>(offsets, (const double*)times,
-                (const double*)values, n, sv.perm, sv.slen, sv.poff, sv.packed, hdr);
+                (const double*)values, n, sv.perm, sv.slen, sv.poff, sv.packed, hdr, gate, want64);
         else
             pack_kernel<double, float><<<g, 256, 0, s>>>(offsets, (const double*)times,
-                (const double*)values, n, sv.perm, sv.slen, sv.poff, sv.packed, hdr);
+                (const double*)values, n, sv.perm, sv.slen, sv.poff, sv.packed, hdr, gate, want64);
     } else {
         if (form == kPackF64)
             pack_kernel<float, double><<<g, 256, 0, s>>>(offsets, (const float*)times,
-                (const float*)values, n, sv.perm, sv.slen, sv.poff, sv.packed, hdr);
+                (const float*)values, n, sv.perm, sv.slen, sv.poff, sv.packed, hdr, gate, want64);
         else
             pack_kernel<float, float><<<g, 256, 0, s>>>(offsets, (const float*)times,
-                (const float*)values, n, sv.perm, sv.slen, sv.poff, sv.packed, hdr);
+                (const float*)values, n, sv.perm, sv.slen, sv.poff, sv.packed, hdr, gate, want64);
     }
     return cudaGetLastError();
 }
 
 cudaError_t prepare_set(const int64_t* offsets, const void* times, const void* values,
                         int in_dtype, int64_t n, int64_t nnz_total, bool whole,
-                        int form, Header* hdr, SetView& sv, cudaStream_t s, const KeyOut* ko)
+                        int form, Header* hdr, SetView& sv, cudaStream_t s, const KeyOut* ko,
+                        bool auto64)
 {
     if (n == 0) return cudaSuccess;
     const int g = grid_for_warps(n);
     const int walk_f32 = form != kPackF64;
+    const int a64 = auto64 && walk_f32 ? 1 : 0;
     if (in_dtype == PCF_F64) {
         validate_kernel<double><<<g, 256, 0, s>>>(offsets, (const double*)times,
-            (const double*)values, n, nnz_total, whole, walk_f32, sv.lens, sv.skey, hdr, sv.slot);
+            (const double*)values, n, nnz_total, whole, walk_f32, sv.lens, sv.skey, hdr, sv.slot,
+            a64);
     } else {
         validate_kernel<float><<<g, 256, 0, s>>>(offsets, (const float*)times,
-            (const float*)values, n, nnz_total, whole, walk_f32, sv.lens, sv.skey, hdr, sv.slot);
+            (const float*)values, n, nnz_total, whole, walk_f32, sv.lens, sv.skey, hdr, sv.slot,
+            a64);
     }
     sort_scan_kernel<<<1, kSortThreads, 0, s>>>(sv.lens, sv.skey, n, hdr, sv.slot, sv.perm, sv.slen,
                                                  sv.khi[0], sv.klo[0], sv.kv[0], sv.khi[1],
                                                  sv.klo[1], sv.kv[1], sv.poff);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return pack_set(offsets, times, values, in_dtype, n, form, hdr, sv, s, ko);
+    if (!a64) return pack_set(offsets, times, values, in_dtype, n, form, hdr, sv, s, ko);
+    // both forms, gated on the need found by the validation of every set
+    e = pack_set(offsets, times, values, in_dtype, n, form, hdr, sv, s, ko, &hdr->need64, 0);
+    if (e != cudaSuccess) return e;
+    return pack_set(offsets, times, values, in_dtype, n, kPackF64, hdr, sv, s, nullptr,
+                    &hdr->need64, 1);
 }
 
 }  // namespace pcfgb

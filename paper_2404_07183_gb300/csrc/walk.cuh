@@ -338,6 +338,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
     __shared__ K sT1part[2];
     __shared__ int64_t sTile;
 
+    if (gated_off(a.gate, a.gate_want64)) return;   // the other walk of an AUTO64 call
     if (block_sees_error(a.hdr)) return;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;

@@ -64,6 +64,28 @@ def test_workspace_size_host_only(lib):
                                   ctypes.byref(out)) == abi.PCF_EINVAL
 
 
+def test_workspace_size_of_the_precision_modifiers(lib):
+    """float64 input in a float32 precision packs 16-byte keyed elements plus
+    the key sort's buffers; the rounded-times opt-in packs 8-byte elements;
+    AUTO64 holds either form; both modifiers are invalid with PCF_PREC_F64."""
+    out = ctypes.c_size_t()
+
+    def size(x, prec):
+        rc = lib.pcf_workspace_size(ctypes.byref(x), None, prec, abi.PCF_WS_FORWARD,
+                                    ctypes.byref(out))
+        return out.value if rc == abi.PCF_OK else rc
+
+    x64, x32 = _csr(1000, 55000, abi.PCF_F64), _csr(1000, 55000, abi.PCF_F32)
+    keyed = size(x64, abi.PCF_PREC_F32_COMP)
+    rounded = size(x64, abi.PCF_PREC_F32_COMP | abi.PCF_PREC_ROUND_TIMES)
+    assert rounded == size(x32, abi.PCF_PREC_F32_COMP)
+    assert keyed >= rounded + 55000 * (8 + 2 * 8 + 2 * 4)
+    assert size(x64, abi.PCF_PREC_F32_COMP | abi.PCF_PREC_AUTO64) >= keyed
+    assert size(x32, abi.PCF_PREC_F32_COMP | abi.PCF_PREC_AUTO64) >= size(x32, abi.PCF_PREC_F64)
+    for mod in (abi.PCF_PREC_ROUND_TIMES, abi.PCF_PREC_AUTO64, 0x400):
+        assert size(x64, abi.PCF_PREC_F64 | mod) == abi.PCF_EINVAL
+
+
 def test_argument_errors_return_before_any_device_work(lib):
     x = _csr(10, 100)
     req = (abi.PcfIntegral * 1)()
