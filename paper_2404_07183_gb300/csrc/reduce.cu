@@ -208,7 +208,12 @@ constexpr unsigned long long kStAgg = 1ull << 62;    // the chunk's own row coun
 constexpr unsigned long long kStIncl = 2ull << 62;   // rows of chunks 0..c
 constexpr unsigned long long kStErr = 3ull << 62;    // gave up: successors stop too
 constexpr unsigned long long kStVal = (1ull << 62) - 1;
-constexpr long long kSpinPolls = 1ll << 20;          // per predecessor, ~0.1 s
+// Polls before a wait gives up, per group of 32 predecessors: at least
+// 0.27 s in the 64 ns sleeps alone.  A predecessor holds a lower ticket, so it
+// is already running and publishes within microseconds unless its SM is
+// time-sliced to another process's context; such slices last milliseconds,
+// two orders of magnitude below the limit.
+constexpr long long kSpinPolls = 1ll << 22;
 
 // Output position of chunk c's first row (decoupled look-back by one warp,
 // every lane calls this): publish this chunk's count, then read the states
