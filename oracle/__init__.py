@@ -82,6 +82,8 @@ def _load():
             lib.orc_segment_sq.argtypes = [P, P, i64]
             lib.orc_integral_ab.restype = dbl
             lib.orc_integral_ab.argtypes = [P, P, i64, P, P, i64, ip, dbl, dbl, dbl, dbl]
+            lib.orc_integral_w.restype = dbl
+            lib.orc_integral_w.argtypes = [P, P, i64, P, P, i64, P, P, i64, ip, dbl]
             lib.orc_segment_integral.restype = dbl
             lib.orc_segment_integral.argtypes = [P, P, i64, ip, dbl, dbl, dbl]
             lib.orc_reduce_pair.restype = i64
@@ -118,6 +120,41 @@ def integral_ab(tf, vf, tg, vg, metric="l1", p=1.0, a=0.0, b=float("inf"), lam=0
     tf, vf, tg, vg = map(_f64, (tf, vf, tg, vg))
     return _load().orc_integral_ab(_ptr(tf), _ptr(vf), tf.size, _ptr(tg), _ptr(vg), tg.size,
                                    _metric(metric), float(p), float(a), float(b), float(lam))
+
+
+def integral_w(tf, vf, tg, vg, tw, vw, metric="l1", p=1.0) -> float:
+    """int_0^inf h(f, g) w dt for a non-negative PCF weight w (no root)."""
+    tf, vf, tg, vg, tw, vw = map(_f64, (tf, vf, tg, vg, tw, vw))
+    return _load().orc_integral_w(_ptr(tf), _ptr(vf), tf.size, _ptr(tg), _ptr(vg), tg.size,
+                                  _ptr(tw), _ptr(vw), tw.size, _metric(metric), float(p))
+
+
+def matrix_w(a, w, b=None, metric="l1", p=1.0, apply_root=True) -> np.ndarray:
+    """Weighted pairwise (b None) or cross matrix: r(int h(a_i, b_j) w dt)
+    with w = (times, values) one PCF; pair by pair (small inputs)."""
+    bb = a if b is None else b
+    tw, vw = _f64(w[0]), _f64(w[1])
+    out = np.empty((a.n, bb.n))
+    for i in range(a.n):
+        tf, vf = a.pcf(i)
+        for j in range(bb.n):
+            if b is None and j < i:
+                out[i, j] = out[j, i]
+                continue
+            I = integral_w(tf, vf, *bb.pcf(j), tw, vw, metric, p)
+            out[i, j] = _root(metric, p, I) if apply_root else I
+    return out
+
+
+def _root(metric, p, x):
+    if metric == "gram":
+        return x
+    e = {"l1": 1.0, "l2": 2.0}.get(metric, p)
+    if e == 1.0:
+        return x
+    if e == 2.0:
+        return float(np.sqrt(x))
+    return x ** (1.0 / e)
 
 
 def rectangles(tf, vf, tg, vg):

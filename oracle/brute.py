@@ -100,3 +100,39 @@ def exact_integral(tf, vf, tg, vg, metric="l1", p=1):
         elif val != 0:
             return None
     return total
+
+
+def integral_w(tf, vf, tg, vg, tw, vw, metric="l1", p=1.0) -> float:
+    """int h(f, g) w dt on the common refinement of the three breakpoint sets:
+    every cell [s_k, s_{k+1}) adds h(f(s_k), g(s_k)) w(s_k) (s_{k+1} - s_k);
+    the last cell adds 0 when h w = 0 there and +-inf otherwise."""
+    s = np.unique(np.concatenate([np.asarray(x, np.float64) for x in (tf, tg, tw)]))
+    hw = _h(metric, p, evaluate(tf, vf, s), evaluate(tg, vg, s)) * evaluate(tw, vw, s)
+    body = float(np.sum(hw[:-1] * np.diff(s)))
+    if hw[-1] != 0:
+        return body + float(hw[-1]) * np.inf
+    return body
+
+
+def exact_integral_w(tf, vf, tg, vg, tw, vw, metric="l1", p=1):
+    """Exact rational value of the weighted integral (None if it diverges)."""
+    T = [[Fraction(float(x)) for x in a] for a in (tf, tg, tw)]
+    V = [[Fraction(float(x)) for x in a] for a in (vf, vg, vw)]
+    grid = sorted(set(T[0]) | set(T[1]) | set(T[2]))
+
+    def at(t, v, s):
+        k = 0
+        while k + 1 < len(t) and t[k + 1] <= s:
+            k += 1
+        return v[k]
+
+    e = {"l1": 1, "l2": 2}.get(metric, p)
+    total = Fraction(0)
+    for k, s in enumerate(grid):
+        x, y, w = (at(T[q], V[q], s) for q in range(3))
+        val = (x * y if metric == "gram" else abs(x - y) ** int(e)) * w
+        if k + 1 < len(grid):
+            total += val * (grid[k + 1] - s)
+        elif val != 0:
+            return None
+    return total

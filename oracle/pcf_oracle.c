@@ -18,6 +18,12 @@
  *                                                             (Sec. 3, Alg. 1
  *                                                              bounds; Sec. 2.1
  *                                                              time-dependent h)
+ *   orc_integral_w      int h(f, g) w dt for a non-negative PCF weight w
+ *                       (rectangle iteration over three breakpoint lists)
+ *                                                             (Sec. 2.2 weighted
+ *                                                              L_p; Sec. 2.1
+ *                                                              time-dependent h;
+ *                                                              Alg. 1/2)
  *   orc_segment_sq      integral of f^2 by segment iteration  (Sec. 3.2, Alg. 3)
  *   orc_segment_integral integral of f or |f|^p over [a, b]    (Sec. 3.2, Alg. 3)
  *   orc_reduce_pair     ReducePair: the PCF h_*(f, g) with repeated values
@@ -260,6 +266,41 @@ double orc_integral_ab(const double* tf, const double* vf, int64_t nf,
         I += h * dw;
     }
     return I;
+}
+
+/*
+ * Weighted combination integral int_0^inf h(f(t), g(t)) w(t) dt for a
+ * non-negative PCF weight w (the weighted L_p distance of Sec. 2.2 with the
+ * weight multiplying |f - g|^p, and the weighted inner product), by rectangle
+ * iteration over the three breakpoint lists T_f, T_g, T_w: the scanline moves
+ * to the earliest next breakpoint of the three, every list whose next
+ * breakpoint is there moves with it, and each rectangle [l, r) on which f, g
+ * and w are constant adds h(f, g) * w * (r - l).  The last rectangle,
+ * [t_last, inf), adds 0 when h * w = 0 there and +-inf otherwise.
+ */
+double orc_integral_w(const double* tf, const double* vf, int64_t nf,
+                      const double* tg, const double* vg, int64_t ng,
+                      const double* tw, const double* vw, int64_t nw,
+                      int metric, double p)
+{
+    int64_t i = 0, j = 0, k = 0;
+    double t = 0.0, I = 0.0;
+    for (;;) {
+        double next = INFINITY;
+        if (i + 1 < nf && tf[i + 1] < next) next = tf[i + 1];
+        if (j + 1 < ng && tg[j + 1] < next) next = tg[j + 1];
+        if (k + 1 < nw && tw[k + 1] < next) next = tw[k + 1];
+        const double hw = orc_h(metric, p, vf[i], vg[j]) * vw[k];
+        if (isinf(next)) {
+            if (hw != 0.0) I += hw * INFINITY;
+            return I;
+        }
+        I += hw * (next - t);
+        t = next;
+        if (i + 1 < nf && tf[i + 1] == next) i += 1;
+        if (j + 1 < ng && tg[j + 1] == next) j += 1;
+        if (k + 1 < nw && tw[k + 1] == next) k += 1;
+    }
 }
 
 /* Number of rectangles of the pair = |T_f u T_g| (the merge-step count). */
