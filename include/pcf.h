@@ -350,6 +350,30 @@ int pcf_pairwise_backward_ex(const pcf_csr* x, int metric, double p, int apply_r
                              void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
 /*
+ * Pairwise matrices against a non-negative PCF weight w (the weighted L_p
+ * distance of Sec. 2.2, the weight multiplying |f - g|^p; the weighted inner
+ * product for PCF_GRAM):
+ *   F_ij = r( int_0^inf h(x_i(t), x_j(t)) w(t) dt ).
+ * w: a collection of exactly one PCF (device arrays, offsets {0, nnz}), with
+ * t_0 = 0, increasing finite times and finite values >= 0.  With
+ * W(t) = int_0^t w, each rectangle [l, r) of a pair walk adds
+ * h * (W(r) - W(l)) (the antiderivative form of Sec. 3): the call moves every
+ * breakpoint of x to W(t_k) (float64; intervals where w = 0 vanish; when w's
+ * last value is 0 the integrals stop at W(inf)) and computes the unweighted
+ * matrices of the moved collection with the precision, layout and schedule
+ * given, as pcf_pairwise does.  A pair integrates to +-inf only when its
+ * tails differ and w's last value is positive.
+ * Workspace: pcf_weighted_workspace_size (caller-owned, 256-byte aligned).
+ * Returns as pcf_pairwise; pcf_check reports invalid data of x (reasons
+ * 1-6) and of w (reason 10, index = element of w).
+ */
+int pcf_weighted_workspace_size(const pcf_csr* x, const pcf_csr* w, int precision,
+                                size_t* bytes);
+int pcf_pairwise_weighted(const pcf_csr* x, const pcf_csr* w, const pcf_integral* F, int nF,
+                          int precision, int layout, int out_dtype, const pcf_schedule* schedule,
+                          void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/*
  * Single-PCF integrals by segment iteration (Sec. 3.2, Alg. 3):
  *   out[i] = r( int_a^b h(f_i(t)) dt ),  0 <= a < b <= inf,
  * h per pcf_functional; r(x) = x^(1/p) for PCF_FN_LP with apply_root, else x.
@@ -388,7 +412,9 @@ int pcf_sort_order(const pcf_csr* x, int precision, const void* workspace,
  * element index wins.  Reductions and combinations also report PCF_ENOWS
  * with reason 8 when a result or an intermediate needs more rows than the
  * output capacity or the workspace holds (*index = the rows needed, or the
- * merge positions of the pass that did not fit).  detail/index may be NULL.
+ * merge positions of the pass that did not fit).  pcf_pairwise_weighted
+ * reports an invalid weight with reason 10 (*index = element of the weight).
+ * detail/index may be NULL.
  */
 int pcf_check(const void* workspace, cudaStream_t stream, int* detail, int64_t* index);
 

@@ -33,11 +33,12 @@ ERR_DETAIL = {
     7: "more coincident float32 breakpoints than one window holds",
     8: "result or intermediate larger than the output capacity or the workspace",
     9: "a bounded device wait gave up",
+    10: "weight PCF invalid (negative or non-finite value, t_0 != 0, times not increasing)",
 }
 
 SYMBOLS = ("pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross", "pcf_pairwise_backward",
            "pcf_check", "pcf_status_string", "pcf_version", "pcf_pairwise_noalloc",
-           "pcf_walk_promoted",
+           "pcf_walk_promoted", "pcf_weighted_workspace_size", "pcf_pairwise_weighted",
            "pcf_pairwise_ex", "pcf_cross_ex", "pcf_sort_order", "pcf_segment_integrals",
            "pcf_reduce_workspace_size", "pcf_reduce", "pcf_combine_workspace_size",
            "pcf_combine", "pcf_reduce_counters", "pcf_selftest_wait_timeout",
@@ -132,6 +133,10 @@ def load(build_if_missing: bool = False):
         lib.pcf_check.argtypes = [P, P, ctypes.POINTER(I), ctypes.POINTER(I64)]
         lib.pcf_walk_promoted.restype = I
         lib.pcf_walk_promoted.argtypes = [P, P, ctypes.POINTER(I)]
+        lib.pcf_weighted_workspace_size.restype = I
+        lib.pcf_weighted_workspace_size.argtypes = [CSR, CSR, I, ctypes.POINTER(SZ)]
+        lib.pcf_pairwise_weighted.restype = I
+        lib.pcf_pairwise_weighted.argtypes = [CSR, CSR, INT, I, I, I, I, P, P, SZ, P]
         lib.pcf_status_string.restype = ctypes.c_char_p
         lib.pcf_status_string.argtypes = [I]
         lib.pcf_pairwise_noalloc.restype = I

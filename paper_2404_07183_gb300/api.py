@@ -25,7 +25,8 @@ __all__ = ["PcfError", "PcfTensors", "pcf_workspace_size", "pcf_prepare", "pcf_s
            "pcf_segment_integrals",
            "pcf_pairwise", "pcf_cross",
            "pcf_cross_to_host",
-           "pcf_pairwise_backward", "pcf_check", "pcf_walk_promoted", "PairwiseFn", "PairwiseGraph", "pdist",
+           "pcf_pairwise_backward", "pcf_check", "pcf_walk_promoted", "pcf_pairwise_weighted",
+           "pcf_weighted_workspace_size", "PairwiseFn", "PairwiseGraph", "pdist",
            "l2_kernel", "pcf_reduce", "pcf_combine", "pcf_reduce_counters", "mean", "std",
            "parse_metric", "PRECISIONS", "REDUCTIONS", "OPS"]
 
@@ -300,6 +301,63 @@ def pcf_pairwise(x: PcfTensors, metrics=("l1",), precision="f32c", layout="full"
         pcf_check(ws, stream, "pcf_pairwise")
     return out
 
+
+
+def _weight_tensors(w, device):
+    """A weight PCF as a one-PCF PcfTensors on `device`: PcfTensors, a host set
+    with offsets/times/values, or a (times, values) pair."""
+    if isinstance(w, PcfTensors):
+        return w
+    if hasattr(w, "offsets"):
+        return PcfTensors.from_numpy(w, device)
+    t, v = (np.asarray(a, dtype=np.float64) for a in w)
+    o = np.array([0, t.size], dtype=np.int64)
+    return PcfTensors(*(torch.from_numpy(np.ascontiguousarray(a)).to(device) for a in (o, t, v)))
+
+
+def pcf_weighted_workspace_size(x: PcfTensors, w, precision="f32c") -> int:
+    lib = abi.load()
+    cw = _weight_tensors(w, x.times.device).csr()
+    cx = x.csr()
+    out = ctypes.c_size_t()
+    rc = lib.pcf_weighted_workspace_size(ctypes.byref(cx), ctypes.byref(cw), _prec(precision),
+                                         ctypes.byref(out))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_weighted_workspace_size")
+    return int(out.value)
+
+
+def pcf_pairwise_weighted(x: PcfTensors, w, metrics=("l1",), precision="f32c", layout="full",
+                          out_dtype=torch.float32, out=None, workspace=None, stream=None,
+                          check=True, schedule=None):
+    """Pairwise matrices r(int h(x_i, x_j) w dt) against one non-negative PCF
+    weight ``w`` (weighted L_p of Sec. 2.2; weighted inner product for
+    "gram"); layouts and precisions as ``pcf_pairwise``."""
+    lib = abi.load()
+    if isinstance(metrics, (str, tuple)):
+        metrics = [metrics]
+    metrics = list(metrics)
+    n = x.n
+    lay = {"full": abi.PCF_OUT_FULL, "upper": abi.PCF_OUT_UPPER_PACKED,
+           "sorted": abi.PCF_OUT_FULL_SORTED}[layout]
+    shape = (n * (n + 1) // 2,) if lay == abi.PCF_OUT_UPPER_PACKED else (n, n)
+    dev = x.times.device
+    wt = _weight_tensors(w, dev)
+    if out is None:
+        out = [torch.empty(shape, dtype=out_dtype, device=dev) for _ in metrics]
+    ws = _workspace(pcf_weighted_workspace_size(x, wt, precision), dev, workspace)
+    cx, cw = x.csr(), wt.csr()
+    req = _requests(metrics, out)
+    od = abi.PCF_F64 if out[0].dtype == torch.float64 else abi.PCF_F32
+    rc = lib.pcf_pairwise_weighted(ctypes.byref(cx), ctypes.byref(cw), req, len(metrics),
+                                   _prec(precision), lay, od, _schedule(schedule),
+                                   ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                   _stream_handle(stream))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_pairwise_weighted")
+    if check:
+        pcf_check(ws, stream, "pcf_pairwise_weighted")
+    return out
 
 def pcf_cross(a: PcfTensors, b: PcfTensors, row_begin=0, row_end=None, metrics=("l1",),
               precision="f32c", out_dtype=torch.float32, out=None, ld_out=None,

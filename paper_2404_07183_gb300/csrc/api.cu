@@ -933,6 +933,105 @@ int pcf_check(const void* workspace, cudaStream_t stream, int* detail, int64_t* 
     return PCF_EINVAL;
 }
 
+// The collection x moved to the weighted time W(t): same PCF count, at most
+// one breakpoint more per PCF, float64, offsets known on the device only.
+static pcf_csr moved_shape(const pcf_csr* x)
+{
+    pcf_csr m;
+    memset(&m, 0, sizeof m);
+    m.n = x->n;
+    m.nnz = x->nnz + x->n;
+    m.dtype = PCF_F64;
+    return m;
+}
+
+static bool weight_ok(const pcf_csr* w)
+{
+    return csr_ok(w) && w->n == 1 && w->nnz >= 1;
+}
+
+int pcf_weighted_workspace_size(const pcf_csr* x, const pcf_csr* w, int precision, size_t* bytes)
+{
+    if (!bytes || !x || x->n < 0 || x->nnz < 0 || x->n > 0x7fffffffLL) return PCF_EINVAL;
+    if (!w || w->n != 1 || w->nnz < 1) return PCF_EINVAL;
+    const pcf_csr m = moved_shape(x);
+    size_t inner = 0;
+    const int rc = pcf_workspace_size(&m, nullptr, precision, PCF_WS_FORWARD, &inner);
+    if (rc != PCF_OK) return rc;
+    *bytes = align_up(inner) + weight_scratch_bytes(x->n, x->nnz, w->nnz);
+    return PCF_OK;
+}
+
+int pcf_pairwise_weighted(const pcf_csr* x, const pcf_csr* w, const pcf_integral* F, int nF,
+                          int precision, int layout, int out_dtype, const pcf_schedule* schedule,
+                          void* workspace, size_t workspace_bytes, cudaStream_t stream)
+{
+    if (!csr_ok(x) || !weight_ok(w)) return PCF_EINVAL;
+    Prec pr;
+    if (!parse_prec(precision, &pr)) return PCF_EINVAL;
+    if (layout != PCF_OUT_FULL && layout != PCF_OUT_UPPER_PACKED && layout != PCF_OUT_FULL_SORTED)
+        return PCF_EINVAL;
+    if (out_dtype != PCF_F32 && out_dtype != PCF_F64) return PCF_EINVAL;
+    if (check_schedule(schedule) != PCF_OK) return PCF_EINVAL;
+    int rc = check_requests(F, nF, x->n > 0);
+    if (rc != PCF_OK) return rc;
+    size_t need = 0;
+    rc = pcf_weighted_workspace_size(x, w, precision, &need);
+    if (rc != PCF_OK) return rc;
+    if (!workspace || ((uintptr_t)workspace % kAlign) != 0 || workspace_bytes < need) return PCF_ENOWS;
+    if (x->n == 0) return PCF_OK;
+
+    // [the pairwise workspace of the moved collection][the weight scratch]
+    pcf_csr m = moved_shape(x);
+    size_t inner = 0;
+    pcf_workspace_size(&m, nullptr, precision, PCF_WS_FORWARD, &inner);
+    char* wcur = (char*)workspace + align_up(inner);
+    const WeightScratch wsc = carve_weight(wcur, x->n, x->nnz, w->nnz);
+    m.offsets = wsc.off2;
+    m.times = wsc.t2;
+    m.values = wsc.v2;
+    Header* hdr;
+    SetView sv;
+    KeySort ks;
+    int form = kPackF64;
+    rc = pairwise_common(&m, precision, workspace, inner, &hdr, &sv, &ks, &form);
+    if (rc != PCF_OK) return rc;
+
+    init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
+    // x and w are checked before the moved collection is built from them
+    if (launch_validate(x->offsets, x->times, x->values, x->dtype, x->n, x->nnz, kPackF64, hdr, sv,
+                        stream) != cudaSuccess ||
+        launch_weight_move(x, w, wsc, hdr, stream) != cudaSuccess)
+        return PCF_ECUDA;
+    KeyOut ko;
+    if (form == kPackKeyed) { ko.key = ks.key[0]; ko.pay = ks.pay[0]; }
+    if (prepare_set(m.offsets, m.times, m.values, PCF_F64, m.n, m.nnz, false, form, hdr, sv, stream,
+                    form == kPackKeyed ? &ko : nullptr, pr.auto64, true) != cudaSuccess)
+        return PCF_ECUDA;
+    if (form == kPackKeyed &&
+        rank_keys(ks, reinterpret_cast<KElem*>(sv.packed), sv.poff, m.n, nullptr, nullptr, 0, hdr,
+                  stream) != cudaSuccess)
+        return PCF_ECUDA;
+
+    WalkArgs wa;
+    memset(&wa, 0, sizeof wa);
+    wa.pack_r = wa.pack_c = sv.packed;
+    wa.poff_r = wa.poff_c = sv.poff;
+    wa.slen_r = wa.slen_c = sv.slen;
+    wa.perm_r = wa.perm_c = sv.perm;
+    wa.n_r = wa.n_c = m.n;
+    wa.nb_r = wa.nb_c = (m.n + kTile - 1) / kTile;
+    wa.ntiles = wa.nb_r * (wa.nb_r + 1) / 2;
+    wa.symmetric = 1;
+    wa.hdr = hdr;
+    wa.layout = layout;
+    wa.out_f64 = out_dtype == PCF_F64;
+    wa.ld_out = m.n;
+    KElem* kp = reinterpret_cast<KElem*>(sv.packed);
+    keyed_bounds(wa, nullptr, form, ks, kp, kp, hdr, stream);
+    return run_walks_for(wa, F, nF, pr, form, schedule, nullptr, stream);
+}
+
 int pcf_walk_promoted(const void* workspace, cudaStream_t stream, int* promoted)
 {
     if (!workspace || !promoted) return PCF_EINVAL;

@@ -39,7 +39,8 @@ constexpr size_t kAlign = 256;
 //   is reported first, then the smallest offending element.
 enum ErrDetail : int {
     kErrOffsets = 1, kErrT0 = 2, kErrOrder = 3, kErrTimeNaN = 4,
-    kErrValueNaN = 5, kErrRange32 = 6, kErrDense32 = 7, kErrCapacity = 8, kErrWait = 9
+    kErrValueNaN = 5, kErrRange32 = 6, kErrDense32 = 7, kErrCapacity = 8, kErrWait = 9,
+    kErrWeight = 10
 };
 constexpr unsigned long long kNoError = ~0ull;
 
@@ -159,10 +160,12 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // (Header::need64, set by the validation), in which case the float64 form is
 // packed into the same buffer instead (both kernels are enqueued; each
 // returns at once when the other form is the one needed).
+// built: the collection was written by an earlier kernel of the same call,
+// which skips its work after an input error; so is this validation then.
 cudaError_t prepare_set(const int64_t* offsets, const void* times, const void* values,
                         int in_dtype, int64_t n, int64_t nnz_total, bool whole,
                         int form, Header* hdr, SetView& sv, cudaStream_t s,
-                        const KeyOut* ko = nullptr, bool auto64 = false);
+                        const KeyOut* ko = nullptr, bool auto64 = false, bool built = false);
 // The pack step alone (validation and length sort already done): used by
 // cross calls that reuse B's sort but must re-rank its keys.  gate: null,
 // or run only when (*gate != 0) == want64.
@@ -250,6 +253,20 @@ cudaError_t launch_backward(const BackArgs& a, cudaStream_t s);
 cudaError_t launch_scatter_grad(const SetView& sv, const int64_t* offsets, const double* gv,
                                 const double* gt, void* grad_values, void* grad_times,
                                 int out_f64, Header* hdr, cudaStream_t s);
+
+// A collection moved to the weighted time s = W(t) = int_0^t w (weight.cu).
+struct WeightScratch {
+    double* Wt = nullptr;      // W at the weight's breakpoints
+    int64_t* lens2 = nullptr;  // lengths of the moved PCFs
+    int64_t* off2 = nullptr;   // their offsets (n + 1)
+    double* t2 = nullptr;      // moved breakpoints (capacity nnz + n)
+    double* v2 = nullptr;      // their values
+    int64_t cap = 0;
+};
+size_t weight_scratch_bytes(int64_t n, int64_t nnz, int64_t nw);
+WeightScratch carve_weight(char*& cursor, int64_t n, int64_t nnz, int64_t nw);
+cudaError_t launch_weight_move(const pcf_csr* x, const pcf_csr* w, const WeightScratch& ws,
+                               Header* hdr, cudaStream_t s);
 
 cudaError_t launch_segments(const pcf_csr* x, int functional, double p, int apply_root,
                             double lo, double hi, int precision, void* out, int out_f64,

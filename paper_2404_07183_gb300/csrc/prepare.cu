@@ -27,8 +27,11 @@ __global__ void validate_kernel(const int64_t* __restrict__ offsets,
                                 const T* __restrict__ times, const T* __restrict__ values,
                                 int64_t n, int64_t nnz_total, int whole, int walk_f32,
                                 int32_t* __restrict__ lens, uint32_t* __restrict__ skey,
-                                Header* hdr, int slot, int auto64)
+                                Header* hdr, int slot, int auto64, int skip_on_error = 0)
 {
+    // a collection built by an earlier kernel of the call is only checked
+    // when that kernel ran (no error recorded before it)
+    if (skip_on_error && hdr->err != kNoError) return;
     bool need64 = false;
     const int lane = threadIdx.x & 31;
     const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -413,7 +416,7 @@ cudaError_t pack_set(const int64_t* offsets, const void* times, const void* valu
 cudaError_t prepare_set(const int64_t* offsets, const void* times, const void* values,
                         int in_dtype, int64_t n, int64_t nnz_total, bool whole,
                         int form, Header* hdr, SetView& sv, cudaStream_t s, const KeyOut* ko,
-                        bool auto64)
+                        bool auto64, bool built)
 {
     if (n == 0) return cudaSuccess;
     const int g = grid_for_warps(n);
@@ -422,11 +425,11 @@ cudaError_t prepare_set(const int64_t* offsets, const void* times, const void* v
     if (in_dtype == PCF_F64) {
         validate_kernel<double><<<g, 256, 0, s>>>(offsets, (const double*)times,
             (const double*)values, n, nnz_total, whole, walk_f32, sv.lens, sv.skey, hdr, sv.slot,
-            a64);
+            a64, built ? 1 : 0);
     } else {
         validate_kernel<float><<<g, 256, 0, s>>>(offsets, (const float*)times,
             (const float*)values, n, nnz_total, whole, walk_f32, sv.lens, sv.skey, hdr, sv.slot,
-            a64);
+            a64, built ? 1 : 0);
     }
     sort_scan_kernel<<<1, kSortThreads, 0, s>>>(sv.lens, sv.skey, n, hdr, sv.slot, sv.perm, sv.slen,
                                                  sv.khi[0], sv.klo[0], sv.kv[0], sv.khi[1],
