@@ -674,6 +674,45 @@ def _cpu_rows(a, metrics, b=None, seconds_target=8.0, row0=0, p=None):
                       "metrics, float64 oracle walk, one thread per core"}
 
 
+def _clip_after(s, t_end):
+    """Breakpoints of each PCF before t_end, plus one at t_end (the moved
+    collection of a weight that vanishes after t_end has this shape)."""
+    offs, ts, vs = [0], [], []
+    for i in range(s.n):
+        t, v = s.pcf(i)
+        keep = t < t_end
+        ts.append(np.append(t[keep], t_end))
+        vs.append(np.append(v[keep], 0.0))
+        offs.append(offs[-1] + ts[-1].size)
+    return np.array(offs, np.int64), np.concatenate(ts), np.concatenate(vs)
+
+
+def _cpu_rows_weighted(a, w, seconds_target=8.0, row0=1000):
+    """The oracle's weighted walk (one row per pool task) on a row sample."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    cores = len(os.sched_getaffinity(0))
+
+    def row(i):
+        tf, vf = a.pcf(i)
+        for j in range(a.n):
+            for m, p in (("l1", 1.0), ("l2", 2.0), ("gram", 1.0)):
+                oracle.integral_w(tf, vf, *a.pcf(j), *w, m, p)
+
+    t0 = time.perf_counter()
+    row(row0)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    rows = int(max(1, min(64, seconds_target / dt)))
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(cores) as ex:
+        list(ex.map(row, range(row0, row0 + rows)))
+    dt = time.perf_counter() - t0
+    return {"value": 3 * rows * a.n / dt, "unit": "pair-integrals/s", "cores": cores,
+            "kind": "oracle", "seconds": dt,
+            "sample": f"rows {row0}..{row0 + rows} x all {a.n} columns x 3 metrics, float64 "
+                      "three-list walk called pair by pair from Python threads"}
+
+
 def _line(name, value, unit, ms, steps, warmup, dtype, config, **extra):
     d = {"metric": "pair-integrals/s and merge-steps/s at 1 GB300 (FP32-comp vs FP64), "
                    "% issue roofline",
@@ -823,11 +862,66 @@ def run_workload(name, args):
                       "paper_context": "L1 on 500,000 such PCFs: ~423 s on 8 A100 "
                                        "(~3.7e7 pair-integrals/s per GPU, precision not stated)"},
                      merge_steps_per_s=rate,
-                     roofline={"bound": "alu", "achieved": rate, "peak": issue(5 + 1 + 4),
-                               "unit": "merge-steps/s", "frac": rate / issue(5 + 1 + 4),
-                               "note": "whole step; tally 10 ops/step (L1, Kahan)"},
+                     roofline={"bound": "alu", "achieved": rate, "peak": issue(5 + 1 + 4 + KEYED_EXTRA),
+                               "unit": "merge-steps/s",
+                               "frac": rate / issue(5 + 1 + 4 + KEYED_EXTRA),
+                               "note": "whole step; tally 13 ops/step (L1, Kahan, exact float64 "
+                                       "comparisons by order keys)"},
                      forms=res,
                      cpu_baseline=_cpu_rows(s, ["l1"], seconds_target=8.0, row0=N // 3))
+
+    if name == "weighted":
+        # the stable-rank workload against a PCF weight: a decaying step
+        # weight w = 1, 1/2, 1/4, ... on [0, 5), [5, 10), ..., 0 after 40 (the
+        # curves' features near the start count more; compact support)
+        s = workload(0, args.n)
+        N = s.n
+        tw = np.arange(0.0, 45.0, 5.0)
+        vw = np.concatenate([0.5 ** np.arange(8), [0.0]])
+        x = P.PcfTensors.from_numpy(s, dev)
+        pairs = 2 * (N * (N - 1) // 2) + N * (N + 1) // 2
+        outs = [torch.empty((N, N), dtype=torch.float32, device=dev) for _ in METRICS]
+        # merge steps of the moved collection: the weight leaves the breakpoints
+        # of [0, 40) and drops those after 40 (a zero-valued end at W(inf))
+        cut = synth.PcfSet(*_clip_after(s, 40.0))
+        steps_walk, diag_steps = exact_walk_steps(cut)
+        res = {}
+        for prec in ("f32c", "f64"):
+            sched = args.schedule or ("tile512x2" if prec == "f32c" else "tile1024")
+            ws = torch.empty(P.pcf_weighted_workspace_size(x, (tw, vw), prec), dtype=torch.uint8,
+                             device=dev)
+
+            def step():
+                P.pcf_pairwise_weighted(x, (tw, vw), METRICS, precision=prec, out=outs,
+                                        workspace=ws, check=False, schedule=sched)
+            ms = _timed(step, max(1, min(args.steps, 3)), 1, flush, stream)
+            P.pcf_check(ws)
+            res[prec] = {"ms_per_step": float(np.mean(ms)), "schedule": sched}
+            del ws
+        ms = res["f32c"]["ms_per_step"]
+        rate = (steps_walk + diag_steps) / (ms * 1e-3)
+        tally = TALLY["f32c"] + KEYED_EXTRA
+        r64 = (steps_walk + diag_steps) / (res["f64"]["ms_per_step"] * 1e-3)
+        cpu = _cpu_rows_weighted(s, (tw, vw), seconds_target=8.0)
+        return _line(name, pairs / (ms * 1e-3), "pair-integrals/s", ms,
+                     max(1, min(args.steps, 3)), 1, "f32 (compensated)",
+                     {"workload": f"stable_rank N={N} against the PCF weight 2^-k on "
+                                  "[5k, 5k+5), k = 0..7, 0 after 40: L1+L2+Gram fused, "
+                                  "full N x N float32",
+                      "N": N, "pairs": pairs, "merge_steps": steps_walk + diag_steps,
+                      "step": "move the breakpoints to W(t) (compacted, float64) + prepare + "
+                              "walk, one pcf_pairwise_weighted call"},
+                     merge_steps_per_s=rate,
+                     roofline={"bound": "alu", "achieved": rate, "peak": issue(tally),
+                               "unit": "merge-steps/s", "frac": rate / issue(tally),
+                               "note": f"whole step; tally {tally} ops/step (fused L1+L2+Gram, "
+                                       "Kahan, order keys)"},
+                     fp64={"value": pairs / (res["f64"]["ms_per_step"] * 1e-3),
+                           "ms_per_step": res["f64"]["ms_per_step"], "merge_steps_per_s": r64,
+                           "roofline": {"bound": "fp64 pipe", "achieved": r64,
+                                        "peak": fp64(FP64_OPS_PER_STEP),
+                                        "frac": r64 / fp64(FP64_OPS_PER_STEP)}},
+                     forms=res, cpu_baseline=cpu)
 
     if name == "segments":
         s = synth.lognormal(n_pcfs=args.n or 100000)
@@ -1072,7 +1166,7 @@ def main():
                     help="force a walk schedule instead of autotuning it")
     ap.add_argument("--workload", default="stable_rank",
                     choices=["stable_rank", "uniform_small", "lognormal", "gradient", "euler",
-                             "appendix_a", "segments", "reduce", "all"])
+                             "appendix_a", "weighted", "segments", "reduce", "all"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -1094,8 +1188,8 @@ def main():
     elif args.workload == "stable_rank":
         run_ours(args)
     else:
-        names = (["uniform_small", "gradient", "lognormal", "euler", "appendix_a", "segments",
-                  "reduce"]
+        names = (["uniform_small", "gradient", "lognormal", "euler", "appendix_a", "weighted",
+                  "segments", "reduce"]
                  if args.workload == "all"
                  else [args.workload])
         for nm in names:
