@@ -97,11 +97,149 @@ __global__ void __launch_bounds__(128, 16) copy_rows_kernel(RowCopy rc, const in
     }
 }
 
+// pos[perm[s]] = s: the sorted position of every input index (after a data
+// error the permutation was never written and nothing is done).
+__global__ void inverse_perm_kernel(const int32_t* __restrict__ perm, int64_t n,
+                                    uint32_t* __restrict__ pos, const Header* hdr)
+{
+    if (hdr->err != kNoError) return;
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+         s += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t i = perm[s];
+        if (i >= 0 && i < n) pos[i] = (uint32_t)s;
+    }
+}
+
+// Rows of a matrix whose columns are in the sort order, put back into the
+// input order in place: a CTA loads one row into shared memory (coalesced,
+// 16-byte vectors when aligned), then writes entry c from sorted column
+// pos[c].  Reads and writes one matrix size each; pos (4N bytes) stays in L2.
+template <typename V>
+__global__ void __launch_bounds__(512) permute_cols_kernel(PermuteMats pm, int64_t n,
+                                                           const uint32_t* __restrict__ pos,
+                                                           const Header* hdr)
+{
+    extern __shared__ __align__(16) unsigned char psm[];
+    V* row_s = reinterpret_cast<V*>(psm);
+    if (hdr->err != kNoError) return;
+    constexpr int VEC = 16 / (int)sizeof(V);
+    for (int m = 0; m < pm.n; ++m) {
+        V* mat = reinterpret_cast<V*>(pm.mat[m]);
+        for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+            V* row = mat + r * n;
+            const bool vec = (n % VEC) == 0 && ((uintptr_t)row % 16) == 0;
+            if (vec) {
+                const int4* src = reinterpret_cast<const int4*>(row);
+                int4* dst = reinterpret_cast<int4*>(row_s);
+                for (int64_t c = threadIdx.x; c < n / VEC; c += blockDim.x) dst[c] = __ldcs(src + c);
+            } else {
+                for (int64_t c = threadIdx.x; c < n; c += blockDim.x) row_s[c] = row[c];
+            }
+            __syncthreads();
+            if (vec) {
+                int4* dst = reinterpret_cast<int4*>(row);
+                for (int64_t c = threadIdx.x; c < n / VEC; c += blockDim.x) {
+                    union { int4 q; V v[VEC]; } u;
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) u.v[e] = row_s[pos[c * VEC + e]];
+                    dst[c] = u.q;
+                }
+            } else {
+                for (int64_t c = threadIdx.x; c < n; c += blockDim.x) row[c] = row_s[pos[c]];
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Copy of completed rows for matrices whose columns are in the sort order:
+// host row r gets entry c from device column pos[c] (gathered through L2;
+// the device row, 4N or 8N bytes, stays there while it is read), written in
+// 16-byte pieces when aligned.  Same grid and placement as copy_rows_kernel.
+template <typename V>
+__global__ void __launch_bounds__(128, 16) gather_rows_kernel(RowCopy rc,
+                                                              const int32_t* __restrict__ perm,
+                                                              const uint32_t* __restrict__ pos,
+                                                              int64_t n, int64_t s0, int64_t s1,
+                                                              int vec16, const Header* hdr)
+{
+    if (block_sees_error(hdr)) return;
+    constexpr int VEC = 16 / (int)sizeof(V);
+    for (int64_t s = s0 + blockIdx.x; s < s1; s += gridDim.x) {
+        const int64_t row = perm[s];
+        if (row < 0 || row >= n) continue;
+#pragma unroll
+        for (int m = 0; m < PCF_MAX_INTEGRALS; ++m) {
+            if (m >= rc.n) break;
+            const V* src = reinterpret_cast<const V*>(rc.src[m]) + row * n;
+            V* dst = reinterpret_cast<V*>(rc.dst[m]) + row * n;
+            if (vec16) {
+                for (int64_t c = threadIdx.x; c < n / VEC; c += blockDim.x) {
+                    union { int4 q; V v[VEC]; } u;
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) u.v[e] = __ldcg(src + pos[c * VEC + e]);
+                    reinterpret_cast<int4*>(dst)[c] = u.q;
+                }
+            } else {
+                for (int64_t c = threadIdx.x; c < n; c += blockDim.x) dst[c] = __ldcg(src + pos[c]);
+            }
+        }
+    }
+}
+
 __global__ void zero_kernel(double* a, int64_t n)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         a[i] = 0.0;
+}
+
+bool permute_cols_fits(int64_t n, int out_f64)
+{
+    const long long bytes = (long long)n * (out_f64 ? 8 : 4);
+    return n > 0 && bytes + 1024 <= (long long)device_smem_optin();
+}
+
+cudaError_t launch_inverse_perm(const int32_t* perm, int64_t n, uint32_t* pos, const Header* hdr,
+                                cudaStream_t s)
+{
+    int64_t blocks = (n + 255) / 256;
+    const int64_t cap = (int64_t)device_sm_count() * 8;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    inverse_perm_kernel<<<(int)blocks, 256, 0, s>>>(perm, n, pos, hdr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute_cols(void* const* mats, int nmats, int64_t n, int out_f64,
+                                const uint32_t* pos, const Header* hdr, cudaStream_t s)
+{
+    PermuteMats pm;
+    memset(&pm, 0, sizeof pm);
+    pm.n = nmats;
+    for (int k = 0; k < nmats; ++k) pm.mat[k] = mats[k];
+    const size_t smem = (size_t)n * (out_f64 ? 8 : 4);
+    int dev = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    int per = (int)((size_t)per_sm / (smem + 1024));
+    if (per < 1) per = 1;
+    if (per > 4) per = 4;
+    int64_t grid = (int64_t)device_sm_count() * per;
+    if (grid > n) grid = n;
+    cudaError_t e;
+    if (out_f64) {
+        e = cudaFuncSetAttribute(permute_cols_kernel<double>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        permute_cols_kernel<double><<<(int)grid, 512, smem, s>>>(pm, n, pos, hdr);
+    } else {
+        e = cudaFuncSetAttribute(permute_cols_kernel<float>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        permute_cols_kernel<float><<<(int)grid, 512, smem, s>>>(pm, n, pos, hdr);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace pcfgb
@@ -485,6 +623,20 @@ static void keyed_bounds(WalkArgs& wa, const pcf_window* win, int form, const Ke
     }
 }
 
+// Put the columns of matrices written with kOutRowsInputColsSorted back into
+// the input order (the length sort's key buffer holds the inverse order).
+static int finish_cols_sorted(const SetView& sv, const pcf_integral* F, int nF, int64_t n,
+                              int out_f64, Header* hdr, cudaStream_t s)
+{
+    uint32_t* pos = sv.khi[0];
+    void* mats[PCF_MAX_INTEGRALS];
+    for (int k = 0; k < nF; ++k) mats[k] = F[k].out;
+    if (launch_inverse_perm(sv.perm, n, pos, hdr, s) != cudaSuccess ||
+        launch_permute_cols(mats, nF, n, out_f64, pos, hdr, s) != cudaSuccess)
+        return PCF_ECUDA;
+    return PCF_OK;
+}
+
 int pcf_prepare(const pcf_csr* x, int precision, void* workspace, size_t workspace_bytes,
                 cudaStream_t stream)
 {
@@ -550,12 +702,18 @@ int pcf_pairwise_ex(const pcf_csr* x, const pcf_integral* F, int nF, int precisi
     wa.ntiles = wa.nb_r * (wa.nb_r + 1) / 2;
     wa.symmetric = 1;
     wa.hdr = hdr;
-    wa.layout = layout;
     wa.out_f64 = out_dtype == PCF_F64;
     wa.ld_out = x->n;
+    // FULL matrices of one call (not a shard) whose rows fit the permutation
+    // pass: written with sorted columns, then put back in place
+    const bool cols_sorted = layout == PCF_OUT_FULL && !(schedule && schedule->shard_count > 1) &&
+                             permute_cols_fits(x->n, wa.out_f64);
+    wa.layout = cols_sorted ? kOutRowsInputColsSorted : layout;
     KElem* kp = reinterpret_cast<KElem*>(sv.packed);
     keyed_bounds(wa, window, form, ks, kp, kp, hdr, stream);
-    return run_walks_for(wa, F, nF, pr, form, schedule, window, stream);
+    rc = run_walks_for(wa, F, nF, pr, form, schedule, window, stream);
+    if (rc != PCF_OK || !cols_sorted) return rc;
+    return finish_cols_sorted(sv, F, nF, x->n, wa.out_f64, hdr, stream);
 }
 
 int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int precision,
@@ -610,9 +768,16 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
     wa.ntiles = wa.nb_r * (wa.nb_r + 1) / 2;
     wa.symmetric = 1;
     wa.hdr = hdr;
-    wa.layout = PCF_OUT_FULL;
     wa.out_f64 = out_dtype == PCF_F64;
     wa.ld_out = N;
+    // rows written with sorted columns (whole DRAM sectors), gathered into the
+    // input order by the copies; the device matrices are put back in place
+    // after the last copy
+    const bool cols_sorted = permute_cols_fits(N, wa.out_f64);
+    wa.layout = cols_sorted ? kOutRowsInputColsSorted : PCF_OUT_FULL;
+    uint32_t* pos = sv.khi[0];
+    if (cols_sorted && launch_inverse_perm(sv.perm, N, pos, hdr, stream) != cudaSuccess)
+        return PCF_ECUDA;
     {
         KElem* kp = reinterpret_cast<KElem*>(sv.packed);
         keyed_bounds(wa, nullptr, form, ks, kp, kp, hdr, stream);
@@ -622,6 +787,11 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
     // the walks run with the largest shared-memory carve-out; a CTA that asks
     // for another split of L1 cannot join an SM they occupy
     if (cudaFuncSetAttribute(copy_rows_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
+        cudaFuncSetAttribute(gather_rows_kernel<float>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess ||
+        cudaFuncSetAttribute(gather_rows_kernel<double>,
+                             cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess)
         return PCF_ECUDA;
 
@@ -640,8 +810,15 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
         }
         const int64_t cap = sms / 2 > 0 ? sms / 2 : 1;
         const int64_t grid = (s1 - s0) < cap ? (s1 - s0) : cap;
-        copy_rows_kernel<<<(int)grid, 128, 0, cs>>>(cp, sv.perm, N, s0, s1, row_bytes, vec16 ? 1 : 0,
-                                                    hdr);
+        if (!cols_sorted)
+            copy_rows_kernel<<<(int)grid, 128, 0, cs>>>(cp, sv.perm, N, s0, s1, row_bytes,
+                                                        vec16 ? 1 : 0, hdr);
+        else if (wa.out_f64)
+            gather_rows_kernel<double><<<(int)grid, 128, 0, cs>>>(cp, sv.perm, pos, N, s0, s1,
+                                                                  vec16 ? 1 : 0, hdr);
+        else
+            gather_rows_kernel<float><<<(int)grid, 128, 0, cs>>>(cp, sv.perm, pos, N, s0, s1,
+                                                                 vec16 ? 1 : 0, hdr);
         return cudaGetLastError() == cudaSuccess;
     };
 
@@ -686,6 +863,10 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
         }
     }
     if (!join()) return PCF_ECUDA;
+    if (cols_sorted) {
+        rc = finish_cols_sorted(sv, F, nF, N, wa.out_f64, hdr, stream);
+        if (rc != PCF_OK) return rc;
+    }
     return cudaGetLastError() == cudaSuccess ? PCF_OK : PCF_ECUDA;
 }
 
@@ -1024,12 +1205,16 @@ int pcf_pairwise_weighted(const pcf_csr* x, const pcf_csr* w, const pcf_integral
     wa.ntiles = wa.nb_r * (wa.nb_r + 1) / 2;
     wa.symmetric = 1;
     wa.hdr = hdr;
-    wa.layout = layout;
     wa.out_f64 = out_dtype == PCF_F64;
     wa.ld_out = m.n;
+    const bool cols_sorted = layout == PCF_OUT_FULL && !(schedule && schedule->shard_count > 1) &&
+                             permute_cols_fits(m.n, wa.out_f64);
+    wa.layout = cols_sorted ? kOutRowsInputColsSorted : layout;
     KElem* kp = reinterpret_cast<KElem*>(sv.packed);
     keyed_bounds(wa, nullptr, form, ks, kp, kp, hdr, stream);
-    return run_walks_for(wa, F, nF, pr, form, schedule, nullptr, stream);
+    rc = run_walks_for(wa, F, nF, pr, form, schedule, nullptr, stream);
+    if (rc != PCF_OK || !cols_sorted) return rc;
+    return finish_cols_sorted(sv, F, nF, m.n, wa.out_f64, hdr, stream);
 }
 
 int pcf_walk_promoted(const void* workspace, cudaStream_t stream, int* promoted)

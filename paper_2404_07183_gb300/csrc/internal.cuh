@@ -215,6 +215,13 @@ __device__ __forceinline__ bool gated_off(const unsigned int* gate, int want64)
 }
 #endif
 
+// Internal output layout of the FULL pairwise matrices: rows in the input
+// order, columns in the sort order, entry (i, t) = F(x_i, x[perm[t]]).  A
+// tile's results then fill contiguous 128-byte row segments (whole DRAM
+// sectors) instead of single entries scattered by the permutation; a
+// per-row pass (permute_cols_kernel) restores the input order of the columns.
+constexpr int kOutRowsInputColsSorted = 100;
+
 // Metric combination codes compiled into the walk kernels.
 enum Combo : int {
     kComboL1 = 0, kComboL2 = 1, kComboGram = 2, kComboLP = 3, kComboL3 = 4,
@@ -283,5 +290,17 @@ constexpr double kAuto64MinRelGap = 9.313225746154785e-10;   // 2^-30
 
 int device_sm_count();
 int device_smem_optin();
+
+// Columns of rows-in-input-order matrices back to the input order (api.cu).
+struct PermuteMats {
+    void* mat[PCF_MAX_INTEGRALS];
+    int n;
+};
+cudaError_t launch_inverse_perm(const int32_t* perm, int64_t n, uint32_t* pos, const Header* hdr,
+                                cudaStream_t s);
+cudaError_t launch_permute_cols(void* const* mats, int nmats, int64_t n, int out_f64,
+                                const uint32_t* pos, const Header* hdr, cudaStream_t s);
+// Largest N whose row fits the permutation pass's shared memory.
+bool permute_cols_fits(int64_t n, int out_f64);
 
 }  // namespace pcfgb

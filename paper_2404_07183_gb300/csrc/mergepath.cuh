@@ -173,6 +173,9 @@ __global__ void __launch_bounds__(256, 4) mergepath_kernel(const WalkArgs a, int
                 } else if (a.layout == PCF_OUT_FULL) {
                     put(i * a.ld_out + j);
                     if (gi != gj) put(j * a.ld_out + i);
+                } else if (a.layout == kOutRowsInputColsSorted) {
+                    put(i * a.ld_out + gj);
+                    if (gi != gj) put(j * a.ld_out + gi);
                 } else if (a.layout == PCF_OUT_FULL_SORTED) {
                     put(gi * a.ld_out + gj);
                     if (gi != gj) put(gj * a.ld_out + gi);

@@ -615,6 +615,9 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                 } else if (a.layout == PCF_OUT_FULL) {
                     put(i * a.ld_out + j);
                     if (bi != bj) put(j * a.ld_out + i);
+                } else if (a.layout == kOutRowsInputColsSorted) {
+                    put(i * a.ld_out + gj);
+                    if (bi != bj) put(j * a.ld_out + gi);
                 } else if (a.layout == PCF_OUT_FULL_SORTED) {
                     put(gi * a.ld_out + gj);
                     if (bi != bj) put(gj * a.ld_out + gi);
