@@ -62,11 +62,10 @@ def tally(prec, input_f64=True):
 FP64_OPS_PER_STEP = 1 + 1 + 1 + 2 + 2   # dt, d, L1 fma, L2 mul+fma, Gram mul+fma
 
 # DRAM bytes (read + write) per launch of the benchmark's compensated walk,
-# from one ncu capture (profiles/walk_f32c_dram_traffic_stable_rank_n20000.md),
+# from one ncu capture (profiles/walk_f32ck_dram_traffic_stable_rank_n20000.md),
 # valid only while the walk's source is the one that was measured.
-TRAFFIC_RECORD = {"source_sha256_16": "83224553141c903e+6476604921ab2901",
-                  "by_schedule_layout": {("tile512x3", "full"): 34976396800 + 32674568192,
-                                         ("tile512x3", "sorted"): 381729280 + 5583988992}}
+TRAFFIC_RECORD = {"source_sha256_16": "63b51f2f820f772e+0292acba9d35fba0",
+                  "by_schedule_layout": {("tile512x2", "full"): 5169820672 + 4782777088}}
 
 
 def walk_source_id():
