@@ -84,6 +84,17 @@ def dist_env():
     return rank, world, local
 
 
+def step_launches(prec, layout="full", input_f64=True):
+    """Kernels one timed step launches: pcf_prepare (header, validation,
+    length sort, pack; for float64 input in a float32 walk the key sort: key
+    count, 8 passes of histogram + two row scans + scatter, distinct-key
+    count, its scan and the rank write), pcf_pairwise (tile counter, walk;
+    FULL layout: inverse permutation and the column pass)."""
+    keyed = input_f64 and prec in ("f32c", "f32b", "f32")
+    n = 4 + (1 + 8 * 4 + 3 if keyed else 0) + 2
+    return n + (2 if layout == "full" else 0)
+
+
 def resolve_launch(gpus, env, device_count):
     """What to do with ``--gpus N`` in this process: ("run", world) when the
     process is one of the N ranks (WORLD_SIZE == N under torchrun, or N == 1),
@@ -545,7 +556,7 @@ def run_ours(args):
         "merge_steps_per_s": units * (walk_steps + diag_steps) / (head["ms_per_step"] * 1e-3),
         "walk": {"ms": head["walk_ms"], "prepare_ms": head["prepare_ms"],
                  "merge_steps_per_s": walk_rate},
-        "gpu_launches": head["steps"] * (4 + 2 + (23 if "round" not in prec else 0)),
+        "gpu_launches": head["steps"] * step_launches(prec, args.layout),
         "e2e": {"value": units * pairs / e2e_s, "unit": "pair-integrals/s",
                 "h2d_bytes_per_step": world * h2d, "d2h_bytes_per_step": world * d2h,
                 "ms_per_step": e2e_s * 1e3,
@@ -834,7 +845,7 @@ def run_workload(name, args):
         o = [torch.empty((N, N), dtype=torch.float32, device=dev)]
         from paper_2404_07183_gb300 import autotune
         res = {}
-        for prec in ("f32c", "f32", "f64"):
+        for prec in ("f32c", "f32", "f64", "f32c_round"):
             if args.schedule:
                 sched = args.schedule
             else:

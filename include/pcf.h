@@ -374,6 +374,19 @@ int pcf_pairwise_weighted(const pcf_csr* x, const pcf_csr* w, const pcf_integral
                           void* workspace, size_t workspace_bytes, cudaStream_t stream);
 
 /*
+ * Cross matrices against a non-negative PCF weight w: rows [row_begin,
+ * row_end) of a against all of b, F_ij = r(int h(a_i, b_j) w dt), output
+ * blocks as pcf_cross.  Both collections are moved to W(t) for every call
+ * (there is no reuse of b).  Workspace: pcf_cross_weighted_workspace_size.
+ */
+int pcf_cross_weighted_workspace_size(const pcf_csr* a, const pcf_csr* b, const pcf_csr* w,
+                                      int precision, size_t* bytes);
+int pcf_cross_weighted(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row_end,
+                       const pcf_csr* w, const pcf_integral* F, int nF, int precision,
+                       int64_t ld_out, int out_dtype, const pcf_schedule* schedule,
+                       void* workspace, size_t workspace_bytes, cudaStream_t stream);
+
+/*
  * Single-PCF integrals by segment iteration (Sec. 3.2, Alg. 3):
  *   out[i] = r( int_a^b h(f_i(t)) dt ),  0 <= a < b <= inf,
  * h per pcf_functional; r(x) = x^(1/p) for PCF_FN_LP with apply_root, else x.

@@ -39,6 +39,7 @@ ERR_DETAIL = {
 SYMBOLS = ("pcf_workspace_size", "pcf_prepare", "pcf_pairwise", "pcf_cross", "pcf_pairwise_backward",
            "pcf_check", "pcf_status_string", "pcf_version", "pcf_pairwise_noalloc",
            "pcf_walk_promoted", "pcf_weighted_workspace_size", "pcf_pairwise_weighted",
+           "pcf_cross_weighted_workspace_size", "pcf_cross_weighted",
            "pcf_pairwise_ex", "pcf_cross_ex", "pcf_sort_order", "pcf_segment_integrals",
            "pcf_reduce_workspace_size", "pcf_reduce", "pcf_combine_workspace_size",
            "pcf_combine", "pcf_reduce_counters", "pcf_selftest_wait_timeout",
@@ -137,6 +138,10 @@ def load(build_if_missing: bool = False):
         lib.pcf_weighted_workspace_size.argtypes = [CSR, CSR, I, ctypes.POINTER(SZ)]
         lib.pcf_pairwise_weighted.restype = I
         lib.pcf_pairwise_weighted.argtypes = [CSR, CSR, INT, I, I, I, I, P, P, SZ, P]
+        lib.pcf_cross_weighted_workspace_size.restype = I
+        lib.pcf_cross_weighted_workspace_size.argtypes = [CSR, CSR, CSR, I, ctypes.POINTER(SZ)]
+        lib.pcf_cross_weighted.restype = I
+        lib.pcf_cross_weighted.argtypes = [CSR, CSR, I64, I64, CSR, INT, I, I, I64, I, P, P, SZ, P]
         lib.pcf_status_string.restype = ctypes.c_char_p
         lib.pcf_status_string.argtypes = [I]
         lib.pcf_pairwise_noalloc.restype = I

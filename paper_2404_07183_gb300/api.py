@@ -26,7 +26,7 @@ __all__ = ["PcfError", "PcfTensors", "pcf_workspace_size", "pcf_prepare", "pcf_s
            "pcf_pairwise", "pcf_cross",
            "pcf_cross_to_host",
            "pcf_pairwise_backward", "pcf_check", "pcf_walk_promoted", "pcf_pairwise_weighted",
-           "pcf_weighted_workspace_size", "PairwiseFn", "PairwiseGraph", "pdist",
+           "pcf_weighted_workspace_size", "pcf_cross_weighted", "PairwiseFn", "PairwiseGraph", "pdist",
            "l2_kernel", "pcf_reduce", "pcf_combine", "pcf_reduce_counters", "mean", "std",
            "parse_metric", "PRECISIONS", "REDUCTIONS", "OPS"]
 
@@ -357,6 +357,42 @@ def pcf_pairwise_weighted(x: PcfTensors, w, metrics=("l1",), precision="f32c", l
         raise PcfError(rc, "pcf_pairwise_weighted")
     if check:
         pcf_check(ws, stream, "pcf_pairwise_weighted")
+    return out
+
+
+def pcf_cross_weighted(a: PcfTensors, b: PcfTensors, w, row_begin=0, row_end=None,
+                       metrics=("l1",), precision="f32c", out_dtype=torch.float32, out=None,
+                       ld_out=None, workspace=None, stream=None, check=True, schedule=None):
+    """Cross block r(int h(a_i, b_j) w dt) for rows [row_begin, row_end) of
+    ``a`` against all of ``b``, for one non-negative PCF weight ``w``."""
+    lib = abi.load()
+    if isinstance(metrics, (str, tuple)):
+        metrics = [metrics]
+    metrics = list(metrics)
+    row_end = a.n if row_end is None else row_end
+    rows = row_end - row_begin
+    dev = b.times.device
+    wt = _weight_tensors(w, dev)
+    ld = b.n if ld_out is None else ld_out
+    if out is None:
+        out = [torch.empty((rows, ld), dtype=out_dtype, device=dev) for _ in metrics]
+    ca, cb, cw = a.csr(), b.csr(), wt.csr()
+    size = ctypes.c_size_t()
+    rc = lib.pcf_cross_weighted_workspace_size(ctypes.byref(ca), ctypes.byref(cb), ctypes.byref(cw),
+                                               _prec(precision), ctypes.byref(size))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_cross_weighted_workspace_size")
+    ws = _workspace(int(size.value), dev, workspace)
+    req = _requests(metrics, out)
+    od = abi.PCF_F64 if out[0].dtype == torch.float64 else abi.PCF_F32
+    rc = lib.pcf_cross_weighted(ctypes.byref(ca), ctypes.byref(cb), row_begin, row_end,
+                                ctypes.byref(cw), req, len(metrics), _prec(precision), ld, od,
+                                _schedule(schedule), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                _stream_handle(stream))
+    if rc != abi.PCF_OK:
+        raise PcfError(rc, "pcf_cross_weighted")
+    if check:
+        pcf_check(ws, stream, "pcf_cross_weighted")
     return out
 
 def pcf_cross(a: PcfTensors, b: PcfTensors, row_begin=0, row_end=None, metrics=("l1",),

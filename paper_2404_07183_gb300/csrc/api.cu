@@ -878,30 +878,18 @@ int pcf_cross(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row
                         nullptr, nullptr, workspace, workspace_bytes, stream);
 }
 
-int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row_end,
-                 const pcf_integral* F, int nF, int precision, int64_t ld_out, int out_dtype,
-                 int flags, const pcf_schedule* schedule, const pcf_window* window,
-                 void* workspace, size_t workspace_bytes, cudaStream_t stream)
+// The cross walk of rows [row_begin, row_end) of a against b (checked
+// arguments and workspace).  moved: a and b are collections built by earlier
+// kernels of the call (moved to a weight's time): the header is already
+// initialized, their offsets are not whole arrays and their validation is
+// skipped after an earlier error.
+static int cross_impl(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row_end,
+                      const pcf_integral* F, int nF, const Prec& pr, int64_t ld_out, int out_dtype,
+                      int flags, const pcf_schedule* schedule, const pcf_window* window,
+                      void* workspace, cudaStream_t stream, bool moved)
 {
-    if (!csr_ok(a) || !csr_ok(b)) return PCF_EINVAL;
-    Prec pr;
-    if (!parse_prec(precision, &pr)) return PCF_EINVAL;
-    if (out_dtype != PCF_F32 && out_dtype != PCF_F64) return PCF_EINVAL;
-    if (row_begin < 0 || row_end < row_begin || row_end > a->n) return PCF_EINVAL;
-    if (ld_out < b->n) return PCF_EINVAL;
-    if (flags & ~PCF_CROSS_REUSE_B) return PCF_EINVAL;
-    if (check_schedule(schedule) != PCF_OK) return PCF_EINVAL;
-    if (check_window(window) != PCF_OK) return PCF_EINVAL;
     const int64_t rows = row_end - row_begin;
-    int rc = check_requests(F, nF, rows > 0 && b->n > 0);
-    if (rc != PCF_OK) return rc;
     const int form = call_form(pr, a, b);
-    if (form == kPackKeyed && key_capacity(a, b) > 0x7fffffffLL) return PCF_EUNSUPPORTED;
-    size_t need = 0;
-    pcf_workspace_size(a, b, precision, PCF_WS_FORWARD, &need);
-    if (!workspace || ((uintptr_t)workspace % kAlign) != 0 || workspace_bytes < need) return PCF_ENOWS;
-    if (rows == 0 || b->n == 0) return PCF_OK;
-
     char* cur = (char*)workspace;
     Header* hdr = (Header*)cur;
     cur += sizeof(Header);
@@ -911,7 +899,7 @@ int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t 
     KeySort ks;
     if (form == kPackKeyed) ks = carve_keysort(cur, key_capacity(a, b));
     const bool reuse = (flags & PCF_CROSS_REUSE_B) != 0;
-    init_header_kernel<<<1, 1, 0, stream>>>(hdr, reuse ? 1 : 0);
+    if (!moved) init_header_kernel<<<1, 1, 0, stream>>>(hdr, reuse ? 1 : 0);
     // keyed: B's interval ends first in the sort input, then A's; both are
     // ranked together every call (A's rows change, so B's ranks do too: a
     // reused B keeps its validation and length sort and is packed again)
@@ -927,12 +915,13 @@ int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t 
     const KeyOut* pka = form == kPackKeyed ? &ka : nullptr;
     const bool a64 = pr.auto64 && form != kPackF64;
     if (!reuse) {
-        if (prepare_set(b->offsets, b->times, b->values, b->dtype, b->n, b->nnz, true, form, hdr, sb,
-                        stream, pkb, a64) != cudaSuccess)
+        if (prepare_set(b->offsets, b->times, b->values, b->dtype, b->n, b->nnz, !moved, form, hdr,
+                        sb, stream, pkb, a64, moved) != cudaSuccess)
             return PCF_ECUDA;
     }
     if (prepare_set(a->offsets + row_begin, a->times, a->values, a->dtype, rows, a->nnz,
-                    row_begin == 0 && row_end == a->n, form, hdr, sa, stream, pka, a64) != cudaSuccess)
+                    !moved && row_begin == 0 && row_end == a->n, form, hdr, sa, stream, pka, a64,
+                    moved) != cudaSuccess)
         return PCF_ECUDA;
     if (reuse && a64) {
         // the new rows may change the choice: B packed again in both gated forms
@@ -968,6 +957,33 @@ int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t 
     wa.ld_out = ld_out;
     keyed_bounds(wa, window, form, ks, kpa, kpb, hdr, stream);
     return run_walks_for(wa, F, nF, pr, form, schedule, window, stream);
+}
+
+int pcf_cross_ex(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row_end,
+                 const pcf_integral* F, int nF, int precision, int64_t ld_out, int out_dtype,
+                 int flags, const pcf_schedule* schedule, const pcf_window* window,
+                 void* workspace, size_t workspace_bytes, cudaStream_t stream)
+{
+    if (!csr_ok(a) || !csr_ok(b)) return PCF_EINVAL;
+    Prec pr;
+    if (!parse_prec(precision, &pr)) return PCF_EINVAL;
+    if (out_dtype != PCF_F32 && out_dtype != PCF_F64) return PCF_EINVAL;
+    if (row_begin < 0 || row_end < row_begin || row_end > a->n) return PCF_EINVAL;
+    if (ld_out < b->n) return PCF_EINVAL;
+    if (flags & ~PCF_CROSS_REUSE_B) return PCF_EINVAL;
+    if (check_schedule(schedule) != PCF_OK) return PCF_EINVAL;
+    if (check_window(window) != PCF_OK) return PCF_EINVAL;
+    const int64_t rows = row_end - row_begin;
+    int rc = check_requests(F, nF, rows > 0 && b->n > 0);
+    if (rc != PCF_OK) return rc;
+    const int form = call_form(pr, a, b);
+    if (form == kPackKeyed && key_capacity(a, b) > 0x7fffffffLL) return PCF_EUNSUPPORTED;
+    size_t need = 0;
+    pcf_workspace_size(a, b, precision, PCF_WS_FORWARD, &need);
+    if (!workspace || ((uintptr_t)workspace % kAlign) != 0 || workspace_bytes < need) return PCF_ENOWS;
+    if (rows == 0 || b->n == 0) return PCF_OK;
+    return cross_impl(a, b, row_begin, row_end, F, nF, pr, ld_out, out_dtype, flags, schedule,
+                      window, workspace, stream, false);
 }
 
 int pcf_pairwise_backward(const pcf_csr* x, int metric, double p, int apply_root,
@@ -1215,6 +1231,95 @@ int pcf_pairwise_weighted(const pcf_csr* x, const pcf_csr* w, const pcf_integral
     rc = run_walks_for(wa, F, nF, pr, form, schedule, nullptr, stream);
     if (rc != PCF_OK || !cols_sorted) return rc;
     return finish_cols_sorted(sv, F, nF, m.n, wa.out_f64, hdr, stream);
+}
+
+// Shapes of a cross call against a weight: rows [row_begin, row_end) of a
+// and all of b, each moved to W(t).
+static void cross_moved_shapes(const pcf_csr* a, const pcf_csr* b, int64_t rows, pcf_csr* am,
+                               pcf_csr* bm)
+{
+    pcf_csr ar = *a;
+    ar.n = rows;
+    *am = moved_shape(&ar);
+    *bm = moved_shape(b);
+}
+
+int pcf_cross_weighted_workspace_size(const pcf_csr* a, const pcf_csr* b, const pcf_csr* w,
+                                      int precision, size_t* bytes)
+{
+    if (!bytes || !a || !b || a->n < 0 || b->n < 0 || a->nnz < 0 || b->nnz < 0 ||
+        a->n > 0x7fffffffLL || b->n > 0x7fffffffLL)
+        return PCF_EINVAL;
+    if (!w || w->n != 1 || w->nnz < 1) return PCF_EINVAL;
+    pcf_csr am, bm;
+    cross_moved_shapes(a, b, a->n, &am, &bm);
+    size_t inner = 0;
+    const int rc = pcf_workspace_size(&am, &bm, precision, PCF_WS_FORWARD, &inner);
+    if (rc != PCF_OK) return rc;
+    *bytes = align_up(inner) + weight_scratch_bytes(a->n, a->nnz, w->nnz) +
+             weight_scratch_bytes(b->n, b->nnz, w->nnz);
+    return PCF_OK;
+}
+
+int pcf_cross_weighted(const pcf_csr* a, const pcf_csr* b, int64_t row_begin, int64_t row_end,
+                       const pcf_csr* w, const pcf_integral* F, int nF, int precision,
+                       int64_t ld_out, int out_dtype, const pcf_schedule* schedule,
+                       void* workspace, size_t workspace_bytes, cudaStream_t stream)
+{
+    if (!csr_ok(a) || !csr_ok(b) || !weight_ok(w)) return PCF_EINVAL;
+    Prec pr;
+    if (!parse_prec(precision, &pr)) return PCF_EINVAL;
+    if (out_dtype != PCF_F32 && out_dtype != PCF_F64) return PCF_EINVAL;
+    if (row_begin < 0 || row_end < row_begin || row_end > a->n) return PCF_EINVAL;
+    if (ld_out < b->n) return PCF_EINVAL;
+    if (check_schedule(schedule) != PCF_OK) return PCF_EINVAL;
+    const int64_t rows = row_end - row_begin;
+    int rc = check_requests(F, nF, rows > 0 && b->n > 0);
+    if (rc != PCF_OK) return rc;
+    size_t need = 0;
+    rc = pcf_cross_weighted_workspace_size(a, b, w, precision, &need);
+    if (rc != PCF_OK) return rc;
+    if (!workspace || ((uintptr_t)workspace % kAlign) != 0 || workspace_bytes < need) return PCF_ENOWS;
+    if (rows == 0 || b->n == 0) return PCF_OK;
+
+    // [the cross workspace of the moved collections][weight scratch a][b]
+    pcf_csr am, bm, afull;
+    cross_moved_shapes(a, b, a->n, &am, &afull);
+    cross_moved_shapes(a, b, rows, &am, &bm);
+    size_t inner = 0;
+    {
+        pcf_csr am_full = moved_shape(a);
+        pcf_workspace_size(&am_full, &bm, precision, PCF_WS_FORWARD, &inner);
+    }
+    char* wcur = (char*)workspace + align_up(inner);
+    const WeightScratch wa_s = carve_weight(wcur, rows, a->nnz, w->nnz);
+    const WeightScratch wb_s = carve_weight(wcur, b->n, b->nnz, w->nnz);
+    am.offsets = wa_s.off2; am.times = wa_s.t2; am.values = wa_s.v2;
+    bm.offsets = wb_s.off2; bm.times = wb_s.t2; bm.values = wb_s.v2;
+    const int form = call_form(pr, &am, &bm);
+    if (form == kPackKeyed && key_capacity(&am, &bm) > 0x7fffffffLL) return PCF_EUNSUPPORTED;
+
+    Header* hdr = (Header*)workspace;
+    init_header_kernel<<<1, 1, 0, stream>>>(hdr, 0);
+    // the inputs are checked before they are moved (scratch set views of the
+    // cross workspace serve the checks' length arrays)
+    {
+        char* cur = (char*)workspace + sizeof(Header);
+        SetView sb = carve_set(cur, bm.n, bm.nnz, call_elem_bytes(pr, form), 1);
+        SetView sa = carve_set(cur, rows, am.nnz, call_elem_bytes(pr, form), 0);
+        pcf_csr arows = *a;
+        arows.offsets = a->offsets + row_begin;
+        arows.n = rows;
+        if (launch_validate(b->offsets, b->times, b->values, b->dtype, b->n, b->nnz, kPackF64, hdr,
+                            sb, stream) != cudaSuccess ||
+            launch_validate(arows.offsets, a->times, a->values, a->dtype, rows, a->nnz, kPackF64,
+                            hdr, sa, stream, row_begin == 0 && row_end == a->n) != cudaSuccess ||
+            launch_weight_move(&arows, w, wa_s, hdr, stream) != cudaSuccess ||
+            launch_weight_move(b, w, wb_s, hdr, stream) != cudaSuccess)
+            return PCF_ECUDA;
+    }
+    return cross_impl(&am, &bm, 0, rows, F, nF, pr, ld_out, out_dtype, 0, schedule, nullptr,
+                      workspace, stream, true);
 }
 
 int pcf_walk_promoted(const void* workspace, cudaStream_t stream, int* promoted)

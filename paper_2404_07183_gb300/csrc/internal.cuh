@@ -280,7 +280,7 @@ cudaError_t launch_segments(const pcf_csr* x, int functional, double p, int appl
                             Header* hdr, void* scratch, cudaStream_t s);
 cudaError_t launch_validate(const int64_t* offsets, const void* times, const void* values,
                             int in_dtype, int64_t n, int64_t nnz_total, int form,
-                            Header* hdr, SetView& sv, cudaStream_t s);
+                            Header* hdr, SetView& sv, cudaStream_t s, int whole = 1);
 
 // AUTO64 thresholds: a float64 collection needs the float64 walk when a time
 // or value lies outside float32's normal range (above FLT_MAX, or nonzero

@@ -364,17 +364,17 @@ static int grid_for_warps(int64_t warps)
 
 cudaError_t launch_validate(const int64_t* offsets, const void* times, const void* values,
                             int in_dtype, int64_t n, int64_t nnz_total, int form,
-                            Header* hdr, SetView& sv, cudaStream_t s)
+                            Header* hdr, SetView& sv, cudaStream_t s, int whole)
 {
     if (n == 0) return cudaSuccess;
     const int g = grid_for_warps(n);
     const int walk_f32 = form != kPackF64;
     if (in_dtype == PCF_F64) {
         validate_kernel<double><<<g, 256, 0, s>>>(offsets, (const double*)times,
-            (const double*)values, n, nnz_total, 1, walk_f32, sv.lens, sv.skey, hdr, sv.slot, 0);
+            (const double*)values, n, nnz_total, whole, walk_f32, sv.lens, sv.skey, hdr, sv.slot, 0);
     } else {
         validate_kernel<float><<<g, 256, 0, s>>>(offsets, (const float*)times,
-            (const float*)values, n, nnz_total, 1, walk_f32, sv.lens, sv.skey, hdr, sv.slot, 0);
+            (const float*)values, n, nnz_total, whole, walk_f32, sv.lens, sv.skey, hdr, sv.slot, 0);
     }
     return cudaGetLastError();
 }

@@ -173,6 +173,23 @@ struct AccSet {
         for (int m = 0; m < NM; ++m) a[m].flush();
     }
     __device__ __forceinline__ double value(int m) const { return a[m].value(); }
+    // the step's integrand values h(va, vb) per metric, before the advance
+    struct Terms { float h[NM]; };
+    template <typename T>
+    __device__ __forceinline__ Terms terms(T va, T vb, T p) const
+    {
+        Terms t;
+        const T d = va - vb;
+        t.h[0] = term_h<combo_metric(COMBO, 0)>(va, vb, d, p);
+        if constexpr (NM > 1) t.h[1] = term_h<combo_metric(COMBO, 1)>(va, vb, d, p);
+        if constexpr (NM > 2) t.h[2] = term_h<combo_metric(COMBO, 2)>(va, vb, d, p);
+        return t;
+    }
+    __device__ __forceinline__ void add_terms(const Terms& t, float dt)
+    {
+#pragma unroll
+        for (int m = 0; m < NM; ++m) a[m].add(t.h[m], dt);
+    }
 };
 
 template <int PREC, int COMBO>
@@ -229,24 +246,29 @@ __device__ __forceinline__ void advance_cursor(unsigned& af, double& tf, double&
                  : "memory");
 }
 
-// Keyed form: the side whose interval ends first is the one with the smaller
-// order key (f on equal keys, i.e. equal float64 times); it advances and its
-// next KElem (key, hi, lo, value) is loaded in place.
+// Keyed advance: the side whose interval ends first is the one with the
+// smaller order key (f on equal keys, i.e. equal float64 times).  One
+// predicate selects that side's end (hi, lo), the rectangle's right end, and
+// then advances the side, loading its next KElem (key, hi, lo, value) in
+// place: the compare is made once for both.
 template <unsigned kRowBytes>
-__device__ __forceinline__ void advance_cursor_keyed(unsigned& af, uint32_t& kf, float& hf,
+__device__ __forceinline__ void advance_select_keyed(unsigned& af, uint32_t& kf, float& hf,
                                                      float& lf, float& vf, unsigned& ag,
-                                                     uint32_t& kg, float& hg, float& lg, float& vg)
+                                                     uint32_t& kg, float& hg, float& lg, float& vg,
+                                                     float& hn, float& ln)
 {
     asm volatile("{\n\t"
                  ".reg .pred p;\n\t"
                  "setp.le.u32 p, %1, %6;\n\t"
-                 "@p add.u32 %0, %0, %10;\n\t"
+                 "selp.f32 %10, %2, %7, p;\n\t"
+                 "selp.f32 %11, %3, %8, p;\n\t"
+                 "@p add.u32 %0, %0, %12;\n\t"
                  "@p ld.shared.v4.b32 {%1, %2, %3, %4}, [%0];\n\t"
-                 "@!p add.u32 %5, %5, %10;\n\t"
+                 "@!p add.u32 %5, %5, %12;\n\t"
                  "@!p ld.shared.v4.b32 {%6, %7, %8, %9}, [%5];\n\t"
                  "}"
                  : "+r"(af), "+r"(kf), "+f"(hf), "+f"(lf), "+f"(vf),
-                   "+r"(ag), "+r"(kg), "+f"(hg), "+f"(lg), "+f"(vg)
+                   "+r"(ag), "+r"(kg), "+f"(hg), "+f"(lg), "+f"(vg), "=f"(hn), "=f"(ln)
                  : "n"(kRowBytes)
                  : "memory");
 }
@@ -530,14 +552,17 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                     // width of [tc, te_n) from the hi and lo parts of both ends
 #define PCF_WALK_STEP()                                                           \
                     {                                                             \
-                        const bool fe = kf <= kg;                                 \
-                        const float hn = fe ? hf : hg, ln = fe ? lf : lg;         \
+                        /* integrand values from the current elements, then the */ \
+                        /* end of the rectangle and the advance in one PTX block */ \
+                        const float va = vf, vb = vg;                             \
+                        float hn, ln;                                             \
+                        auto terms = acc.terms(va, vb, p0);                       \
+                        advance_select_keyed<kRow>(af, kf, hf, lf, vf, ag, kg, hg, lg, vg, hn, ln); \
                         const float w = __fadd_rn(__fsub_rn(hn, tc), __fsub_rn(ln, tcl)); \
                         const float dt = weight_span<WEIGHT>(tc, w, lam, inv_lam); \
                         tc = hn;                                                  \
                         tcl = ln;                                                 \
-                        acc.add(vf, vg, dt, p0);                                  \
-                        advance_cursor_keyed<kRow>(af, kf, hf, lf, vf, ag, kg, hg, lg, vg); \
+                        acc.add_terms(terms, dt);                                 \
                     }
 #pragma unroll 1
                     for (; cnt >= 16; cnt -= 16) {

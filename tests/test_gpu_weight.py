@@ -175,3 +175,37 @@ def test_invalid_collection_reported_before_the_weight_is_applied(pcf):
     with pytest.raises(pcf.PcfError) as ei:
         pcf.pcf_pairwise_weighted(x, _weight(512), ["l1"], precision="f32c")
     assert ei.value.detail == 3 and ei.value.index == k + 1
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32c"])
+def test_weighted_cross_row_blocks(pcf, prec):
+    """Row blocks of a against b, each call moving both to W(t)."""
+    import torch
+    a = synth.random_set(70, seed=513, min_len=1, max_len=50)
+    b = synth.random_set(45, seed=514, min_len=1, max_len=70)
+    w = _weight(515)
+    xa, xb = pcf.PcfTensors.from_numpy(a, "cuda"), pcf.PcfTensors.from_numpy(b, "cuda")
+    out = torch.full((a.n, b.n + 2), np.nan, dtype=torch.float64, device="cuda")
+    outs = [out.clone() for _ in range(2)]
+    for r0 in range(0, a.n, 32):
+        r1 = min(a.n, r0 + 32)
+        pcf.pcf_cross_weighted(xa, xb, w, r0, r1, ["l1", "gram"], precision=prec,
+                               out=[o[r0:r1] for o in outs], ld_out=b.n + 2)
+    da = np.array([oracle.integral_w(*a.pcf(i), *a.pcf(i), *w, "gram") for i in range(a.n)])
+    db = np.array([oracle.integral_w(*b.pcf(j), *b.pcf(j), *w, "gram") for j in range(b.n)])
+    for m, o in zip(("l1", "gram"), outs):
+        o = o.cpu().numpy()
+        assert np.all(np.isnan(o[:, b.n:]))
+        want = oracle.matrix_w(a, w, b, metric=m)
+        if m == "gram":
+            scale = np.sqrt(np.outer(da, db))
+            err = np.max(np.abs(o[:, :b.n] - want) / np.where(scale > 0, scale, 1.0))
+        else:
+            err = max_rel_error(m, o[:, :b.n], want)
+        assert err <= TOL[prec], (m, err)
+    # w = 1: the unweighted cross block bit for bit
+    one = (np.array([0.0]), np.array([1.0]))
+    got = pcf.pcf_cross_weighted(xa, xb, one, 10, 50, ["l1"], precision=prec,
+                                 out_dtype=torch.float64)[0]
+    ref = pcf.pcf_cross(xa, xb, 10, 50, ["l1"], precision=prec, out_dtype=torch.float64)[0]
+    np.testing.assert_array_equal(got.cpu().numpy(), ref.cpu().numpy())
