@@ -64,8 +64,8 @@ FP64_OPS_PER_STEP = 1 + 1 + 1 + 2 + 2   # dt, d, L1 fma, L2 mul+fma, Gram mul+fm
 # DRAM bytes (read + write) per launch of the benchmark's compensated walk,
 # from one ncu capture (profiles/walk_f32ck_dram_traffic_stable_rank_n20000.md),
 # valid only while the walk's source is the one that was measured.
-TRAFFIC_RECORD = {"source_sha256_16": "3f93f6a809eaf2f1+5659efc8ee16f9a3",
-                  "by_schedule_layout": {("tile512x2", "full"): 5581926656 + 4807574784}}
+TRAFFIC_RECORD = {"source_sha256_16": "ebc615548d7cdf49+5659efc8ee16f9a3",
+                  "by_schedule_layout": {("tile512x2", "full"): 5263351808 + 4801109760}}
 
 
 def walk_source_id():
