@@ -733,12 +733,27 @@ def _line(name, value, unit, ms, steps, warmup, dtype, config, **extra):
     return d
 
 
+# secondary workloads that split over several ranks (the others are one-GPU
+# measurements and are skipped under torchrun)
+MULTI_RANK_WORKLOADS = ("gradient",)
+
+
+def dist_world():
+    return dist_env()[1]
+
+
 def run_workload(name, args):
     import torch
     import paper_2404_07183_gb300 as P
     P.build.build()
-    dev = "cuda:0"
-    torch.cuda.set_device(0)
+    rank, world, local = dist_env()
+    dev = f"cuda:{local}"
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        assert name in MULTI_RANK_WORKLOADS, name
+        if not dist.is_initialized():
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     pp = pipe_peaks()
@@ -1065,30 +1080,57 @@ def run_workload(name, args):
         x = P.PcfTensors.from_numpy(s, dev)
         Gt = torch.from_numpy(G).to(dev)
         pairs = N * (N - 1) // 2
+        # several ranks (torchrun): each walks its strided share of the tiles
+        # and one NCCL sum all-reduce of the two gradient arrays gives every
+        # rank the whole gradient
+        world = dist_world()
+        shard = (dist_env()[0], world) if world > 1 else None
 
         def step():
-            P.pcf_pairwise_backward(x, ("l2", False), Gt, check=False)
+            gv, gt = P.pcf_pairwise_backward(x, ("l2", False), Gt, check=False, shard=shard)
+            if world > 1:
+                import torch.distributed as dist
+                dist.all_reduce(gv)
+                dist.all_reduce(gt)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+            torch.cuda.synchronize()
         ms = float(np.mean(_timed(step, args.steps, args.warmup, flush, stream)))
+        if world > 1:
+            # every timed step ends in the all-reduce, so the ranks finish
+            # together; the slowest rank's mean is the step time
+            t = torch.tensor([ms], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
         rate = steps_walk / (ms * 1e-3)
         import oracle
         sub = synth.subset(s, np.arange(300))
         t0 = time.perf_counter()
-        if not args.no_cpu:
+        if not args.no_cpu and rank == 0:
             oracle.backward(sub, G[:300, :300], metric="l2", p=2.0)
         dt = max(time.perf_counter() - t0, 1e-9)
         # float64 operations per rectangle of the L2 adjoint: dt, d, d*dt, two
         # value-gradient fma; time gradient of the advancing side: v_new - v_other,
         # its square, fma(d, d, -b*b), times the weight
         bw_ops = 9
+        cfg = {"workload": "gradient N=4096 n~U{20..200} Exp(1) N(0,1) float64, "
+                           "d(sum G*D2^2)/d(values, times)", "N": N, "pairs": pairs,
+               "merge_steps": steps_walk, "l2": "flushed between steps"}
+        extra = {}
+        if world > 1:
+            cfg["parallelism"] = f"tile shards over {world} ranks + NCCL sum all-reduce of the gradients"
+            extra = {"n_gpus": world, "scaling": "strong"}
         return _line(name, pairs / (ms * 1e-3), "pair-gradients/s", ms, args.steps, args.warmup,
-                     "f64", {"workload": "gradient N=4096 n~U{20..200} Exp(1) N(0,1) float64, "
-                             "d(sum G*D2^2)/d(values, times)", "N": N, "pairs": pairs,
-                             "merge_steps": steps_walk, "l2": "flushed between steps"},
-                     merge_steps_per_s=rate,
-                     roofline={"bound": "fp64 pipe", "achieved": rate, "peak": fp64(bw_ops),
-                               "unit": "merge-steps/s", "frac": rate / fp64(bw_ops),
-                               "note": f"whole backward call (recomputing walk + scatter); "
-                                       f"{bw_ops} float64 ops per merge step"},
+                     "f64", cfg, merge_steps_per_s=rate,
+                     roofline={"bound": "fp64 pipe", "achieved": rate,
+                               "peak": fp64(bw_ops) * world,
+                               "unit": "merge-steps/s", "frac": rate / (fp64(bw_ops) * world),
+                               "note": f"whole backward call (recomputing walk + scatter"
+                                       f"{' + all-reduce' if world > 1 else ''}); "
+                                       f"{bw_ops} float64 ops per merge step"
+                                       f"{f', peak of {world} GPUs' if world > 1 else ''}"},
+                     **extra,
                      cpu_baseline={"value": 300 * 299 / 2 / dt, "unit": "pair-gradients/s",
                                    "cores": 1, "kind": "oracle", "seconds": dt,
                                    "sample": "first 300 PCFs, single-threaded oracle adjoint"})
@@ -1202,7 +1244,20 @@ def main():
                   "segments", "reduce"]
                  if args.workload == "all"
                  else [args.workload])
+        rank, world, _ = dist_env()
+        if world > 1:
+            names = [nm for nm in names if nm in MULTI_RANK_WORKLOADS]
+            if not names:
+                if rank == 0:
+                    print(json.dumps({"error": f"--workload {args.workload} runs on one GPU; "
+                                               "with several GPUs the headline and the "
+                                               "gradient workloads split their work"}), flush=True)
+                sys.exit(2)
         for nm in names:
+            d = None
+            if rank != 0:
+                run_workload(nm, args)
+                continue
             # clocks sampled over the whole workload run (its timed steps are
             # too short for the 200 ms sampling period alone)
             clk_path = os.path.join(tempfile.gettempdir(), f"pcf_bench_clocks_{nm}.csv")
@@ -1213,6 +1268,10 @@ def main():
             if d["clocks"] is not None:
                 d["clocks"]["window"] = "whole workload run"
             print(json.dumps(d), flush=True)
+        if world > 1:
+            import torch.distributed as dist
+            if dist.is_initialized():
+                dist.destroy_process_group()
 
 
 if __name__ == "__main__":
