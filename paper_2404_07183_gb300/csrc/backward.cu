@@ -73,15 +73,9 @@ __global__ void __launch_bounds__(1024) backward_kernel(const BackArgs a)
     for (int64_t u = blockIdx.x;; u += gridDim.x) {
         const int64_t t = a.shard_index + u * a.shard_count;   // this shard's tiles
         if (t >= a.ntiles) break;
-        // upper-triangle tile order (row block bi <= column block bj)
-        const double q = 2.0 * (double)NB + 1.0;
-        const double disc = q * q - 8.0 * (double)t;
-        int64_t m = (int64_t)((q - sqrt(disc > 0.0 ? disc : 0.0)) * 0.5);
-        if (m < 0) m = 0;
-        while (m > 0 && m * NB - m * (m - 1) / 2 > t) --m;
-        while ((m + 1) * NB - (m + 1) * m / 2 <= t) ++m;
-        const int64_t bj = NB - 1 - m;
-        const int64_t bi = bj - (t - (m * NB - m * (m - 1) / 2));
+        // the forward walk's upper-triangle tile order (row block bi <= column block bj)
+        int64_t bi, bj;
+        decode_upper_tile(NB, t, 0, bi, bj);
         const int64_t gi = bi * kTile + r, gj = bj * kTile + c;
         if (gi >= a.n || gj >= a.n) continue;
         if (bi == bj && r > c) continue;

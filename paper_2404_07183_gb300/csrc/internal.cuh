@@ -32,6 +32,13 @@ constexpr int kGroup = 16;       // PCFs interleaved per shared-memory region
 constexpr int kTilePcfs = 64;    // 32 row PCFs + 32 column PCFs
 constexpr int kWalkThreads = 1024;  // 32 warps: one diagonal of the tile each
 constexpr size_t kAlign = 256;
+// Tile queue bands: the default orders take the blocks of one side in bands
+// of kTileBand and, inside a band, every block of the other side in turn
+// against the band's blocks.  Each PCF of the other side is then staged from
+// memory once per band rather than once per block of the first side, which
+// cuts the walk's re-reads of the packed input (evicted from L2 by the
+// output stream) by about kTileBand.
+constexpr int kTileBand = 8;
 
 // Device-side error key, minimum wins (~0 = no error):
 //   bit 62: 0 for offsets errors (PCF index), 1 for element errors (element
@@ -73,6 +80,59 @@ __device__ __forceinline__ void record_error(Header* h, int detail, long long in
 __device__ __forceinline__ bool block_sees_error(const Header* h)
 {
     return __syncthreads_or(threadIdx.x == 0 && h->err != kNoError) != 0;
+}
+
+// Tile t of the queue (longest PCFs first) -> (row block bi, column block bj).
+// Symmetric (bi <= bj, NB blocks): line m of the triangle holds NB - m tiles
+// and starts at tile m NB - m (m - 1) / 2.  Order 1: line m is row block m,
+// columns NB - 1 down to m.  Order 0 (default): line m is column block
+// NB - 1 - m; the lines are taken in bands of kTileBand columns c1 down to
+// c0, and inside a band row blocks c1 down to 0 each take the band's columns
+// from c1 down (row c1 - r of the band's top triangle takes r + 1 of them).
+__device__ __forceinline__ void decode_upper_tile(int64_t NB, int64_t t, int order,
+                                                  int64_t& bi, int64_t& bj)
+{
+    auto start = [NB](int64_t m) { return m * NB - m * (m - 1) / 2; };
+    const double q = 2.0 * (double)NB + 1.0;
+    const double disc = q * q - 8.0 * (double)t;
+    int64_t m = (int64_t)((q - sqrt(disc > 0.0 ? disc : 0.0)) * 0.5);
+    if (m < 0) m = 0;
+    while (m > 0 && start(m) > t) --m;
+    while (start(m + 1) <= t) ++m;
+    if (order) {
+        bi = m;
+        bj = NB - 1 - (t - start(m));
+        return;
+    }
+    const int64_t m0 = (m / kTileBand) * kTileBand;                // the band's first line
+    const int64_t Bq = NB - m0 < kTileBand ? NB - m0 : kTileBand;  // its columns
+    const int64_t c1 = NB - 1 - m0, c0 = c1 - Bq + 1;
+    int64_t u = t - start(m0);
+    const int64_t tri = Bq * (Bq + 1) / 2;
+    if (u < tri) {
+        int64_t r = 0;
+        while ((r + 1) * (r + 2) / 2 <= u) ++r;
+        bi = c1 - r;
+        bj = c1 - (u - r * (r + 1) / 2);
+    } else {
+        u -= tri;
+        bi = c0 - 1 - u / Bq;
+        bj = c1 - u % Bq;
+    }
+}
+
+// Cross (nb_r x nb_c blocks): bands of kTileBand row blocks from the last
+// down; inside a band, column blocks from the last down, each against the
+// band's rows from the last down.
+__device__ __forceinline__ void decode_cross_tile(int64_t NBr, int64_t NBc, int64_t t,
+                                                  int64_t& bi, int64_t& bj)
+{
+    const int64_t band = t / ((int64_t)kTileBand * NBc);
+    const int64_t r1 = NBr - 1 - band * kTileBand;
+    const int64_t Bq = r1 + 1 < kTileBand ? r1 + 1 : kTileBand;
+    const int64_t u = t - band * (int64_t)kTileBand * NBc;
+    bj = NBc - 1 - u / Bq;
+    bi = r1 - u % Bq;
 }
 #endif
 

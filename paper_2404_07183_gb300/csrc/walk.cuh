@@ -306,27 +306,8 @@ __device__ __forceinline__ double weight_span(double l, double dt, double lam, d
 
 __device__ __forceinline__ void decode_tile(const WalkArgs& a, int64_t t, int64_t& bi, int64_t& bj)
 {
-    if (a.symmetric) {
-        const int64_t NB = a.nb_r;
-        double q = 2.0 * (double)NB + 1.0;
-        double disc = q * q - 8.0 * (double)t;
-        int64_t m = (int64_t)((q - sqrt(disc > 0.0 ? disc : 0.0)) * 0.5);
-        if (m < 0) m = 0;
-        while (m > 0 && m * NB - m * (m - 1) / 2 > t) --m;
-        while ((m + 1) * NB - (m + 1) * m / 2 <= t) ++m;
-        const int64_t within = t - (m * NB - m * (m - 1) / 2);
-        if (a.tile_order) {          // row block m, columns NB - 1 down to m
-            bi = m;
-            bj = NB - 1 - within;
-        } else {                     // column block NB - 1 - m, rows down from it
-            bj = NB - 1 - m;
-            bi = bj - within;
-        }
-    } else {
-        const int64_t q = t / a.nb_c, r = t - q * a.nb_c;
-        bi = a.nb_r - 1 - q;
-        bj = a.nb_c - 1 - r;
-    }
+    if (a.symmetric) decode_upper_tile(a.nb_r, t, a.tile_order, bi, bj);
+    else decode_cross_tile(a.nb_r, a.nb_c, t, bi, bj);
 }
 
 // CTAS: resident CTAs per SM the launch is built for (1 for 1024 threads; 2 or

@@ -43,14 +43,21 @@ def sorted_order(lengths, last_times=None) -> np.ndarray:
     return np.lexsort((lo, hi))
 
 
+TILE_BAND = 8
+
+
 def tile_order(n: int):
-    """(row block, column block) of the pairwise tiles in queue order:
-    column blocks from the last (longest PCFs) down, rows bi = bj .. 0."""
+    """(row block, column block) of the pairwise tiles in queue order: column
+    blocks from the last (longest PCFs) down in bands of TILE_BAND; inside a
+    band, row blocks from the band's last column down to 0, each against the
+    band's columns (those >= the row block) from the last down."""
     nb = (n + TILE - 1) // TILE
     out = []
-    for bj in range(nb - 1, -1, -1):
-        for bi in range(bj, -1, -1):
-            out.append((bi, bj))
+    for c1 in range(nb - 1, -1, -TILE_BAND):
+        c0 = max(0, c1 - TILE_BAND + 1)
+        for bi in range(c1, -1, -1):
+            for bj in range(c1, max(bi, c0) - 1, -1):
+                out.append((bi, bj))
     return out
 
 

@@ -31,16 +31,19 @@ def test_shards_sum_to_the_whole(sched, world):
         np.testing.assert_array_equal(t.cpu().numpy(), w.cpu().numpy())
 
 
-def test_host_mirror_matches_device_ownership():
+@pytest.mark.parametrize("n_short,n_long,sched", [(60, 40, "tile1024"), (500, 140, "tile1024"),
+                                                  (500, 140, "tile512x2")])
+def test_host_mirror_matches_device_ownership(n_short, n_long, sched):
     """The host mirror of the sort (length, then time scale for PCFs longer
-    than 256 points) and of the tile order names exactly the entries the
-    device writes for a shard."""
+    than 256 points) and of the tile order (bands of column blocks; 640 PCFs
+    make 20 blocks, three bands) names exactly the entries the device writes
+    for a shard."""
     if not gpu_available():
         pytest.skip("no CUDA device")
     import torch
     import paper_2404_07183_gb300 as P
     rng = np.random.default_rng(7)
-    lens = np.concatenate([rng.integers(2, 60, 60), rng.integers(257, 700, 40)])
+    lens = np.concatenate([rng.integers(2, 60, n_short), rng.integers(257, 700, n_long)])
     scales = np.exp(rng.normal(0, 1.5, lens.size))
     s = synth.from_lengths(lens, lambda r, m: r.exponential(1.0, m),
                            lambda r, o: r.standard_normal(o[-1]) + 3.0, rng, np.float64, "scaled")
@@ -53,7 +56,7 @@ def test_host_mirror_matches_device_ownership():
     last = s.times[s.offsets[1:] - 1]
     for r in range(3):
         part = shard.pairwise_shard(x, ["gram"], r, 3, precision="f64",
-                                    out_dtype=torch.float64, schedule="tile1024")[0].cpu().numpy()
+                                    out_dtype=torch.float64, schedule=sched)[0].cpu().numpy()
         got = {(i, j) for i, j in zip(*np.nonzero(part)) if i <= j}
         want = shard.shard_pairs(s.lengths(), r, 3, last_times=last)
         assert got == want

@@ -148,3 +148,25 @@ def test_shard_units_partition():
     assert set().union(*parts) == allp
     with pytest.raises(ValueError):
         list(shard.shard_units(10, 4, 4))
+
+
+def test_tile_order_mirror():
+    """Queue order of the pairwise tiles: every upper-triangle tile once, the
+    longest column band first, and inside a band of 8 column blocks each row
+    block's tiles consecutive (so a row block is staged once per band)."""
+    from paper_2404_07183_gb300 import shard
+    for n in (1, 32, 33, 300, 1000, 5000):
+        nb = (n + 31) // 32
+        tiles = shard.tile_order(n)
+        assert len(tiles) == nb * (nb + 1) // 2 == len(set(tiles))
+        assert all(bi <= bj for bi, bj in tiles)
+        assert tiles[0] == (nb - 1, nb - 1)
+        k = 0
+        for c1 in range(nb - 1, -1, -shard.TILE_BAND):
+            c0 = max(0, c1 - shard.TILE_BAND + 1)
+            band = tiles[k:k + sum(bj + 1 for bj in range(c0, c1 + 1))]
+            k += len(band)
+            assert {bj for _, bj in band} == set(range(c0, c1 + 1))
+            rows = [bi for bi, _ in band]
+            assert rows == sorted(rows, reverse=True)
+        assert k == len(tiles)
