@@ -817,7 +817,7 @@ def run_workload(name, args):
             sched, tune_ms = args.schedule, None
         else:
             sched, tune_ms = autotune.tune_pairwise(x, ["gram"], "f32c", layout="upper", repeats=1)
-        for prec in ("f32c", "f32"):
+        for prec in ("f32c", "f32", "f64"):
             ws = torch.empty(P.pcf_workspace_size(x, None, prec), dtype=torch.uint8, device=dev)
             mids = []
 
@@ -828,11 +828,15 @@ def run_workload(name, args):
                 mids.append(e)
                 P.pcf_pairwise(x, ["gram"], precision=prec, layout="upper", out=o, workspace=ws,
                                prepared=True, check=False, schedule=sched)
-            ms = _timed(step, max(1, min(args.steps, 2)), 1, flush, stream)
+            # the float64 walk takes ~10 s per step at full size: one timed step
+            nst = 1 if prec == "f64" else max(1, min(args.steps, 2))
+            ms = _timed(step, nst, 1, flush, stream)
             P.pcf_check(ws)
             res[prec] = float(np.mean(ms))
             del ws
         ms = res["f32c"]
+        # float64 operations per merge step of the Gram walk: dt, a*b, fma
+        gram64_ops = 3
         rate = (steps_walk + diag) / (ms * 1e-3)
         tally = 5 + 2 + 3
         return _line(name, pairs / (ms * 1e-3), "pair-integrals/s", ms, max(1, min(args.steps, 2)),
@@ -848,6 +852,12 @@ def run_workload(name, args):
                                "note": f"whole step; tally {tally} ops/step (Gram, Kahan)"},
                      f32={"ms_per_step": res["f32"], "value": pairs / (res["f32"] * 1e-3),
                           "frac": (steps_walk + diag) / (res["f32"] * 1e-3) / issue(5 + 2)},
+                     fp64={"ms_per_step": res["f64"], "value": pairs / (res["f64"] * 1e-3),
+                           "merge_steps_per_s": (steps_walk + diag) / (res["f64"] * 1e-3),
+                           "frac": (steps_walk + diag) / (res["f64"] * 1e-3) / fp64(gram64_ops),
+                           "bound": "fp64 pipe",
+                           "note": f"{gram64_ops} float64 ops per merge step (dt, a*b, fma); "
+                                   "one timed step"},
                      cpu_baseline=(None if args.no_cpu else
                                    _cpu_rows(s, ["gram"], seconds_target=8.0, row0=N // 2)))
 
