@@ -304,6 +304,16 @@ __device__ __forceinline__ double weight_span(double l, double dt, double lam, d
     else return exp(-lam * l) * (-expm1(-lam * dt)) * inv_lam;
 }
 
+// One 32-byte sector of global memory (32-byte aligned, read-only for the
+// kernel's lifetime) in a single 256-bit load.
+__device__ __forceinline__ void ldg_sector(const void* p, float (&r)[8])
+{
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(r[0]), "=f"(r[1]), "=f"(r[2]), "=f"(r[3]),
+          "=f"(r[4]), "=f"(r[5]), "=f"(r[6]), "=f"(r[7])
+        : "l"(p));
+}
+
 __device__ __forceinline__ void decode_tile(const WalkArgs& a, int64_t t, int64_t& bi, int64_t& bj)
 {
     if (a.symmetric) decode_upper_tile(a.nb_r, t, a.tile_order, bi, bj);
@@ -467,7 +477,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
             //      window start moved (the others are still in place) ----
             // THREADS is a multiple of 16, so a thread always serves the same
             // slot (tid & 15) of each region.  A thread copies whole 32-byte
-            // sectors of its PCF (G elements, two 16-byte loads; the packed
+            // sectors of its PCF (G elements, one 256-bit load; the packed
             // arrays are 256-byte aligned, so a sector holding one element of
             // the set lies inside its buffer) and stores the ones inside the
             // window; the 16 lanes of a half-warp store 16 different slots, so
@@ -488,17 +498,23 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                     const E* src = (p < kTile ? packR : packC) + (g0 - lead);
                     const int nsec = (kend + lead + G - 1) / G;
                     unsigned char* dst = smem + (unsigned)region * regionBytes + (unsigned)slot * sizeof(E);
-                    for (int sc = tid >> 4; sc < nsec; sc += THREADS / 16) {
-                        const float4* q = reinterpret_cast<const float4*>(src + sc * G);
-                        union { float4 f[2]; E e[G]; } u;
-                        u.f[0] = __ldg(q);
-                        u.f[1] = __ldg(q + 1);
+                    auto copy_sector = [&](int sc) {
+                        union { float f[8]; E e[G]; } u;
+                        ldg_sector(src + sc * G, u.f);
 #pragma unroll
                         for (int v = 0; v < G; ++v) {
                             const int k = sc * G - lead + v;
                             if (k >= 0 && k < kend)
                                 *reinterpret_cast<E*>(dst + (unsigned)k * kRow) = u.e[v];
                         }
+                    };
+                    if constexpr (CTAS >= 3) {
+                        // 40 registers per thread: one sector in flight
+                        for (int sc = tid >> 4; sc < nsec; sc += THREADS / 16) copy_sector(sc);
+                    } else {
+                        // up to four sectors' loads in flight per thread
+#pragma unroll 4
+                        for (int sc = tid >> 4; sc < nsec; sc += THREADS / 16) copy_sector(sc);
                     }
                 }
             }
@@ -602,9 +618,16 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
         if (lane_valid) {
             const int64_t gi = bi * kTile + my_r, gj = col0 + my_c;
             const int64_t i = a.perm_r[gi], j = a.perm_c[gj];
-            // values on the last intervals [t_last, inf) of both PCFs
-            const T vlf = WF::val(packR[sOff[pf] + sLen[pf] - 1]);
-            const T vlg = WF::val(packC[sOff[pg] + sLen[pg] - 1]);
+            // values on the last intervals [t_last, inf) of both PCFs (they
+            // decide only unbounded walks, whose last window holds every
+            // PCF's remaining elements)
+            T vlf = T(0), vlg = T(0);
+            if (!bounded) {
+                vlf = WF::val(*reinterpret_cast<const E*>(
+                    smem + base_f + (unsigned)(sLen[pf] - 1 - sS[pf]) * kRow));
+                vlg = WF::val(*reinterpret_cast<const E*>(
+                    smem + base_g + (unsigned)(sLen[pg] - 1 - sS[pg]) * kRow));
+            }
 #pragma unroll
             for (int m = 0; m < NM; ++m) {
                 const int MI = combo_metric(COMBO, m);
