@@ -17,7 +17,9 @@
 //     positions the lanes have reached.
 //   * Long PCFs are staged in time windows [T0, T1): T1 is the smallest end
 //     time of the W-th remaining element over the tile's PCFs, so every PCF's
-//     elements up to T1 fit.  A lane walks exactly the rectangles that end
+//     elements up to T1 fit (keyed and float64 walks may give the row side
+//     more of the window memory than the column side, or less, each window:
+//     see the split below).  A lane walks exactly the rectangles that end
 //     before T1 and resumes in the next window at element 0 of both its PCFs;
 //     the rectangles, their order and their arithmetic are the same as in one
 //     uninterrupted walk.
@@ -353,7 +355,15 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int32_t sS[kTilePcfs], sNext[kTilePcfs], sLen[kTilePcfs], sStaged[kTilePcfs];
     __shared__ int64_t sOff[kTilePcfs];
-    __shared__ K sT1part[2];
+    // split candidates: the keyed and float64 walks (16-byte elements, half
+    // the window of the plain float32 walk) choose among five; the plain
+    // float32 walk keeps the even split (measured: the choice cost it 3% on
+    // the stable-rank set at its larger window)
+    constexpr int kSplits = (KEYED || sizeof(T) == 8) ? 5 : 1;
+    constexpr bool kAdapt = kSplits > 1;
+    // window end per split candidate: [0] rows' minimum, [1] columns'
+    __shared__ K sT1part[2][kSplits];
+    __shared__ int sSplit;                          // split of the staged windows
     __shared__ int64_t sTile;
 
     if (gated_off(a.gate, a.gate_want64)) return;   // the other walk of an AUTO64 call
@@ -361,7 +371,17 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int W = a.window;
-    const unsigned regionBytes = (unsigned)W * kRow;
+    // The window memory holds NR regions of W elements per PCF: 2 regions of
+    // row PCFs and RC of column PCFs.  Each window splits it between the two
+    // sides (split c gives the rows Wr(c) elements, the columns Wc(c), with
+    // 2 Wr + RC Wc <= NR W), taking the split whose window reaches furthest:
+    // when the rows are dense in time and the columns sparse (or the other
+    // way round), the dense side gets the room, and the tile needs fewer
+    // windows.
+    constexpr int RC = NPCF / kGroup - 2, NR = 2 + RC;
+    auto split_wr = [W](int c) { return c == 0 ? W : (W * (c == 1 ? 3 : c == 2 ? 5 : c == 3 ? 2 : 6)) / 4; };
+    auto split_wc = [W](int c, int wr) { return (NR * W - 2 * wr) / RC; };
+    auto split_ok = [](int wr, int wc) { return wr >= 4 && wc >= 4; };
     const T p0 = (T)a.p[0];
     const unsigned smem_base = (unsigned)__cvta_generic_to_shared(smem);
     const E* packR = reinterpret_cast<const E*>(a.pack_r);
@@ -389,8 +409,18 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
     const int my_r = (lane + warp) & 31;
     const int my_c = lane & (TCOLS - 1);
     const int pf = my_r, pg = kTile + my_c;        // staged PCF indices
-    const unsigned base_f = (unsigned)(pf >> 4) * regionBytes + (unsigned)(pf & 15) * sizeof(E);
-    const unsigned base_g = (unsigned)(pg >> 4) * regionBytes + (unsigned)(pg & 15) * sizeof(E);
+    // byte offset of staged PCF p's slot when the rows hold wr elements per
+    // PCF and the columns wc (regions 0, 1: rows; 2 ..: columns)
+    auto slot_base = [](int p, int wr, int wc) -> unsigned {
+        const int r = p >> 4;
+        const unsigned e = r < 2 ? (unsigned)r * (unsigned)wr
+                                 : 2u * (unsigned)wr + (unsigned)(r - 2) * (unsigned)wc;
+        return e * kRow + (unsigned)(p & 15) * (unsigned)sizeof(E);
+    };
+    // the even split's slots (the only ones of the plain float32 walk)
+    const unsigned regionBytes = (unsigned)W * kRow;    // a region of the even split
+    const unsigned even_base_f = (unsigned)(pf >> 4) * regionBytes + (unsigned)(pf & 15) * sizeof(E);
+    const unsigned even_base_g = (unsigned)(pg >> 4) * regionBytes + (unsigned)(pg & 15) * sizeof(E);
 
     for (;;) {
         if (tid == 0) {
@@ -433,6 +463,7 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
             sNext[tid] = 0;
             sStaged[tid] = -1;   // window start of what is in shared memory
         }
+        if (kAdapt && tid == 0) sSplit = -1;
         const bool lane_valid = (bi * kTile + my_r < a.n_r) && (col0 + my_c < a.n_c);
 
         typename AccFor<PREC, COMBO>::type acc;
@@ -446,7 +477,10 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
         for (bool first = true;; first = false) {
             // ---- advance the window starts; window end T1 = min over PCFs of
             //      te[S + W - 1] (clamped to the last element) ----
-            if (tid < 64) {
+            //      for every split: warp 0 holds the 32 row PCFs, warp 1 the
+            //      column PCFs ----
+            if (!kAdapt && tid < 64) {
+                // one split: the window end of the even layout
                 K cand;
                 if constexpr (KEYED) cand = (K)kKeyInf; else cand = T(INFINITY);
                 const int len = tid < NPCF ? sLen[tid] : 0;
@@ -460,11 +494,55 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                     K other = __shfl_xor_sync(0xffffffffu, cand, o);
                     cand = other < cand ? other : cand;
                 }
-                if (lane == 0) sT1part[warp] = cand;
+                if (lane == 0) sT1part[warp][0] = cand;
+            }
+            if (kAdapt && tid < 64) {
+                K kinf;
+                if constexpr (KEYED) kinf = (K)kKeyInf; else kinf = T(INFINITY);
+                const int len = tid < NPCF ? sLen[tid] : 0;
+                if (len > 0 && !first) sS[tid] = sNext[tid];
+                const int S = len > 0 ? sS[tid] : 0;
+                const E* src = (tid < kTile ? packR : packC) + (len > 0 ? sOff[tid] : 0);
+#pragma unroll
+                for (int c = 0; c < kSplits; ++c) {
+                    const int wr = split_wr(c), wc = split_wc(c, wr);
+                    K cand = kinf;
+                    if (len > 0 && split_ok(wr, wc)) {
+                        int idx = S + (tid < kTile ? wr : wc) - 1;
+                        if (idx > len - 1) idx = len - 1;
+                        cand = WF::key(src[idx]);
+                    }
+                    for (int o = 16; o > 0; o >>= 1) {
+                        K other = __shfl_xor_sync(0xffffffffu, cand, o);
+                        cand = other < cand ? other : cand;
+                    }
+                    if (lane == 0) sT1part[warp][c] = cand;
+                }
             }
             __syncthreads();
-            K T1 = sT1part[0] < sT1part[1] ? sT1part[0] : sT1part[1];
+            // the split whose window reaches furthest (the even split on ties)
+            int split = 0;
+            K T1 = sT1part[0][0] < sT1part[1][0] ? sT1part[0][0] : sT1part[1][0];
+#pragma unroll
+            for (int c = 1; c < kSplits; ++c) {
+                const int wr = split_wr(c), wc = split_wc(c, wr);
+                const K t = sT1part[0][c] < sT1part[1][c] ? sT1part[0][c] : sT1part[1][c];
+                if (split_ok(wr, wc) && t > T1 && T1 < hi) { T1 = t; split = c; }
+            }
             if (T1 > hi) T1 = hi;
+            const int Wr = kAdapt ? split_wr(split) : W;
+            const int Wc = kAdapt ? split_wc(split, Wr) : W;
+            const bool moved = kAdapt && split != sSplit;   // regions moved: stage every PCF
+            // byte offset of region r (rows: 0, 1; columns: 2 ..)
+            auto region_base = [&](int r) -> unsigned {
+                if constexpr (!kAdapt) return (unsigned)r * regionBytes;
+                return r < 2 ? (unsigned)r * (unsigned)Wr * kRow
+                             : (2u * (unsigned)Wr + (unsigned)(r - 2) * (unsigned)Wc) * kRow;
+            };
+            auto pcf_w = [&](int p) {
+                if constexpr (!kAdapt) return W;
+                return p < kTile ? Wr : Wc;
+            };
             const bool last = !(T1 < hi);
             if (!(T1 > T0)) {
                 // more than W coincident interval ends in one PCF (only possible
@@ -489,15 +567,15 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                 for (int region = 0; region < NPCF / kGroup; ++region) {
                     const int p = region * kGroup + slot;
                     const int S = sS[p];
-                    if (S == sStaged[p]) continue;
+                    if (S == sStaged[p] && !moved) continue;
                     const int len = sLen[p];
                     int kend = len - S;
-                    if (kend > W) kend = W;
+                    if (kend > pcf_w(p)) kend = pcf_w(p);
                     const int64_t g0 = sOff[p] + S;               // first element of the window
                     const int lead = (int)(g0 & (G - 1));         // its place in its sector
                     const E* src = (p < kTile ? packR : packC) + (g0 - lead);
                     const int nsec = (kend + lead + G - 1) / G;
-                    unsigned char* dst = smem + (unsigned)region * regionBytes + (unsigned)slot * sizeof(E);
+                    unsigned char* dst = smem + region_base(region) + (unsigned)slot * sizeof(E);
                     auto copy_sector = [&](int sc) {
                         union { float f[8]; E e[G]; } u;
                         ldg_sector(src + sc * G, u.f);
@@ -526,8 +604,8 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                 int next = 0;
                 if (len > 0) {
                     int cnt = len - sS[tid];
-                    if (cnt > W) cnt = W;
-                    const unsigned colbase = (unsigned)(tid >> 4) * regionBytes + (unsigned)(tid & 15) * sizeof(E);
+                    if (cnt > pcf_w(tid)) cnt = pcf_w(tid);
+                    const unsigned colbase = region_base(tid >> 4) + (unsigned)(tid & 15) * sizeof(E);
                     int lo2 = 0, hi2 = cnt - 1;        // te[hi2] >= T1 holds by the choice of T1
                     while (lo2 < hi2) {
                         int mid = (lo2 + hi2) >> 1;
@@ -540,10 +618,13 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                 sStaged[tid] = sS[tid];
             }
             __syncthreads();
+            if (kAdapt && tid == 0) sSplit = split;
 
             // ---- walk this window ----
             if (lane_valid) {
                 int cnt = (sNext[pf] - sS[pf]) + (sNext[pg] - sS[pg]);
+                const unsigned base_f = kAdapt ? slot_base(pf, Wr, Wc) : even_base_f;
+                const unsigned base_g = kAdapt ? slot_base(pg, Wr, Wc) : even_base_g;
                 unsigned af = smem_base + base_f, ag = smem_base + base_g;
                 const E ef = *reinterpret_cast<const E*>(smem + base_f);
                 const E eg = *reinterpret_cast<const E*>(smem + base_g);
@@ -623,10 +704,14 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
             // PCF's remaining elements)
             T vlf = T(0), vlg = T(0);
             if (!bounded) {
+                const int wr_last = kAdapt ? split_wr(sSplit) : W;
+                const int wc_last = kAdapt ? split_wc(sSplit, wr_last) : W;
                 vlf = WF::val(*reinterpret_cast<const E*>(
-                    smem + base_f + (unsigned)(sLen[pf] - 1 - sS[pf]) * kRow));
+                    smem + (kAdapt ? slot_base(pf, wr_last, wc_last) : even_base_f) +
+                    (unsigned)(sLen[pf] - 1 - sS[pf]) * kRow));
                 vlg = WF::val(*reinterpret_cast<const E*>(
-                    smem + base_g + (unsigned)(sLen[pg] - 1 - sS[pg]) * kRow));
+                    smem + (kAdapt ? slot_base(pg, wr_last, wc_last) : even_base_g) +
+                    (unsigned)(sLen[pg] - 1 - sS[pg]) * kRow));
             }
 #pragma unroll
             for (int m = 0; m < NM; ++m) {

@@ -67,6 +67,31 @@ def test_schedule_dyadic_bitwise(pcf, sched):
         np.testing.assert_array_equal(g.cpu().numpy(), want)
 
 
+@pytest.mark.parametrize("prec", ["f64", "f32c", "f32c_round"])
+@pytest.mark.parametrize("sched", ["tile1024", "tile512x2", ("tile1024", 8), ("tile512x2", 24),
+                                   ("tile512x3", 40)], ids=str)
+def test_mixed_time_scales_dyadic_bitwise(pcf, prec, sched):
+    """Blocks whose PCFs run on time scales 2^-2 .. 2^3 apart (so the rows and
+    the columns of a tile fill their windows at different rates and the walks
+    that split the window memory between the two sides change the split from
+    window to window), with small windows: dyadic data keeps every integral
+    exact, so each form must give the oracle's matrices bit for bit."""
+    import torch
+    s = synth.dyadic(90, seed=83, max_len=150, min_len=1, max_gap=2, max_abs_value=6)
+    scale = 2.0 ** np.random.default_rng(84).integers(-2, 4, s.n)
+    t = s.times.copy()
+    for i in range(s.n):
+        t[s.offsets[i]:s.offsets[i + 1]] *= scale[i]
+    s = synth.PcfSet(s.offsets, t, s.values)
+    x = pcf.PcfTensors.from_numpy(s, "cuda")
+    got = pcf.pcf_pairwise(x, ["l1", ("l2", False), "gram"], precision=prec,
+                           out_dtype=torch.float64, schedule=sched)
+    for m, g in zip(["l1", ("l2", False), "gram"], got):
+        code = m if isinstance(m, str) else m[0]
+        want = oracle.matrix(s, metric=code, apply_root=isinstance(m, str))
+        np.testing.assert_array_equal(g.cpu().numpy(), want)
+
+
 @pytest.mark.parametrize("sched", ["tile512x2", "mergepath", ("tile1024", 16)], ids=str)
 def test_schedule_cross_and_packed(pcf, sched):
     import torch
