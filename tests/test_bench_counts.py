@@ -58,3 +58,21 @@ def test_matrix_errors_measure():
     assert abs(e["l1"] - 0.1) < 1e-12 and e["l2"] == 0.0 and abs(e["gram"] - 0.1) < 1e-12
     got["l2"][0, 0] = 1e-9
     assert bench.matrix_errors(got, want, np.array([4.0, 9.0]), 0)["l2"] == float("inf")
+
+
+def test_one_gpu_workloads_refuse_several_ranks():
+    """Under a launcher with two ranks, a workload that runs on one GPU only
+    (every secondary workload but the gradient) stops with an error line and
+    exit code 2 before any device work; the gradient workload is the one
+    secondary workload that splits over ranks."""
+    import json
+    import subprocess
+    env = dict(os.environ, RANK="0", WORLD_SIZE="2", LOCAL_RANK="0",
+               MASTER_ADDR="127.0.0.1", MASTER_PORT="29613")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2",
+                        "--workload", "uniform_small"], env=env, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 2, r.stderr[-2000:]
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert "runs on one GPU" in line["error"]
+    assert bench.MULTI_RANK_WORKLOADS == ("gradient",)
