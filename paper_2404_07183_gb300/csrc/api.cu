@@ -114,10 +114,13 @@ __global__ void inverse_perm_kernel(const int32_t* __restrict__ perm, int64_t n,
 // input order in place: a CTA loads one row into shared memory (coalesced,
 // 16-byte vectors when aligned), then writes entry c from sorted column
 // pos[c].  Reads and writes one matrix size each; pos (4N bytes) stays in L2.
+// The rows are r0 .. r1 - 1, or (rows != null) rows[r0 .. r1 - 1].
 template <typename V>
 __global__ void __launch_bounds__(512) permute_cols_kernel(PermuteMats pm, int64_t n,
                                                            const uint32_t* __restrict__ pos,
-                                                           const Header* hdr)
+                                                           const Header* hdr,
+                                                           const int32_t* __restrict__ rows,
+                                                           int64_t r0, int64_t r1)
 {
     extern __shared__ __align__(16) unsigned char psm[];
     V* row_s = reinterpret_cast<V*>(psm);
@@ -125,7 +128,9 @@ __global__ void __launch_bounds__(512) permute_cols_kernel(PermuteMats pm, int64
     constexpr int VEC = 16 / (int)sizeof(V);
     for (int m = 0; m < pm.n; ++m) {
         V* mat = reinterpret_cast<V*>(pm.mat[m]);
-        for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+        for (int64_t k = r0 + blockIdx.x; k < r1; k += gridDim.x) {
+            const int64_t r = rows ? (int64_t)rows[k] : k;
+            if (r < 0 || r >= n) continue;
             V* row = mat + r * n;
             const bool vec = (n % VEC) == 0 && ((uintptr_t)row % 16) == 0;
             if (vec) {
@@ -212,8 +217,11 @@ cudaError_t launch_inverse_perm(const int32_t* perm, int64_t n, uint32_t* pos, c
 }
 
 cudaError_t launch_permute_cols(void* const* mats, int nmats, int64_t n, int out_f64,
-                                const uint32_t* pos, const Header* hdr, cudaStream_t s)
+                                const uint32_t* pos, const Header* hdr, cudaStream_t s,
+                                const int32_t* rows, int64_t r0, int64_t r1)
 {
+    if (r1 < 0) r1 = n;
+    if (r1 <= r0) return cudaSuccess;
     PermuteMats pm;
     memset(&pm, 0, sizeof pm);
     pm.n = nmats;
@@ -226,18 +234,18 @@ cudaError_t launch_permute_cols(void* const* mats, int nmats, int64_t n, int out
     if (per < 1) per = 1;
     if (per > 4) per = 4;
     int64_t grid = (int64_t)device_sm_count() * per;
-    if (grid > n) grid = n;
+    if (grid > r1 - r0) grid = r1 - r0;
     cudaError_t e;
     if (out_f64) {
         e = cudaFuncSetAttribute(permute_cols_kernel<double>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        permute_cols_kernel<double><<<(int)grid, 512, smem, s>>>(pm, n, pos, hdr);
+        permute_cols_kernel<double><<<(int)grid, 512, smem, s>>>(pm, n, pos, hdr, rows, r0, r1);
     } else {
         e = cudaFuncSetAttribute(permute_cols_kernel<float>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        permute_cols_kernel<float><<<(int)grid, 512, smem, s>>>(pm, n, pos, hdr);
+        permute_cols_kernel<float><<<(int)grid, 512, smem, s>>>(pm, n, pos, hdr, rows, r0, r1);
     }
     return cudaGetLastError();
 }
@@ -625,14 +633,22 @@ static void keyed_bounds(WalkArgs& wa, const pcf_window* win, int form, const Ke
 
 // Put the columns of matrices written with kOutRowsInputColsSorted back into
 // the input order (the length sort's key buffer holds the inverse order).
+// With s0 < s1 only the rows of sorted positions s0 .. s1 - 1, whose inverse
+// order the caller has already computed.
 static int finish_cols_sorted(const SetView& sv, const pcf_integral* F, int nF, int64_t n,
-                              int out_f64, Header* hdr, cudaStream_t s)
+                              int out_f64, Header* hdr, cudaStream_t s, int64_t s0 = 0,
+                              int64_t s1 = -1)
 {
     uint32_t* pos = sv.khi[0];
     void* mats[PCF_MAX_INTEGRALS];
     for (int k = 0; k < nF; ++k) mats[k] = F[k].out;
-    if (launch_inverse_perm(sv.perm, n, pos, hdr, s) != cudaSuccess ||
-        launch_permute_cols(mats, nF, n, out_f64, pos, hdr, s) != cudaSuccess)
+    if (s1 < 0) {
+        if (launch_inverse_perm(sv.perm, n, pos, hdr, s) != cudaSuccess ||
+            launch_permute_cols(mats, nF, n, out_f64, pos, hdr, s) != cudaSuccess)
+            return PCF_ECUDA;
+        return PCF_OK;
+    }
+    if (launch_permute_cols(mats, nF, n, out_f64, pos, hdr, s, sv.perm, s0, s1) != cudaSuccess)
         return PCF_ECUDA;
     return PCF_OK;
 }
@@ -840,6 +856,7 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
         return ok;
     };
     auto fail = [&](int code) { join(); return code; };
+    int64_t permuted = 0;   // sorted rows whose columns are back in the input order
     if (sch.kernel == PCF_SCHED_MERGEPATH || nbands == 1) {
         rc = run_walks_for(wa, F, nF, pr, form, &sch, nullptr, stream);
         if (rc != PCF_OK) return rc;
@@ -859,12 +876,36 @@ int pcf_pairwise_to_host(const pcf_csr* x, const pcf_integral* F, int nF, int pr
             if (rc != PCF_OK) return fail(rc);
             const int64_t s0 = m0 * kTile;
             const int64_t s1 = m1 * kTile < N ? m1 * kTile : N;
-            if (!copy_rows(s0, s1)) return fail(PCF_ECUDA);
+            const bool last_band = k + 2 == cuts.size();
+            cudaEvent_t copied = nullptr;    // the copies of the earlier bands
+            if (last_band && cols_sorted && two) {
+                if (cudaEventCreateWithFlags(&copied, cudaEventDisableTiming) != cudaSuccess ||
+                    cudaEventRecord(copied, copy_stream) != cudaSuccess) {
+                    if (copied) cudaEventDestroy(copied);
+                    return fail(PCF_ECUDA);
+                }
+            }
+            if (!copy_rows(s0, s1)) {
+                if (copied) cudaEventDestroy(copied);
+                return fail(PCF_ECUDA);
+            }
+            if (copied) {
+                // the device rows of the earlier bands are final and copied:
+                // their columns go back to the input order while the last
+                // band's rows are copied
+                const bool ok = cudaStreamWaitEvent(stream, copied, 0) == cudaSuccess;
+                cudaEventDestroy(copied);
+                if (!ok) return fail(PCF_ECUDA);
+                rc = finish_cols_sorted(sv, F, nF, N, wa.out_f64, hdr, stream, 0, s0);
+                if (rc != PCF_OK) return fail(rc);
+                permuted = s0;
+            }
         }
     }
     if (!join()) return PCF_ECUDA;
     if (cols_sorted) {
-        rc = finish_cols_sorted(sv, F, nF, N, wa.out_f64, hdr, stream);
+        rc = permuted > 0 ? finish_cols_sorted(sv, F, nF, N, wa.out_f64, hdr, stream, permuted, N)
+                          : finish_cols_sorted(sv, F, nF, N, wa.out_f64, hdr, stream);
         if (rc != PCF_OK) return rc;
     }
     return cudaGetLastError() == cudaSuccess ? PCF_OK : PCF_ECUDA;

@@ -359,7 +359,8 @@ struct PermuteMats {
 cudaError_t launch_inverse_perm(const int32_t* perm, int64_t n, uint32_t* pos, const Header* hdr,
                                 cudaStream_t s);
 cudaError_t launch_permute_cols(void* const* mats, int nmats, int64_t n, int out_f64,
-                                const uint32_t* pos, const Header* hdr, cudaStream_t s);
+                                const uint32_t* pos, const Header* hdr, cudaStream_t s,
+                                const int32_t* rows = nullptr, int64_t r0 = 0, int64_t r1 = -1);
 // Largest N whose row fits the permutation pass's shared memory.
 bool permute_cols_fits(int64_t n, int out_f64);
 

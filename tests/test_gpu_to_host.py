@@ -85,6 +85,26 @@ def test_to_host_same_stream_and_given_buffers(pcf, stable700):
             np.testing.assert_array_equal(h.numpy(), w.cpu().numpy())
 
 
+@pytest.mark.parametrize("bands", [0, 3, 16])
+@pytest.mark.parametrize("schedule", ["tile512x2", "tile1024"])
+def test_to_host_device_matrices_in_input_order(pcf, stable700, bands, schedule):
+    """With a second copy stream the columns of the earlier bands' rows go
+    back to the input order while the last band's rows are copied: the device
+    matrices the call leaves behind equal pcf_pairwise's, bit for bit."""
+    import torch
+    s, x = stable700
+    dev = [torch.full((s.n, s.n), float("nan"), dtype=torch.float32, device="cuda")
+           for _ in METRICS]
+    cs = torch.cuda.Stream()
+    host = pcf.pcf_pairwise_to_host(x, METRICS, precision="f32c", out=dev, bands=bands,
+                                    schedule=schedule, copy_stream=cs)
+    torch.cuda.synchronize()
+    want = pcf.pcf_pairwise(x, METRICS, precision="f32c", schedule=schedule)
+    for w, d, h in zip(want, dev, host):
+        np.testing.assert_array_equal(d.cpu().numpy(), w.cpu().numpy())
+        np.testing.assert_array_equal(h.numpy(), w.cpu().numpy())
+
+
 def test_to_host_rejects_pageable_buffers(pcf, stable700):
     import torch
     s, x = stable700
