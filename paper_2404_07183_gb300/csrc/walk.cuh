@@ -344,11 +344,12 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
     constexpr int UNITS = kTile / TCOLS;            // work units per 32 x 32 tile
     constexpr int NPCF = kTile + TCOLS;             // staged PCFs: 32 rows + TCOLS columns
     constexpr unsigned kRow = kGroup * sizeof(E);   // bytes between element k and k+1 of a PCF
-    // steps per unrolled body: 4 (measured against 8 and 16: the shorter
-    // remainder loop per window wins, 1-2% on the keyed, plain and float64
-    // walks), except for the block-compensated accumulator, whose blocks are
-    // the unrolled bodies (16 rectangles)
-    constexpr int kUnroll = PREC == kF32B ? 16 : 4;
+    // steps per unrolled body: 4 for the keyed and float64 walks, 6 for the
+    // plain float32 walk (measured against 2, 8 and 16: a short remainder
+    // loop per window against the loop overhead per step), except for the
+    // block-compensated accumulator, whose blocks are the unrolled bodies
+    // (16 rectangles)
+    constexpr int kUnroll = PREC == kF32B ? 16 : (KEYED || sizeof(T) == 8 ? 4 : 6);
     static_assert(THREADS == 1024 || THREADS == 512, "thread count");
     static_assert(!KEYED || sizeof(T) == 4, "keyed walks are float32 walks");
 
