@@ -64,8 +64,8 @@ FP64_OPS_PER_STEP = 1 + 1 + 1 + 2 + 2   # dt, d, L1 fma, L2 mul+fma, Gram mul+fm
 # DRAM bytes (read + write) per launch of the benchmark's compensated walk,
 # from one ncu capture (profiles/walk_f32ck_dram_traffic_stable_rank_n20000.md),
 # valid only while the walk's source is the one that was measured.
-TRAFFIC_RECORD = {"source_sha256_16": "caf7a0a295c3db92+2f0e1f25a356a7dc",
-                  "by_schedule_layout": {("tile512x2", "full"): 2014162688 + 4878936064}}
+TRAFFIC_RECORD = {"source_sha256_16": "cc8a5afd078a05bc+2f0e1f25a356a7dc",
+                  "by_schedule_layout": {("tile512x2", "full"): 2015051264 + 4879343104}}
 
 
 def walk_source_id():

@@ -477,9 +477,9 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
 
         for (bool first = true;; first = false) {
             // ---- advance the window starts; window end T1 = min over PCFs of
-            //      te[S + W - 1] (clamped to the last element) ----
-            //      for every split: warp 0 holds the 32 row PCFs, warp 1 the
-            //      column PCFs ----
+            //      te[S + W_p - 1] (clamped to the last element), W_p the
+            //      share of the PCF's side (W for the even split); warp 0
+            //      holds the 32 row PCFs, warp 1 the column PCFs ----
             if (!kAdapt && tid < 64) {
                 // one split: the window end of the even layout
                 K cand;
@@ -552,8 +552,9 @@ __global__ void __launch_bounds__(THREADS, CTAS) walk_kernel(const WalkArgs a)
                 return;
             }
 
-            // ---- stage elements [S, S + min(W, len - S)) of the PCFs whose
-            //      window start moved (the others are still in place) ----
+            // ---- stage elements [S, S + min(W_p, len - S)) of the PCFs whose
+            //      window start moved, or all of them when the split changed
+            //      (the others are still in place) ----
             // THREADS is a multiple of 16, so a thread always serves the same
             // slot (tid & 15) of each region.  A thread copies whole 32-byte
             // sectors of its PCF (G elements, one 256-bit load; the packed
