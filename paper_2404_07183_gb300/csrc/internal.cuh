@@ -38,7 +38,7 @@ constexpr size_t kAlign = 256;
 // memory once per band rather than once per block of the first side, which
 // cuts the walk's re-reads of the packed input (evicted from L2 by the
 // output stream) by about kTileBand.
-constexpr int kTileBand = 8;
+constexpr int kTileBand = 16;
 
 // Device-side error key, minimum wins (~0 = no error):
 //   bit 62: 0 for offsets errors (PCF index), 1 for element errors (element

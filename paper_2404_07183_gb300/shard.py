@@ -43,7 +43,7 @@ def sorted_order(lengths, last_times=None) -> np.ndarray:
     return np.lexsort((lo, hi))
 
 
-TILE_BAND = 8
+TILE_BAND = 16
 
 
 def tile_order(n: int):

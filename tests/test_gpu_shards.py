@@ -36,7 +36,7 @@ def test_shards_sum_to_the_whole(sched, world):
 def test_host_mirror_matches_device_ownership(n_short, n_long, sched):
     """The host mirror of the sort (length, then time scale for PCFs longer
     than 256 points) and of the tile order (bands of column blocks; 640 PCFs
-    make 20 blocks, three bands) names exactly the entries the device writes
+    make 20 blocks, two bands) names exactly the entries the device writes
     for a shard."""
     if not gpu_available():
         pytest.skip("no CUDA device")

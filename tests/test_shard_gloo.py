@@ -152,7 +152,7 @@ def test_shard_units_partition():
 
 def test_tile_order_mirror():
     """Queue order of the pairwise tiles: every upper-triangle tile once, the
-    longest column band first, and inside a band of 8 column blocks each row
+    longest column band first, and inside a band of TILE_BAND column blocks each row
     block's tiles consecutive (so a row block is staged once per band)."""
     from paper_2404_07183_gb300 import shard
     for n in (1, 32, 33, 300, 1000, 5000):
